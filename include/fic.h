@@ -1,0 +1,219 @@
+/*
+ * fic.h -- C ABI of the GB300 fractal image coder (libfic.so).
+ *
+ * The library implements the modified no-search (MNS) fractal encoder of
+ * Salarian, Mohamadinia and Rasekhi, "A Modified No Search Algorithm for
+ * Fractal Image Compression", the comparison modes it is measured against
+ * and an iterated fixed-point decoder, as hand-written CUDA kernels for
+ * sm_103a.  Every entry point is plain C: device or host pointers and sizes,
+ * no framework types.  All GPU work is asynchronous on the cudaStream_t passed
+ * as `stream` (NULL = legacy default stream); results are readable after the
+ * stream is synchronised.
+ *
+ * Conventions
+ *   image     8-bit greyscale, row-major, pitch = width bytes, on the device.
+ *             The device pointer must be 16-byte aligned.
+ *   range     B x B block of the image; B runs bmax, bmax/2, ..., bmin over
+ *             the quadtree levels 1..L (L <= 4), Section 3 of the paper.
+ *   domain    2B x 2B block, decimated 2:1 by the mean of each 2x2 group
+ *             (Section 3, "mean filter to four neighbor pixels").
+ *   transform rhat = O + s (d - mean d): contrast s coded on 2^s_bits cells of
+ *             [-1, 1) (fixed point c = 128 s), luminance O on 2^o_bits levels
+ *             of 0..255 (Section 3.3).
+ *
+ * Errors: every call returns FIC_OK (0) or a negative FIC_E* code.  Argument
+ * errors are detected on the host before anything is enqueued.  Errors found
+ * on the device (a bounded wait that ran out, a record buffer too small) are
+ * written to the stream's info block (FIC_INFO_ERROR) and reported by
+ * fic_stream_info().
+ */
+#ifndef FIC_H
+#define FIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FIC_API __attribute__((visibility("default")))
+#else
+#define FIC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Search modes. */
+#define FIC_NOSEARCH 0   /* one centred domain per range, Section 3 */
+#define FIC_MNS 1        /* no-search + phase 2 (Technique 1), Sections 3.1-3.2 */
+#define FIC_LOCAL 2      /* domains around the centred one, Section 2 */
+#define FIC_EXHAUSTIVE 3 /* every domain on a grid, every isometry, Section 1 */
+
+/* Return codes. */
+#define FIC_OK 0
+#define FIC_EBADSIZE -1   /* width/height not supported for these params */
+#define FIC_EBADPARAM -2  /* invalid fic_params or pointer */
+#define FIC_ENOMEM -3     /* workspace or buffer too small / allocation failed */
+#define FIC_ECAPACITY -4  /* record buffer too small */
+#define FIC_ECUDA -5      /* a CUDA call failed */
+#define FIC_ETIMEOUT -6   /* a bounded device wait ran out */
+#define FIC_EBUDGET -7    /* serving: request can never fit the memory budget */
+#define FIC_EBUSY -8      /* serving: queue full / not finished yet */
+#define FIC_ECANCELLED -9 /* serving: request cancelled or server stopped */
+
+/* Encoder parameters (one set per image). */
+typedef struct fic_params {
+    int32_t mode;         /* FIC_NOSEARCH .. FIC_EXHAUSTIVE */
+    int32_t bmax, bmin;   /* range sides, powers of two, 4 <= bmin <= bmax <= 32, L <= 4 */
+    double thr_rms[4];    /* RMS error threshold E_j per level j=1..4 (Section 3);
+                             compared as SSE < round(256 T^2)/256 * n */
+    int32_t s_bits;       /* contrast code bits, 1..7 (5: 32 cells) */
+    int32_t o_bits;       /* luminance code bits, 1..8 (7: 128 levels) */
+    int32_t phase2;       /* MNS only: 1 = try phase 2 before splitting */
+    int32_t local_radius; /* FIC_LOCAL: search radius in pixels (16) */
+    int32_t local_step;   /* FIC_LOCAL: offset step, even (4) */
+    int32_t dom_step;     /* FIC_EXHAUSTIVE: domain grid step, even (4) */
+    int32_t isometries;   /* FIC_EXHAUSTIVE: 1 or 8 */
+} fic_params;
+
+/* One stored transform = one quadtree leaf (16 bytes).
+ * phase 1: k = contrast code, q = luminance code.
+ * phase 2 (MNS, Section 3.3): the block is coded as four sub-blocks TL, TR,
+ *   BL, BR; q = code of the block mean O_i, delta[0..2] = O_k - O_i for the
+ *   first three sub-blocks (O_4 follows from eq. (1)), bit b of k = contrast
+ *   choice of sub-block b from the level's two-element set (Section 3.2).
+ * dx, dy, iso: domain position and isometry (centred domain for
+ *   no-search/MNS). */
+typedef struct fic_record {
+    uint16_t x, y;
+    uint8_t level;
+    uint8_t phase;
+    uint8_t k;
+    uint8_t q;
+    int8_t delta[3];
+    uint8_t iso;
+    uint16_t dx, dy;
+} fic_record;
+
+/* Info block words (uint32) written by the encoder. */
+#define FIC_INFO_RECORDS 0  /* number of records */
+#define FIC_INFO_ERROR 1    /* 0 or a positive device error bit set */
+#define FIC_INFO_FITS_LO 2  /* range-domain fits evaluated (64-bit, low word) */
+#define FIC_INFO_FITS_HI 3
+#define FIC_INFO_WORDS 16
+
+/* Device error bits in FIC_INFO_ERROR. */
+#define FIC_DEVERR_TIMEOUT 1u
+#define FIC_DEVERR_CAPACITY 2u
+
+/* A transform stream in device memory.  The caller allocates every buffer
+ * (sizes from fic_stream_sizes) and keeps ownership.
+ *   records      capacity entries; leaves in canonical order: top-level
+ *                blocks in raster order, inside each the quadtree in
+ *                depth-first order TL, TR, BL, BR.
+ *   tile_offsets ntop + 1 entries: index of the first record of each
+ *                top-level block; the last entry is the record count.
+ *   split        ntop entries: bit 0 = the top-level block was split,
+ *                bits 1..4 = its children, bits 5..20 = grandchildren
+ *                (each group in depth-first order).
+ *   info         FIC_INFO_WORDS uint32 (record count, error bits, fits). */
+typedef struct fic_stream {
+    int32_t width, height;
+    fic_params params;
+    int32_t ntop;
+    int32_t capacity;
+    fic_record *records;
+    uint32_t *tile_offsets;
+    uint32_t *split;
+    uint32_t *info;
+} fic_stream;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+FIC_API int fic_version(void);
+
+/* Check width/height/params for the GPU encoder.  Returns FIC_OK or the
+ * error code the encoder would return.  Requirements: width and height
+ * multiples of bmax and of 16, at least 2*bmax, at most 65535. */
+FIC_API int fic_validate(int width, int height, const fic_params *p);
+
+/* Sizes of the buffers of a stream for this image: number of top-level
+ * blocks and the largest possible record count (every range at bmin). */
+FIC_API int fic_stream_sizes(int width, int height, const fic_params *p, int32_t *ntop,
+                     int32_t *max_records);
+
+/* Device workspace (bytes) fic_encode_batch needs for these images (fic_encode
+ * is a batch of one).  The workspace holds the image descriptors and the
+ * look-back state of the stream packer; it is overwritten by every call. */
+FIC_API size_t fic_encode_workspace_bytes(int count, const int *widths, const int *heights,
+                                  const fic_params *params);
+
+/* Encode one image (MNS quadtree, Section 3; or the mode in p).
+ * d_img: device image; out: stream whose buffers the caller allocated (its
+ * width/height/params/ntop/capacity are filled in).  d_workspace: device
+ * buffer of at least fic_encode_workspace_bytes(1, ...) bytes.
+ * One persistent kernel launch does the whole encode: moments, phase 1,
+ * phase 2, split and stream packing of every level. */
+FIC_API int fic_encode(const uint8_t *d_img, int width, int height, const fic_params *p, fic_stream *out,
+               void *d_workspace, size_t workspace_bytes, void *stream);
+
+/* Encode `count` images of any sizes in one persistent launch.  d_imgs,
+ * widths, heights, params, outs are host arrays of `count` entries (params
+ * may differ per image but all must share one bmax and one mode family). */
+FIC_API int fic_encode_batch(const uint8_t *const *d_imgs, const int *widths, const int *heights,
+                     int count, const fic_params *params, fic_stream *outs, void *d_workspace,
+                     size_t workspace_bytes, void *stream);
+
+/* Device workspace (bytes) fic_decode_batch needs: one image-sized scratch
+ * buffer per image (the Jacobi iterate) plus the descriptor table. */
+FIC_API size_t fic_decode_workspace_bytes(int count, const int *widths, const int *heights);
+
+/* Decode a stream: start from mid-grey (128) and apply every transform to
+ * the previous iterate `iters` times (Jacobi); the result (uint8, width x
+ * height) is written to d_out.  The paper leaves the decoder unspecified
+ * beyond its iterated-function-system basis (Section 1). */
+FIC_API int fic_decode(const fic_stream *st, int iters, uint8_t *d_out, void *d_workspace,
+               size_t workspace_bytes, void *stream);
+
+/* Decode `count` streams, one kernel launch per iteration for all of them. */
+FIC_API int fic_decode_batch(const fic_stream *sts, int count, int iters, uint8_t *const *d_outs,
+                     void *d_workspace, size_t workspace_bytes, void *stream);
+
+/* Copy a stream's info block to the host (synchronises `stream`) and return
+ * FIC_OK, FIC_ETIMEOUT or FIC_ECAPACITY according to its error bits.
+ * records/fits may be NULL. */
+FIC_API int fic_stream_info(const fic_stream *st, int64_t *records, int64_t *fits, void *stream);
+
+/* ---- Plans: prepare once, launch many times (e.g. inside a CUDA graph) ----
+ * A plan uploads the image descriptors of a batch into the caller's
+ * workspace (one synchronous-staging host-to-device copy) and records the
+ * launch geometry on the host.  fic_*_plan_run only enqueues kernels on
+ * `stream`, so it may be captured into a CUDA graph and replayed; the
+ * workspace, images and streams named at creation must stay allocated and
+ * must not be reused by another plan while the plan is in use. */
+typedef struct fic_plan fic_plan;
+
+/* Same arguments as fic_encode_batch; *plan receives a host object that
+ * fic_plan_destroy frees. */
+FIC_API int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, const int *heights,
+                           int count, const fic_params *params, fic_stream *outs, void *d_workspace,
+                           size_t workspace_bytes, void *stream, fic_plan **plan);
+/* Enqueue the encode of every image of the plan: one small initialisation
+ * kernel and one persistent encoder kernel. */
+FIC_API int fic_encode_plan_run(const fic_plan *plan, void *stream);
+
+/* Same arguments as fic_decode_batch, without the iteration count. */
+FIC_API int fic_decode_plan_create(const fic_stream *sts, int count, uint8_t *const *d_outs,
+                           void *d_workspace, size_t workspace_bytes, void *stream, fic_plan **plan);
+/* Enqueue `iters` decoder iterations (one kernel launch each). */
+FIC_API int fic_decode_plan_run(const fic_plan *plan, int iters, void *stream);
+
+FIC_API void fic_plan_destroy(fic_plan *plan);
+
+/* Human-readable name of a return code. */
+FIC_API const char *fic_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIC_H */

@@ -1,0 +1,360 @@
+// api.cu -- the C ABI of libfic.so: argument checks, descriptor tables,
+// workspace layout and kernel launches.  No allocation happens here: every
+// device buffer (streams, outputs, workspace) belongs to the caller.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fic_internal.cuh"
+
+namespace fic {
+cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int total_strips, uint32_t *status,
+                              uint32_t *ticket, cudaStream_t st);
+cudaError_t launch_decode_iter(int bmax, const DecDesc *d_descs, int count, int total_strips, int src_sel,
+                               int first, cudaStream_t st);
+int mns_strip_width(int bmax);
+}  // namespace fic
+
+using namespace fic;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+inline bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int levels_of(const fic_params *p) {
+    int L = 1;
+    for (int b = p->bmax; b > p->bmin; b >>= 1) ++L;
+    return L;
+}
+
+int check_params(const fic_params *p) {
+    if (!p) return FIC_EBADPARAM;
+    if (p->mode != FIC_NOSEARCH && p->mode != FIC_MNS) return FIC_EBADPARAM;
+    if (!(p->bmax == 8 || p->bmax == 16 || p->bmax == 32)) return FIC_EBADPARAM;
+    if (!is_pow2(p->bmin) || p->bmin < 4 || p->bmin > p->bmax) return FIC_EBADPARAM;
+    if (levels_of(p) > 4) return FIC_EBADPARAM;
+    if (p->s_bits < 1 || p->s_bits > 7 || p->o_bits < 1 || p->o_bits > 8) return FIC_EBADPARAM;
+    const int L = levels_of(p);
+    for (int j = 0; j < L; ++j)
+        if (!(p->thr_rms[j] >= 0.0) || !(p->thr_rms[j] < 256.0)) return FIC_EBADPARAM;
+    return FIC_OK;
+}
+
+int check_size(int W, int H, const fic_params *p) {
+    if (W <= 0 || H <= 0 || W > 65535 || H > 65535) return FIC_EBADSIZE;
+    if (W % p->bmax || H % p->bmax || W % 16 || H % 16) return FIC_EBADSIZE;
+    if (W < 2 * p->bmax || H < 2 * p->bmax) return FIC_EBADSIZE;
+    return FIC_OK;
+}
+
+inline int64_t t2q_of(double t) { return (int64_t)(t * t * 256.0 + 0.5); }
+
+int strips_per_row(int W, int bmax) {
+    const int tops = fic::mns_strip_width(bmax) / bmax;
+    const int tw = W / bmax;
+    return (tw + tops - 1) / tops;
+}
+
+int nstrips_of(int W, int H, int bmax) { return strips_per_row(W, bmax) * (H / bmax); }
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? FIC_OK : FIC_ECUDA; }
+
+}  // namespace
+
+// Host-side plan of an encode launch: the uploaded descriptor table and the
+// look-back state live in the caller's workspace.
+struct fic_plan {
+    int kind;  // 0 encode, 1 decode
+    int count;
+    int bmax;
+    int total_strips;
+    void *ws;
+    size_t ws_bytes;
+    EncDesc *d_enc;
+    DecDesc *d_dec;
+    uint32_t *status;
+    uint32_t *ticket;
+    std::vector<DecDesc> hdec;  // decode: host copy (buffers per image)
+    std::vector<uint8_t *> outs;
+    std::vector<size_t> out_bytes;
+};
+
+extern "C" {
+
+int fic_version(void) { return 100; }
+
+const char *fic_strerror(int code) {
+    switch (code) {
+    case FIC_OK: return "ok";
+    case FIC_EBADSIZE: return "unsupported image size";
+    case FIC_EBADPARAM: return "invalid parameter";
+    case FIC_ENOMEM: return "buffer or workspace too small";
+    case FIC_ECAPACITY: return "record buffer too small";
+    case FIC_ECUDA: return "CUDA error";
+    case FIC_ETIMEOUT: return "device wait timed out";
+    case FIC_EBUDGET: return "request exceeds the memory budget";
+    case FIC_EBUSY: return "busy";
+    case FIC_ECANCELLED: return "cancelled";
+    default: return "unknown error";
+    }
+}
+
+int fic_validate(int width, int height, const fic_params *p) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    return check_size(width, height, p);
+}
+
+int fic_stream_sizes(int width, int height, const fic_params *p, int32_t *ntop, int32_t *max_records) {
+    int rc = fic_validate(width, height, p);
+    if (rc) return rc;
+    if (ntop) *ntop = (width / p->bmax) * (height / p->bmax);
+    if (max_records) *max_records = (width / p->bmin) * (height / p->bmin);
+    return FIC_OK;
+}
+
+size_t fic_encode_workspace_bytes(int count, const int *widths, const int *heights, const fic_params *params) {
+    if (count <= 0 || !widths || !heights || !params) return 0;
+    size_t strips = 0;
+    for (int i = 0; i < count; ++i) {
+        if (fic_validate(widths[i], heights[i], &params[i])) return 0;
+        strips += (size_t)nstrips_of(widths[i], heights[i], params[i].bmax);
+    }
+    return align_up(sizeof(EncDesc) * (size_t)count) + align_up(4 * strips) + kAlign;
+}
+
+int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, const int *heights, int count,
+                           const fic_params *params, fic_stream *outs, void *d_workspace, size_t ws_bytes,
+                           void *stream, fic_plan **plan_out) {
+    if (!plan_out || count <= 0 || !d_imgs || !widths || !heights || !params || !outs || !d_workspace)
+        return FIC_EBADPARAM;
+    *plan_out = nullptr;
+    const int bmax = params[0].bmax;
+    std::vector<EncDesc> h((size_t)count);
+    int strips = 0;
+    for (int i = 0; i < count; ++i) {
+        const fic_params *p = &params[i];
+        int rc = fic_validate(widths[i], heights[i], p);
+        if (rc) return rc;
+        if (p->bmax != bmax) return FIC_EBADPARAM;
+        if (!d_imgs[i] || (reinterpret_cast<uintptr_t>(d_imgs[i]) & 15)) return FIC_EBADPARAM;
+        fic_stream *o = &outs[i];
+        if (!o->records || !o->tile_offsets || !o->split || !o->info || o->capacity <= 0) return FIC_EBADPARAM;
+        if (reinterpret_cast<uintptr_t>(o->records) & 15) return FIC_EBADPARAM;
+        if (reinterpret_cast<uintptr_t>(o->info) & 7) return FIC_EBADPARAM;
+        const int W = widths[i], H = heights[i];
+        o->width = W;
+        o->height = H;
+        o->params = *p;
+        o->ntop = (W / bmax) * (H / bmax);
+        EncDesc &d = h[(size_t)i];
+        std::memset(&d, 0, sizeof(d));
+        d.img = d_imgs[i];
+        d.rec = o->records;
+        d.tile_off = o->tile_offsets;
+        d.split = o->split;
+        d.info = o->info;
+        const int L = levels_of(p);
+        for (int j = 0; j < 4; ++j) d.t2q[j] = t2q_of(p->thr_rms[j < L ? j : L - 1]);
+        d.W = W;
+        d.H = H;
+        d.tw = W / bmax;
+        d.th = H / bmax;
+        d.spr = strips_per_row(W, bmax);
+        d.strip_base = strips;
+        d.nstrips = nstrips_of(W, H, bmax);
+        d.capacity = o->capacity;
+        d.mode = p->mode;
+        d.bmin = p->bmin;
+        d.L = L;
+        d.phase2 = p->phase2 ? 1 : 0;
+        d.s_bits = p->s_bits;
+        d.o_bits = p->o_bits;
+        d.local_radius = p->local_radius;
+        d.local_step = p->local_step;
+        strips += d.nstrips;
+    }
+    const size_t need = align_up(sizeof(EncDesc) * (size_t)count) + align_up(4 * (size_t)strips) + kAlign;
+    if (ws_bytes < need || (reinterpret_cast<uintptr_t>(d_workspace) & (kAlign - 1))) return FIC_ENOMEM;
+    fic_plan *pl = new (std::nothrow) fic_plan();
+    if (!pl) return FIC_ENOMEM;
+    uint8_t *w = static_cast<uint8_t *>(d_workspace);
+    pl->kind = 0;
+    pl->count = count;
+    pl->bmax = bmax;
+    pl->total_strips = strips;
+    pl->ws = d_workspace;
+    pl->ws_bytes = ws_bytes;
+    pl->d_enc = reinterpret_cast<EncDesc *>(w);
+    pl->status = reinterpret_cast<uint32_t *>(w + align_up(sizeof(EncDesc) * (size_t)count));
+    pl->ticket = reinterpret_cast<uint32_t *>(w + align_up(sizeof(EncDesc) * (size_t)count) + align_up(4 * (size_t)strips));
+    pl->d_dec = nullptr;
+    cudaError_t e = cudaMemcpyAsync(pl->d_enc, h.data(), sizeof(EncDesc) * (size_t)count, cudaMemcpyHostToDevice,
+                                    static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        delete pl;
+        return FIC_ECUDA;
+    }
+    *plan_out = pl;
+    return FIC_OK;
+}
+
+int fic_encode_plan_run(const fic_plan *pl, void *stream) {
+    if (!pl || pl->kind != 0) return FIC_EBADPARAM;
+    return cuda_rc(launch_mns_encode(pl->bmax, pl->d_enc, pl->count, pl->total_strips, pl->status, pl->ticket,
+                                     static_cast<cudaStream_t>(stream)));
+}
+
+void fic_plan_destroy(fic_plan *pl) { delete pl; }
+
+int fic_encode_batch(const uint8_t *const *d_imgs, const int *widths, const int *heights, int count,
+                     const fic_params *params, fic_stream *outs, void *d_workspace, size_t workspace_bytes,
+                     void *stream) {
+    fic_plan *pl = nullptr;
+    int rc = fic_encode_plan_create(d_imgs, widths, heights, count, params, outs, d_workspace, workspace_bytes,
+                                    stream, &pl);
+    if (rc) return rc;
+    rc = fic_encode_plan_run(pl, stream);
+    fic_plan_destroy(pl);
+    return rc;
+}
+
+int fic_encode(const uint8_t *d_img, int width, int height, const fic_params *p, fic_stream *out,
+               void *d_workspace, size_t workspace_bytes, void *stream) {
+    return fic_encode_batch(&d_img, &width, &height, 1, p, out, d_workspace, workspace_bytes, stream);
+}
+
+size_t fic_decode_workspace_bytes(int count, const int *widths, const int *heights) {
+    if (count <= 0 || !widths || !heights) return 0;
+    size_t b = align_up(sizeof(DecDesc) * (size_t)count);
+    for (int i = 0; i < count; ++i) {
+        if (widths[i] <= 0 || heights[i] <= 0) return 0;
+        b += align_up((size_t)widths[i] * (size_t)heights[i]);
+    }
+    return b;
+}
+
+int fic_decode_plan_create(const fic_stream *sts, int count, uint8_t *const *d_outs, void *d_workspace,
+                           size_t ws_bytes, void *stream, fic_plan **plan_out) {
+    if (!plan_out || count <= 0 || !sts || !d_outs || !d_workspace) return FIC_EBADPARAM;
+    *plan_out = nullptr;
+    const int bmax = sts[0].params.bmax;
+    std::vector<int> ws((size_t)count), hs((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        ws[(size_t)i] = sts[i].width;
+        hs[(size_t)i] = sts[i].height;
+    }
+    const size_t need = fic_decode_workspace_bytes(count, ws.data(), hs.data());
+    if (need == 0) return FIC_EBADPARAM;
+    if (ws_bytes < need || (reinterpret_cast<uintptr_t>(d_workspace) & (kAlign - 1))) return FIC_ENOMEM;
+    fic_plan *pl = new (std::nothrow) fic_plan();
+    if (!pl) return FIC_ENOMEM;
+    pl->hdec.resize((size_t)count);
+    uint8_t *w = static_cast<uint8_t *>(d_workspace);
+    uint8_t *scratch = w + align_up(sizeof(DecDesc) * (size_t)count);
+    int strips = 0;
+    for (int i = 0; i < count; ++i) {
+        const fic_stream *s = &sts[i];
+        int rc = fic_validate(s->width, s->height, &s->params);
+        if (rc == FIC_OK && s->params.bmax != bmax) rc = FIC_EBADPARAM;
+        if (rc == FIC_OK && (!s->records || !s->tile_offsets || !d_outs[i] ||
+                             (reinterpret_cast<uintptr_t>(d_outs[i]) & 15)))
+            rc = FIC_EBADPARAM;
+        if (rc) {
+            delete pl;
+            return rc;
+        }
+        DecDesc &d = pl->hdec[(size_t)i];
+        std::memset(&d, 0, sizeof(d));
+        d.rec = s->records;
+        d.tile_off = s->tile_offsets;
+        d.buf[0] = d_outs[i];
+        d.buf[1] = scratch;
+        scratch += align_up((size_t)s->width * (size_t)s->height);
+        d.W = s->width;
+        d.H = s->height;
+        d.tw = s->width / bmax;
+        d.th = s->height / bmax;
+        d.spr = strips_per_row(s->width, bmax);
+        d.strip_base = strips;
+        d.nstrips = nstrips_of(s->width, s->height, bmax);
+        d.mode = s->params.mode;
+        d.bmin = s->params.bmin;
+        d.L = levels_of(&s->params);
+        d.s_bits = s->params.s_bits;
+        d.o_bits = s->params.o_bits;
+        strips += d.nstrips;
+        pl->outs.push_back(d_outs[i]);
+        pl->out_bytes.push_back((size_t)s->width * (size_t)s->height);
+    }
+    pl->kind = 1;
+    pl->count = count;
+    pl->bmax = bmax;
+    pl->total_strips = strips;
+    pl->ws = d_workspace;
+    pl->ws_bytes = ws_bytes;
+    pl->d_dec = reinterpret_cast<DecDesc *>(w);
+    pl->d_enc = nullptr;
+    cudaError_t e = cudaMemcpyAsync(pl->d_dec, pl->hdec.data(), sizeof(DecDesc) * (size_t)count,
+                                    cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        delete pl;
+        return FIC_ECUDA;
+    }
+    *plan_out = pl;
+    return FIC_OK;
+}
+
+int fic_decode_plan_run(const fic_plan *pl, int iters, void *stream) {
+    if (!pl || pl->kind != 1 || iters < 0) return FIC_EBADPARAM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (iters == 0) {
+        for (size_t i = 0; i < pl->outs.size(); ++i) {
+            cudaError_t e = cudaMemsetAsync(pl->outs[i], 128, pl->out_bytes[i], st);
+            if (e != cudaSuccess) return FIC_ECUDA;
+        }
+        return FIC_OK;
+    }
+    for (int it = 0; it < iters; ++it) {
+        const int src_sel = (iters - it) & 1;  // the last iteration writes buf[0] (the output)
+        cudaError_t e = launch_decode_iter(pl->bmax, pl->d_dec, pl->count, pl->total_strips, src_sel, it == 0, st);
+        if (e != cudaSuccess) return FIC_ECUDA;
+    }
+    return FIC_OK;
+}
+
+int fic_decode_batch(const fic_stream *sts, int count, int iters, uint8_t *const *d_outs, void *d_workspace,
+                     size_t workspace_bytes, void *stream) {
+    fic_plan *pl = nullptr;
+    int rc = fic_decode_plan_create(sts, count, d_outs, d_workspace, workspace_bytes, stream, &pl);
+    if (rc) return rc;
+    rc = fic_decode_plan_run(pl, iters, stream);
+    fic_plan_destroy(pl);
+    return rc;
+}
+
+int fic_decode(const fic_stream *st, int iters, uint8_t *d_out, void *d_workspace, size_t workspace_bytes,
+               void *stream) {
+    return fic_decode_batch(st, 1, iters, &d_out, d_workspace, workspace_bytes, stream);
+}
+
+int fic_stream_info(const fic_stream *st, int64_t *records, int64_t *fits, void *stream) {
+    if (!st || !st->info) return FIC_EBADPARAM;
+    uint32_t h[FIC_INFO_WORDS];
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(h, st->info, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return FIC_ECUDA;
+    if (records) *records = (int64_t)h[FIC_INFO_RECORDS];
+    if (fits) *fits = (int64_t)h[FIC_INFO_FITS_LO] | ((int64_t)h[FIC_INFO_FITS_HI] << 32);
+    if (h[FIC_INFO_ERROR] & FIC_DEVERR_TIMEOUT) return FIC_ETIMEOUT;
+    if (h[FIC_INFO_ERROR] & FIC_DEVERR_CAPACITY) return FIC_ECAPACITY;
+    return FIC_OK;
+}
+
+}  // extern "C"

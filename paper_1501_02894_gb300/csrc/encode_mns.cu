@@ -1,0 +1,600 @@
+// encode_mns.cu -- fused quadtree encoder for the no-search and MNS modes.
+//
+// Paper: Salarian, Mohamadinia, Rasekhi, "A Modified No Search Algorithm for
+// Fractal Image Compression".  Section 3 (no-search quadtree with per-level
+// thresholds, forced acceptance at the last level), Sections 3.1-3.2 (MNS
+// phase 2, "Technique 1"), Section 3.3 (stored parameters, eq. (1)).
+//
+// GPU design.  One warp owns a strip of 1024 pixels: bmax rows by 1024/bmax
+// columns, i.e. 1, 4 or 16 consecutive top-level blocks of one block row
+// (consecutive in the stream's raster order).  Everything the quadtree of
+// those blocks can touch lies inside the union of their level-1 domains, so
+// the warp decimates that window once into shared memory (2x2 sums packed as
+// 16-bit pairs, at even and at odd alignment) and then runs all levels out of
+// registers and shared memory:
+//   * lane l owns an 8x4-pixel patch of the strip; every quadtree block of
+//     side >= 8 is a power-of-two group of lanes, a 4x4 block is half a patch;
+//   * moments per level: sum r*d4 and sum d4^2 by dp2a on packed operands,
+//     sums by packed adds, group totals by xor-shuffle butterflies;
+//   * the phase-1 code choice, the collage error and the phase-2 test are
+//     exact int64 integer arithmetic, evaluated redundantly by every lane of
+//     a block (lock-step, no divergence between blocks);
+//   * a level is skipped as soon as no block of the strip needs it;
+//   * leaves are ranked in the canonical order by a 64-bit warp mask and
+//     written with one 16-byte store each; the strip's offset in the stream
+//     comes from a decoupled look-back over the strips of the image (bounded
+//     spin), so the stream is packed in the same launch.
+// The grid is persistent: each warp takes strips from an atomic ticket in
+// stream order, which also guarantees progress of the look-back.
+#include "fic_internal.cuh"
+
+namespace fic {
+
+template <int BMAX>
+struct Geom {
+    static constexpr int SW = 1024 / BMAX;  // strip width, pixels
+    static constexpr int PC = SW / 8;       // patches per patch row
+    static constexpr int PR = BMAX / 4;     // patch rows
+    static constexpr int TOPS = SW / BMAX;  // top-level blocks per strip
+    // words per row of each packed decimated array (pairs of 2x2 sums)
+    static constexpr int NP = BMAX == 32 ? 16 : (BMAX == 16 ? 24 : 40);
+    static constexpr int WORDS = BMAX * NP;
+};
+
+constexpr int kWarps = 8;
+constexpr uint32_t kAgg = 1u << 30, kIncl = 2u << 30, kValMask = (1u << 30) - 1;
+
+// Result of the phase-1 fit of one block.
+struct Fit {
+    long long ncrr, ncdr, ncdd;  // n Srr - Sr^2, n Sdr - Sd Sr, n Sdd - Sd^2
+    int sr;
+    int k, q;
+    bool pass;  // collage error below the level threshold
+};
+
+__device__ __forceinline__ int lum(int q, int ko1, uint32_t magic) {
+    // floor((510 q + ko1) / (2 ko1)) by multiply-high; exact for these ranges
+    return (int)__umulhi((uint32_t)(510 * q + ko1), magic);
+}
+
+// Phase-1 fit (Section 3: the best contrast factor for the one domain, the
+// error, the threshold test).  Exact: the contrast code is the grid point
+// nearest to c* = 512 nCdr / nCdd, found from a float estimate and settled by
+// int64 comparisons against the grid midpoints; ties go to the smaller |c|,
+// then to c > 0.  The luminance code is the level nearest the block mean.
+__device__ __forceinline__ void fit_phase1(int sr, int srr, int sd, int sdd, int sdr, int lg2n,
+                                           int s_bits, int ko1, uint32_t magic, float qscale,
+                                           long long thr, Fit &f) {
+    f.sr = sr;
+    f.ncrr = ((long long)srr << lg2n) - (long long)sr * sr;
+    f.ncdr = ((long long)sdr << lg2n) - (long long)sd * sr;
+    f.ncdd = ((long long)sdd << lg2n) - (long long)sd * sd;
+    const int K = 1 << s_bits, step = 256 >> s_bits;
+    int k;
+    if (f.ncdd <= 0) {
+        k = K >> 1;
+    } else {
+        float cs = 512.f * (float)f.ncdr / (float)f.ncdd;
+        float kf = (cs + 128.f) / (float)step - 0.5f;
+        kf = fminf(fmaxf(kf, 0.f), (float)(K - 1));
+        k = __float2int_rn(kf);
+        const long long a = 512LL * f.ncdr;
+#pragma unroll 1
+        for (int it = 0; it < K && k < K - 1; ++it) {
+            long long m = (long long)(step * (k + 1) - 128);
+            long long b = m * f.ncdd;
+            if (a > b || (a == b && m <= 0)) ++k;
+            else break;
+        }
+#pragma unroll 1
+        for (int it = 0; it < K && k > 0; ++it) {
+            long long m = (long long)(step * k - 128);
+            long long b = m * f.ncdd;
+            if (a > b || (a == b && m <= 0)) break;
+            --k;
+        }
+    }
+    int q0 = __float2int_rn((float)sr * qscale * __int_as_float((127 - lg2n) << 23));
+    q0 = clampi(q0, 0, ko1);
+    int bq = q0, bd = 0x7fffffff;
+#pragma unroll
+    for (int dq = -1; dq <= 1; ++dq) {
+        int q = q0 + dq;
+        if (q < 0 || q > ko1) continue;
+        int d = abs(sr - (lum(q, ko1, magic) << lg2n));
+        if (d < bd) {
+            bd = d;
+            bq = q;
+        }
+    }
+    f.k = k;
+    f.q = bq;
+    const long long c = contrast_code(k, s_bits);
+    const long long e = (long long)bd;
+    const long long E = 262144LL * f.ncrr - 1024LL * c * f.ncdr + c * c * f.ncdd + 262144LL * e * e;
+    f.pass = E < thr;
+}
+
+// Collage error of a phase-2 sub-block with a given luminance and the
+// better of the level's two contrasts (Section 3.2); returns pass and bit.
+__device__ __forceinline__ bool fit_phase2_sub(const Fit &f, int lg2n, int O, int c0, int c1,
+                                               long long thr, int &bit) {
+    // E(c1) < E(c0)  <=>  (c1 + c0) nCdd < 1024 nCdr   (c1 > c0)
+    bit = ((long long)(c1 + c0) * f.ncdd < 1024LL * f.ncdr) ? 1 : 0;
+    const long long c = bit ? c1 : c0;
+    const long long e = (long long)f.sr - ((long long)O << lg2n);
+    const long long E = 262144LL * f.ncrr - 1024LL * c * f.ncdr + c * c * f.ncdd + 262144LL * e * e;
+    return E < thr;
+}
+
+__device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y) {
+    uint32_t z = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) z |= (((x >> b) & 1u) << (2 * b)) | (((y >> b) & 1u) << (2 * b + 1));
+    return z;
+}
+
+// Bitmask of the lanes that form the lane's block when a block spans gx patch
+// columns and gy patch rows.
+template <int PC>
+__device__ __forceinline__ uint32_t group_mask(int pc, int pr, int gx, int gy) {
+    int base = (pr - pr % gy) * PC + (pc - pc % gx);
+    uint32_t row = (gx >= 32) ? 0xffffffffu : ((1u << gx) - 1u);
+    uint32_t m = 0;
+    for (int i = 0; i < gy; ++i) m |= row << (base + i * PC);
+    return m;
+}
+
+template <int PC>
+__device__ __forceinline__ int group_sum(int v, int gx, int gy) {
+    for (int m = 1; m < gx; m <<= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    for (int m = 1; m < gy; m <<= 1) v += __shfl_xor_sync(0xffffffffu, v, m * PC);
+    return v;
+}
+
+template <int PC>
+__device__ __forceinline__ uint32_t group_or(uint32_t v, int gx, int gy) {
+    for (int m = 1; m < gx; m <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, m);
+    for (int m = 1; m < gy; m <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, m * PC);
+    return v;
+}
+
+struct Leaf {
+    uint32_t w0, w1, w2, w3;  // the 16-byte fic_record
+    int pos;                  // canonical position in the strip, -1 = none
+};
+
+__device__ __forceinline__ void make_leaf(Leaf &L, int x, int y, int level, int phase, int k, int q,
+                                          int d0, int d1, int d2, int dx, int dy, int pos) {
+    L.w0 = (uint32_t)x | ((uint32_t)y << 16);
+    L.w1 = (uint32_t)level | ((uint32_t)phase << 8) | ((uint32_t)k << 16) | ((uint32_t)q << 24);
+    L.w2 = ((uint32_t)d0 & 0xffu) | (((uint32_t)d1 & 0xffu) << 8) | (((uint32_t)d2 & 0xffu) << 16);
+    L.w3 = (uint32_t)dx | ((uint32_t)dy << 16);
+    L.pos = pos;
+}
+
+// Moments of the lane's part of a block of side B >= 8: the patch's 4 rows x
+// 8 pixels against the 4 x 8 decimated domain values at (c, rr) (c even).
+template <int NP>
+__device__ __forceinline__ void patch_moments(const uint32_t *d4e, int c, int rr, const uint2 *rw,
+                                              int &sd, int &sdd, int &sdr) {
+    unsigned a_dr = 0, pk = 0, ql = 0, qh = 0;
+    const uint32_t *base = d4e + rr * NP + (c >> 1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint2 lo = *reinterpret_cast<const uint2 *>(base + i * NP);
+        const uint2 hi = *reinterpret_cast<const uint2 *>(base + i * NP + 2);
+        a_dr = dp2a_lo(lo.x, rw[i].x, a_dr);
+        a_dr = dp2a_hi(lo.y, rw[i].x, a_dr);
+        a_dr = dp2a_lo(hi.x, rw[i].y, a_dr);
+        a_dr = dp2a_hi(hi.y, rw[i].y, a_dr);
+        pk += lo.x + lo.y + hi.x + hi.y;
+        acc_sq(lo.x, ql, qh);
+        acc_sq(lo.y, ql, qh);
+        acc_sq(hi.x, ql, qh);
+        acc_sq(hi.y, ql, qh);
+    }
+    sd = (int)((pk & 0xffffu) + (pk >> 16));
+    sdd = (int)(ql + (qh << 8));
+    sdr = (int)a_dr;
+}
+
+// Moments of one 4x4 block (one half of the patch): 4 rows x 4 pixels (word
+// `h` of each row) against 4 x 4 decimated values starting at column c of
+// either parity.
+template <int NP>
+__device__ __forceinline__ void half_moments(const uint32_t *d4e, const uint32_t *d4o, int c, int rr,
+                                             const uint2 *rw, int h, int &sd, int &sdd, int &sdr) {
+    unsigned a_dr = 0, pk = 0, ql = 0, qh = 0;
+    const uint32_t *base = (c & 1) ? d4o + rr * NP + ((c - 1) >> 1) : d4e + rr * NP + (c >> 1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t p0 = base[i * NP], p1 = base[i * NP + 1];
+        const uint32_t r = h ? rw[i].y : rw[i].x;
+        a_dr = dp2a_lo(p0, r, a_dr);
+        a_dr = dp2a_hi(p1, r, a_dr);
+        pk += p0 + p1;
+        acc_sq(p0, ql, qh);
+        acc_sq(p1, ql, qh);
+    }
+    sd = (int)((pk & 0xffffu) + (pk >> 16));
+    sdd = (int)(ql + (qh << 8));
+    sdr = (int)a_dr;
+}
+
+template <int BMAX>
+__global__ void __launch_bounds__(kWarps * 32)
+    mns_encode_kernel(const EncDesc *__restrict__ descs, int count, int total_strips,
+                      uint32_t *__restrict__ status, uint32_t *__restrict__ ticket) {
+    using G = Geom<BMAX>;
+    constexpr int PC = G::PC, NP = G::NP;
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *d4e = smem + warp * 2 * G::WORDS;
+    uint32_t *d4o = d4e + G::WORDS;
+    const int pr = lane / PC, pc = lane % PC;
+    const unsigned FULL = 0xffffffffu;
+
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = (int)atomicAdd(ticket, 1u);
+        g = __shfl_sync(FULL, g, 0);
+        if (g >= total_strips) break;
+        const int img = find_image(descs, count, g);
+        const EncDesc &D = descs[img];
+        const int W = D.W, H = D.H, tw = D.tw;
+        const int s = g - D.strip_base;
+        const int row = s / D.spr, sc = s % D.spr;
+        const int sy0 = row * BMAX, sx0 = sc * G::SW;
+        const int top0 = row * tw + sc * G::TOPS;
+        const int nvalid = min(G::TOPS, tw - sc * G::TOPS);
+        const int lane_top = (8 * pc) / BMAX;
+        const bool valid = lane_top < nvalid;
+        const int L = D.L, bmin = D.bmin, s_bits = D.s_bits;
+        const int ko1 = (1 << D.o_bits) - 1;
+        const uint32_t magic = (uint32_t)((0x100000000ULL + 2 * ko1 - 1) / (2 * ko1));
+        const float qscale = (float)ko1 / 255.f;
+        const bool ph2 = (D.mode == FIC_MNS) && D.phase2;
+
+        // ---- decimated domain window of the strip -> shared memory
+        const int rx0 = clampi(sx0 - BMAX / 2, 0, W - 2 * BMAX);
+        const int xl = sx0 + (nvalid - 1) * BMAX;
+        const int rx1 = clampi(xl - BMAX / 2, 0, W - 2 * BMAX) + 2 * BMAX;
+        const int ax0 = rx0 & ~15, ax1 = (rx1 + 15) & ~15;
+        const int ry0 = clampi(sy0 - BMAX / 2, 0, H - 2 * BMAX);
+        const int c_base = ax0 >> 1, r_base = ry0 >> 1;
+        const int upr = (ax1 - ax0) >> 4;  // 16-pixel units per decimated row
+        const int npairs = upr * 4;
+        __syncwarp();
+        for (int u = lane; u < BMAX * upr; u += 32) {
+            const int r = u / upr, cu = u - r * upr;
+            const uint8_t *p = D.img + (size_t)(ry0 + 2 * r) * W + ax0 + 16 * cu;
+            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
+            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(p + W));
+            uint4 o;
+            o.x = d4_pair(a.x, b.x);
+            o.y = d4_pair(a.y, b.y);
+            o.z = d4_pair(a.z, b.z);
+            o.w = d4_pair(a.w, b.w);
+            *reinterpret_cast<uint4 *>(d4e + r * NP + 4 * cu) = o;
+        }
+        __syncwarp();
+        for (int i = lane; i < BMAX * npairs; i += 32) {
+            const int r = i / npairs, c = i - r * npairs;
+            const uint32_t a = d4e[r * NP + c];
+            const uint32_t b = (c + 1 < npairs) ? d4e[r * NP + c + 1] : 0u;
+            d4o[r * NP + c] = __byte_perm(a, b, 0x5432);
+        }
+        __syncwarp();
+
+        // ---- the lane's range pixels (4 rows x 8)
+        uint2 rw[4];
+        int sr_h[2] = {0, 0}, srr_h[2] = {0, 0};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            rw[i] = valid ? __ldg(reinterpret_cast<const uint2 *>(D.img + (size_t)(sy0 + 4 * pr + i) * W +
+                                                                   sx0 + 8 * pc))
+                          : make_uint2(0u, 0u);
+            sr_h[0] += (int)__dp4a(rw[i].x, 0x01010101u, 0u);
+            sr_h[1] += (int)__dp4a(rw[i].y, 0x01010101u, 0u);
+            srr_h[0] += (int)__dp4a(rw[i].x, rw[i].x, 0u);
+            srr_h[1] += (int)__dp4a(rw[i].y, rw[i].y, 0u);
+        }
+
+        // ---- quadtree, level by level
+        Leaf leaf[2];
+        leaf[0].pos = -1;
+        leaf[1].pos = -1;
+        uint32_t splitbits = 0;
+        unsigned long long fits = 0;
+        const int cpt_side = BMAX / bmin;  // bmin cells per top side
+        const int cpt = cpt_side * cpt_side;
+        bool act = valid;
+        Fit cur;  // level j result (blocks of side >= 8)
+        Fit cur4[2];
+        int B = BMAX;
+        {
+            // level 1 (B = BMAX >= 8)
+            const int gx = B / 8, gy = B / 4;
+            const int bx = (8 * pc) / B, by = (4 * pr) / B;
+            const int xa = sx0 + bx * B, ya = sy0 + by * B;
+            const int dxa = centred_origin(xa, B, W), dya = centred_origin(ya, B, H);
+            const int u0 = 8 * pc - bx * B, v0 = 4 * pr - by * B;
+            int sd = 0, sdd = 0, sdr = 0;
+            if (valid) patch_moments<NP>(d4e, (dxa >> 1) + u0 - c_base, (dya >> 1) + v0 - r_base, rw, sd, sdd, sdr);
+            int sr = group_sum<PC>(sr_h[0] + sr_h[1], gx, gy);
+            int srr = group_sum<PC>(srr_h[0] + srr_h[1], gx, gy);
+            sd = group_sum<PC>(sd, gx, gy);
+            sdd = group_sum<PC>(sdd, gx, gy);
+            sdr = group_sum<PC>(sdr, gx, gy);
+            const int lg2n = 2 * (31 - __clz(B));
+            fit_phase1(sr, srr, sd, sdd, sdr, lg2n, s_bits, ko1, magic, qscale,
+                       D.t2q[0] << (2 * lg2n + 10), cur);
+        }
+        for (int j = 1; j <= L; ++j, B >>= 1) {
+            // blocks of level j: side B; the lane's block (B >= 8) or two halves (B == 4)
+            if (B >= 8) {
+                const int gx = B / 8, gy = B / 4;
+                const int bx = (8 * pc) / B, by = (4 * pr) / B;
+                const int xa = sx0 + bx * B, ya = sy0 + by * B;
+                const int u0 = 8 * pc - bx * B, v0 = 4 * pr - by * B;
+                const bool rep = act && u0 == 0 && v0 == 0;
+                if (rep) fits += 1;
+                const int tx = bx * B - lane_top * BMAX, ty = by * B;  // inside the top block
+                const uint32_t z = morton3(tx / B, ty / B);
+                const int pos = lane_top * cpt + (int)morton3(tx / bmin, ty / bmin);
+                const int dxa = centred_origin(xa, B, W), dya = centred_origin(ya, B, H);
+                if (j == L) {
+                    if (rep) make_leaf(leaf[0], xa, ya, j, 1, cur.k, cur.q, 0, 0, 0, dxa, dya, pos);
+                    break;
+                }
+                if (rep && cur.pass) make_leaf(leaf[0], xa, ya, j, 1, cur.k, cur.q, 0, 0, 0, dxa, dya, pos);
+                const bool need = act && !cur.pass;
+                if (!__any_sync(FULL, need)) break;
+                // ---- level j+1: moments and phase 1 of the children
+                const int Bc = B >> 1;
+                const int lg2c = 2 * (31 - __clz(Bc));
+                const long long thr_c = D.t2q[j] << (2 * lg2c + 10);     // children as level-(j+1) blocks
+                const long long thr_p2 = D.t2q[j - 1] << (2 * lg2c + 10); // sub-blocks coded at level j
+                Fit nxt;
+                if (Bc >= 8) {
+                    const int cgx = Bc / 8, cgy = Bc / 4;
+                    const int cbx = (8 * pc) / Bc, cby = (4 * pr) / Bc;
+                    const int cxa = sx0 + cbx * Bc, cya = sy0 + cby * Bc;
+                    const int cdx = centred_origin(cxa, Bc, W), cdy = centred_origin(cya, Bc, H);
+                    const int cu0 = 8 * pc - cbx * Bc, cv0 = 4 * pr - cby * Bc;
+                    int sd = 0, sdd = 0, sdr = 0;
+                    if (valid)
+                        patch_moments<NP>(d4e, (cdx >> 1) + cu0 - c_base, (cdy >> 1) + cv0 - r_base, rw, sd,
+                                          sdd, sdr);
+                    int sr = group_sum<PC>(sr_h[0] + sr_h[1], cgx, cgy);
+                    int srr = group_sum<PC>(srr_h[0] + srr_h[1], cgx, cgy);
+                    sd = group_sum<PC>(sd, cgx, cgy);
+                    sdd = group_sum<PC>(sdd, cgx, cgy);
+                    sdr = group_sum<PC>(sdr, cgx, cgy);
+                    fit_phase1(sr, srr, sd, sdd, sdr, lg2c, s_bits, ko1, magic, qscale, thr_c, nxt);
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int cxa = sx0 + 8 * pc + 4 * h, cya = sy0 + 4 * pr;
+                        const int cdx = centred_origin(cxa, 4, W), cdy = centred_origin(cya, 4, H);
+                        int sd = 0, sdd = 0, sdr = 0;
+                        if (valid)
+                            half_moments<NP>(d4e, d4o, (cdx >> 1) - c_base, (cdy >> 1) - r_base, rw, h, sd, sdd,
+                                             sdr);
+                        fit_phase1(sr_h[h], srr_h[h], sd, sdd, sdr, 4, s_bits, ko1, magic, qscale, thr_c,
+                                   cur4[h]);
+                    }
+                }
+                // ---- phase 2 of the level-j blocks that failed phase 1 (Sections 3.1-3.3)
+                bool p2 = false;
+                int d[4] = {0, 0, 0, 0};
+                int sbits = 0;
+                if (ph2) {
+                    if (rep && need) fits += 4;
+                    const int lg2n4 = lg2c;
+                    const int Oi = lum(cur.q, ko1, magic);
+                    // the four children's pixel sums
+                    int csr[4];
+                    if (Bc >= 8) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int cbx = 2 * bx + (k & 1), cby = 2 * by + (k >> 1);
+                            const int src = (cby * Bc / 4) * PC + (cbx * Bc / 8);
+                            csr[k] = __shfl_sync(FULL, nxt.sr, src & 31);
+                        }
+                    } else {
+                        // B == 8: the top patch holds TL, TR, the bottom patch BL, BR
+                        const int o0 = __shfl_xor_sync(FULL, cur4[0].sr, PC);
+                        const int o1 = __shfl_xor_sync(FULL, cur4[1].sr, PC);
+                        const bool top = (pr & 1) == 0;
+                        csr[0] = top ? cur4[0].sr : o0;
+                        csr[1] = top ? cur4[1].sr : o1;
+                        csr[2] = top ? o0 : cur4[0].sr;
+                        csr[3] = top ? o1 : cur4[1].sr;
+                    }
+                    const int dmax = (j == 1) ? 15 : 31;
+                    bool inrange = true;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        // round half up of (mean_k - O_i)
+                        d[k] = (2 * (csr[k] - (Oi << lg2n4)) + (1 << lg2n4)) >> (lg2n4 + 1);
+                        inrange = inrange && d[k] <= dmax && d[k] >= -dmax;
+                    }
+                    int O[4];
+                    O[0] = Oi + d[0];
+                    O[1] = Oi + d[1];
+                    O[2] = Oi + d[2];
+                    O[3] = 4 * Oi - (O[0] + O[1] + O[2]);  // eq. (1)
+                    const int c0 = phase2_code(j, 0), c1 = phase2_code(j, 1);
+                    bool ok_lane;
+                    if (Bc >= 8) {
+                        const int cbx = (8 * pc) / Bc, cby = (4 * pr) / Bc;
+                        const int kk = (cbx & 1) | ((cby & 1) << 1);
+                        int bit;
+                        ok_lane = fit_phase2_sub(nxt, lg2n4, O[kk], c0, c1, thr_p2, bit);
+                        const uint32_t bits = __ballot_sync(FULL, bit);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int cbx2 = 2 * bx + (k & 1), cby2 = 2 * by + (k >> 1);
+                            const int src = (cby2 * Bc / 4) * PC + (cbx2 * Bc / 8);
+                            sbits |= (int)((bits >> (src & 31)) & 1u) << k;
+                        }
+                    } else {
+                        const bool top = (pr & 1) == 0;
+                        int b0, b1;
+                        const bool ok0 = fit_phase2_sub(cur4[0], 4, O[top ? 0 : 2], c0, c1, thr_p2, b0);
+                        const bool ok1 = fit_phase2_sub(cur4[1], 4, O[top ? 1 : 3], c0, c1, thr_p2, b1);
+                        ok_lane = ok0 && ok1;
+                        const int my = b0 | (b1 << 1);
+                        const int other = __shfl_xor_sync(FULL, my, PC);
+                        sbits = top ? (my | (other << 2)) : (other | (my << 2));
+                    }
+                    const uint32_t okb = __ballot_sync(FULL, ok_lane);
+                    const uint32_t gm = group_mask<PC>(pc, pr, gx, gy);
+                    p2 = need && inrange && ((okb & gm) == gm);
+                }
+                if (rep && p2) make_leaf(leaf[0], xa, ya, j, 2, sbits, cur.q, d[0], d[1], d[2], dxa, dya, pos);
+                const bool split = need && !p2;
+                if (rep && split) splitbits |= 1u << (((1u << (2 * (j - 1))) - 1) / 3 + z);
+                act = split;
+                if (Bc >= 8) cur = nxt;
+            } else {
+                // B == 4: last level, forced acceptance (two leaves per lane)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!act) continue;
+                    fits += 1;
+                    const int xa = sx0 + 8 * pc + 4 * h, ya = sy0 + 4 * pr;
+                    const int tx = 8 * pc + 4 * h - lane_top * BMAX, ty = 4 * pr;
+                    const int pos = lane_top * cpt + (int)morton3(tx / bmin, ty / bmin);
+                    make_leaf(leaf[h], xa, ya, j, 1, cur4[h].k, cur4[h].q, 0, 0, 0, centred_origin(xa, 4, W),
+                              centred_origin(ya, 4, H), pos);
+                }
+                break;
+            }
+        }
+
+        // ---- canonical ranks, look-back, stores
+        unsigned long long mine = 0;
+        if (leaf[0].pos >= 0) mine |= 1ull << leaf[0].pos;
+        if (leaf[1].pos >= 0) mine |= 1ull << leaf[1].pos;
+        const uint32_t mlo = __reduce_or_sync(FULL, (uint32_t)mine);
+        const uint32_t mhi = __reduce_or_sync(FULL, (uint32_t)(mine >> 32));
+        const unsigned long long mask = ((unsigned long long)mhi << 32) | mlo;
+        const int cnt = __popcll(mask);
+        uint32_t prefix = 0;
+        int ok = 1;
+        if (lane == 0) {
+            uint32_t *st = status + g;
+            if (s == 0) {
+                st_volatile(st, kIncl | (uint32_t)cnt);
+            } else {
+                st_volatile(st, kAgg | (uint32_t)cnt);
+                int p = g - 1;
+                for (;;) {
+                    uint32_t v = 0;
+                    unsigned it = 0;
+                    while ((v = ld_volatile(status + p)) == 0u && ++it < kSpinLimit) __nanosleep(64);
+                    if (v == 0u) {
+                        ok = 0;
+                        break;
+                    }
+                    prefix += v & kValMask;
+                    if ((v & ~kValMask) == kIncl) break;
+                    --p;
+                }
+                if (ok) st_volatile(st, kIncl | (prefix + (uint32_t)cnt));
+                else raise_error(D.info, FIC_DEVERR_TIMEOUT);
+            }
+            fits = fits;  // lane 0's own count is folded in below
+        }
+        ok = __shfl_sync(FULL, ok, 0);
+        prefix = __shfl_sync(FULL, prefix, 0);
+        // fits: warp total
+        unsigned long long ftot = fits;
+        for (int m = 16; m >= 1; m >>= 1) ftot += __shfl_xor_sync(FULL, ftot, m);
+        if (lane == 0 && ftot) atomicAdd(reinterpret_cast<unsigned long long *>(D.info + FIC_INFO_FITS_LO), ftot);
+        if (!ok) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (leaf[h].pos < 0) continue;
+            const uint32_t idx = prefix + (uint32_t)__popcll(mask & ((1ull << leaf[h].pos) - 1ull));
+            if (idx < (uint32_t)D.capacity) {
+                *reinterpret_cast<uint4 *>(D.rec + idx) = make_uint4(leaf[h].w0, leaf[h].w1, leaf[h].w2, leaf[h].w3);
+            } else {
+                raise_error(D.info, FIC_DEVERR_CAPACITY);
+            }
+        }
+        // split masks: OR over the lanes of each top-level block
+        splitbits = group_or<PC>(splitbits, BMAX / 8, BMAX / 4);
+        if (valid && (8 * pc) % BMAX == 0 && pr == 0) {
+            D.split[top0 + lane_top] = splitbits;
+            D.tile_off[top0 + lane_top] =
+                prefix + (uint32_t)__popcll(mask & ((1ull << (lane_top * cpt)) - 1ull));
+        }
+        if (lane == 0 && s == D.nstrips - 1) {
+            D.tile_off[D.tw * D.th] = prefix + (uint32_t)cnt;
+            D.info[FIC_INFO_RECORDS] = prefix + (uint32_t)cnt;
+        }
+    }
+}
+
+// Zero the look-back state, the ticket and every stream's info block.
+__global__ void encode_init_kernel(const EncDesc *__restrict__ descs, int count, uint32_t *status,
+                                   int total_strips, uint32_t *ticket) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    for (int t = i; t < total_strips; t += stride) status[t] = 0u;
+    for (int t = i; t < count * FIC_INFO_WORDS; t += stride) descs[t / FIC_INFO_WORDS].info[t % FIC_INFO_WORDS] = 0u;
+    if (i == 0) *ticket = 0u;
+}
+
+size_t mns_smem_bytes(int bmax) {
+    int words = bmax == 32 ? Geom<32>::WORDS : (bmax == 16 ? Geom<16>::WORDS : Geom<8>::WORDS);
+    return (size_t)kWarps * 2 * words * sizeof(uint32_t);
+}
+
+int mns_strip_width(int bmax) { return 1024 / bmax; }
+
+template <int BMAX>
+static cudaError_t launch_t(const EncDesc *descs, int count, int total_strips, uint32_t *status,
+                            uint32_t *ticket, cudaStream_t st) {
+    static int grid_cache = 0;
+    const size_t smem = mns_smem_bytes(BMAX);
+    if (grid_cache == 0) {
+        cudaError_t e = cudaFuncSetAttribute(mns_encode_kernel<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mns_encode_kernel<BMAX>, kWarps * 32, smem);
+        grid_cache = sms * (per > 0 ? per : 1);
+    }
+    const int need = (total_strips + kWarps - 1) / kWarps;
+    const int grid = need < grid_cache ? need : grid_cache;
+    mns_encode_kernel<BMAX><<<grid, kWarps * 32, smem, st>>>(descs, count, total_strips, status, ticket);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int total_strips,
+                              uint32_t *status, uint32_t *ticket, cudaStream_t st) {
+    const int threads = 256;
+    int blocks = (total_strips + threads - 1) / threads;
+    int b2 = (count * FIC_INFO_WORDS + threads - 1) / threads;
+    if (b2 > blocks) blocks = b2;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 1024) blocks = 1024;
+    encode_init_kernel<<<blocks, threads, 0, st>>>(d_descs, count, status, total_strips, ticket);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    switch (bmax) {
+    case 32: return launch_t<32>(d_descs, count, total_strips, status, ticket, st);
+    case 16: return launch_t<16>(d_descs, count, total_strips, status, ticket, st);
+    case 8: return launch_t<8>(d_descs, count, total_strips, status, ticket, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fic

@@ -1,0 +1,117 @@
+// fic_internal.cuh -- device-side types and helpers shared by the kernels of
+// libfic.so (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fic.h"
+
+namespace fic {
+
+// Bounded spin: a wait that has not finished after this many polls gives up,
+// records FIC_DEVERR_TIMEOUT and lets the kernel return.
+constexpr unsigned kSpinLimit = 1u << 22;
+
+// One image of an encode launch.
+struct EncDesc {
+    const uint8_t *img;
+    fic_record *rec;
+    uint32_t *tile_off;
+    uint32_t *split;
+    uint32_t *info;
+    int64_t t2q[4];      // round(256 T_j^2) per level
+    int32_t W, H;
+    int32_t tw, th;      // top-level blocks per row / column
+    int32_t spr;         // strips per top-block row
+    int32_t strip_base;  // global index of this image's first strip
+    int32_t nstrips;
+    int32_t capacity;
+    int32_t mode, bmin, L, phase2;
+    int32_t s_bits, o_bits;
+    int32_t local_radius, local_step;
+};
+
+// One image of a decode launch.
+struct DecDesc {
+    const fic_record *rec;
+    const uint32_t *tile_off;
+    uint8_t *buf[2];     // ping-pong iterates; the last iteration writes buf[iters & 1]
+    int32_t W, H;
+    int32_t tw, th, spr, strip_base, nstrips;
+    int32_t mode, bmin, L, s_bits, o_bits;
+};
+
+// Fixed-point codebooks (Section 3.3): c = 128 s on 2^s_bits cell midpoints
+// of [-1, 1); luminance levels round(255 q / (2^o_bits - 1)).
+__host__ __device__ inline int contrast_code(int k, int s_bits) {
+    int K = 1 << s_bits;
+    return (2 * k - (K - 1)) * (128 / K);
+}
+
+// Phase-2 contrast sets of Section 3.2 in the c = round(128 s) fixed point:
+// level 1 {.2, .5}, level 2 {.4, .65}, level 3 {.5, .9}.
+__host__ __device__ inline int phase2_code(int level, int bit) {
+    // packed: level-1 (26, 64), level-2 (51, 83), level-3 (64, 115)
+    const int lo[3] = {26, 51, 64};
+    const int hi[3] = {64, 83, 115};
+    return bit ? hi[level - 1] : lo[level - 1];
+}
+
+__host__ __device__ inline int clampi(int v, int lo, int hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Domain with the same centre as the range, moved inside the image.
+__host__ __device__ inline int centred_origin(int x, int B, int W) {
+    return clampi(x - B / 2, 0, W - 2 * B);
+}
+
+__device__ __forceinline__ unsigned dp2a_lo(unsigned a, unsigned b, unsigned c) {
+    return __dp2a_lo(a, b, c);
+}
+__device__ __forceinline__ unsigned dp2a_hi(unsigned a, unsigned b, unsigned c) {
+    return __dp2a_hi(a, b, c);
+}
+
+// Two 2x2 sums from two 4-pixel words of adjacent rows: returns the packed
+// pair (p0+p1+q0+q1, p2+p3+q2+q3) as two 16-bit lanes.
+__device__ __forceinline__ unsigned d4_pair(unsigned a, unsigned b) {
+    unsigned lo = (a & 0x00FF00FFu) + (b & 0x00FF00FFu);
+    unsigned hi = ((a >> 8) & 0x00FF00FFu) + ((b >> 8) & 0x00FF00FFu);
+    return lo + hi;
+}
+
+// Accumulate sum and sum of squares of a packed pair of 10-bit values:
+// v^2 = v * lo8(v) + 256 * v * hi8(v), both halves by dp2a.
+__device__ __forceinline__ void acc_sq(unsigned p, unsigned &sq_lo, unsigned &sq_hi) {
+    unsigned w = __byte_perm(p, 0, 0x3120);  // (v0.lo, v1.lo, v0.hi, v1.hi)
+    sq_lo = dp2a_lo(p, w, sq_lo);
+    sq_hi = dp2a_hi(p, w, sq_hi);
+}
+
+// Record the first device error bit of a stream.
+__device__ __forceinline__ void raise_error(uint32_t *info, uint32_t bit) {
+    atomicOr(info + FIC_INFO_ERROR, bit);
+}
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
+    return *reinterpret_cast<const volatile uint32_t *>(p);
+}
+__device__ __forceinline__ void st_volatile(uint32_t *p, uint32_t v) {
+    *reinterpret_cast<volatile uint32_t *>(p) = v;
+}
+
+// Which image of a launch owns global strip `g` (descs sorted by strip_base).
+template <class D>
+__device__ __forceinline__ int find_image(const D *descs, int count, int g) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (descs[mid].strip_base <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace fic

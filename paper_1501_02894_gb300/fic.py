@@ -1,0 +1,305 @@
+"""Thin Python binding of libfic.so (ctypes): argument marshalling only.
+
+Every step of the coder runs in the library's CUDA kernels; PyTorch is used
+here only to allocate device memory and to name the CUDA stream.  If the
+library is missing, importing this module tries to build it with nvcc and
+raises if that is impossible -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+MODES = {"nosearch": 0, "mns": 1, "local": 2, "exhaustive": 3}
+
+RECORD_DTYPE = np.dtype([
+    ("x", "<u2"), ("y", "<u2"), ("level", "u1"), ("phase", "u1"), ("k", "u1"),
+    ("q", "u1"), ("d", "i1", (3,)), ("iso", "u1"), ("dx", "<u2"), ("dy", "<u2"),
+])
+assert RECORD_DTYPE.itemsize == 16
+
+INFO_WORDS = 16
+ERRORS = {
+    0: "ok", -1: "unsupported image size", -2: "invalid parameter", -3: "buffer or workspace too small",
+    -4: "record buffer too small", -5: "CUDA error", -6: "device wait timed out",
+    -7: "request exceeds the memory budget", -8: "busy", -9: "cancelled",
+}
+
+
+class FicError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {ERRORS.get(code, 'error')} ({code})")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int32), ("bmax", ctypes.c_int32), ("bmin", ctypes.c_int32),
+        ("thr_rms", ctypes.c_double * 4), ("s_bits", ctypes.c_int32), ("o_bits", ctypes.c_int32),
+        ("phase2", ctypes.c_int32), ("local_radius", ctypes.c_int32), ("local_step", ctypes.c_int32),
+        ("dom_step", ctypes.c_int32), ("isometries", ctypes.c_int32),
+    ]
+
+
+class StreamC(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("params", Params),
+        ("ntop", ctypes.c_int32), ("capacity", ctypes.c_int32),
+        ("records", ctypes.c_void_p), ("tile_offsets", ctypes.c_void_p),
+        ("split", ctypes.c_void_p), ("info", ctypes.c_void_p),
+    ]
+
+
+def params(mode="mns", bmax=32, bmin=4, thr=8.0, s_bits=5, o_bits=7, phase2=True,
+           local_radius=16, local_step=4, dom_step=4, isometries=8) -> Params:
+    p = Params()
+    p.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+    p.bmax, p.bmin = int(bmax), int(bmin)
+    thr = list(thr) if isinstance(thr, (list, tuple)) else [float(thr)] * 4
+    thr = (thr + [thr[-1]] * 4)[:4]
+    for i in range(4):
+        p.thr_rms[i] = float(thr[i])
+    p.s_bits, p.o_bits = int(s_bits), int(o_bits)
+    p.phase2 = 1 if phase2 else 0
+    p.local_radius, p.local_step = int(local_radius), int(local_step)
+    p.dom_step, p.isometries = int(dom_step), int(isometries)
+    return p
+
+
+_lib = None
+
+
+def lib():
+    """Load the in-tree libfic.so (building it with nvcc if it is missing)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path) or _build._stale():
+            path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, P = ctypes.c_void_p, ctypes.POINTER
+        i32p = P(ctypes.c_int)
+        L.fic_version.restype = ctypes.c_int
+        L.fic_validate.argtypes = [ctypes.c_int, ctypes.c_int, P(Params)]
+        L.fic_stream_sizes.argtypes = [ctypes.c_int, ctypes.c_int, P(Params), P(ctypes.c_int32), P(ctypes.c_int32)]
+        L.fic_encode_workspace_bytes.argtypes = [ctypes.c_int, i32p, i32p, P(Params)]
+        L.fic_encode_workspace_bytes.restype = ctypes.c_size_t
+        L.fic_encode.argtypes = [vp, ctypes.c_int, ctypes.c_int, P(Params), P(StreamC), vp, ctypes.c_size_t, vp]
+        L.fic_encode_batch.argtypes = [P(vp), i32p, i32p, ctypes.c_int, P(Params), P(StreamC), vp,
+                                       ctypes.c_size_t, vp]
+        L.fic_decode_workspace_bytes.argtypes = [ctypes.c_int, i32p, i32p]
+        L.fic_decode_workspace_bytes.restype = ctypes.c_size_t
+        L.fic_decode.argtypes = [P(StreamC), ctypes.c_int, vp, vp, ctypes.c_size_t, vp]
+        L.fic_decode_batch.argtypes = [P(StreamC), ctypes.c_int, ctypes.c_int, P(vp), vp, ctypes.c_size_t, vp]
+        L.fic_stream_info.argtypes = [P(StreamC), P(ctypes.c_int64), P(ctypes.c_int64), vp]
+        L.fic_encode_plan_create.argtypes = [P(vp), i32p, i32p, ctypes.c_int, P(Params), P(StreamC), vp,
+                                             ctypes.c_size_t, vp, P(vp)]
+        L.fic_encode_plan_run.argtypes = [vp, vp]
+        L.fic_decode_plan_create.argtypes = [P(StreamC), ctypes.c_int, P(vp), vp, ctypes.c_size_t, vp, P(vp)]
+        L.fic_decode_plan_run.argtypes = [vp, ctypes.c_int, vp]
+        L.fic_plan_destroy.argtypes = [vp]
+        L.fic_plan_destroy.restype = None
+        L.fic_strerror.argtypes = [ctypes.c_int]
+        L.fic_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise FicError(rc, where)
+
+
+def _stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Stream:
+    """A transform stream whose device buffers are owned by torch tensors."""
+
+    def __init__(self, width: int, height: int, p: Params, device="cuda"):
+        ntop, cap = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().fic_stream_sizes(width, height, ctypes.byref(p), ctypes.byref(ntop), ctypes.byref(cap)),
+               "fic_stream_sizes")
+        self.width, self.height, self.params = int(width), int(height), p
+        self.ntop, self.capacity = ntop.value, cap.value
+        self.records = torch.empty(self.capacity * 16, dtype=torch.uint8, device=device)
+        self.tile_offsets = torch.empty(self.ntop + 1, dtype=torch.int32, device=device)
+        self.split = torch.empty(self.ntop, dtype=torch.int32, device=device)
+        self.info = torch.zeros(INFO_WORDS, dtype=torch.int32, device=device)
+        self.c = StreamC()
+        self.c.width, self.c.height, self.c.params = self.width, self.height, p
+        self.c.ntop, self.c.capacity = self.ntop, self.capacity
+        self.c.records = self.records.data_ptr()
+        self.c.tile_offsets = self.tile_offsets.data_ptr()
+        self.c.split = self.split.data_ptr()
+        self.c.info = self.info.data_ptr()
+
+    def info_host(self, stream=None):
+        """(record count, fits); raises FicError on a device error."""
+        n, f = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().fic_stream_info(ctypes.byref(self.c), ctypes.byref(n), ctypes.byref(f),
+                                     _stream_handle(stream)), "fic_stream_info")
+        return int(n.value), int(f.value)
+
+    def to_host(self, stream=None):
+        n, fits = self.info_host(stream)
+        rec = self.records[: n * 16].cpu().numpy().view(RECORD_DTYPE).copy()
+        return {
+            "records": rec,
+            "split": self.split.cpu().numpy().view(np.uint32).copy(),
+            "tile_offsets": self.tile_offsets.cpu().numpy().view(np.uint32).copy(),
+            "fits": fits,
+        }
+
+
+def encode_workspace(widths, heights, plist, device="cuda") -> torch.Tensor:
+    n = len(widths)
+    W = (ctypes.c_int * n)(*widths)
+    H = (ctypes.c_int * n)(*heights)
+    P = (Params * n)(*plist)
+    b = lib().fic_encode_workspace_bytes(n, W, H, P)
+    if b == 0:
+        raise FicError(-2, "fic_encode_workspace_bytes")
+    return torch.empty(int(b), dtype=torch.uint8, device=device)
+
+
+def decode_workspace(widths, heights, device="cuda") -> torch.Tensor:
+    n = len(widths)
+    W = (ctypes.c_int * n)(*widths)
+    H = (ctypes.c_int * n)(*heights)
+    b = lib().fic_decode_workspace_bytes(n, W, H)
+    if b == 0:
+        raise FicError(-2, "fic_decode_workspace_bytes")
+    return torch.empty(int(b), dtype=torch.uint8, device=device)
+
+
+def _as_image(img: torch.Tensor) -> torch.Tensor:
+    if not isinstance(img, torch.Tensor) or img.dtype != torch.uint8 or img.dim() != 2 or not img.is_cuda:
+        raise TypeError("image must be a 2-D uint8 CUDA tensor")
+    return img.contiguous()
+
+
+def fic_encode(img: torch.Tensor, p: Params, out: Stream | None = None, workspace: torch.Tensor | None = None,
+               stream=None) -> Stream:
+    img = _as_image(img)
+    H, W = img.shape
+    out = out or Stream(W, H, p, img.device)
+    ws = workspace if workspace is not None else encode_workspace([W], [H], [p], img.device)
+    _check(lib().fic_encode(_ptr(img), W, H, ctypes.byref(p), ctypes.byref(out.c), _ptr(ws), ws.numel(),
+                            _stream_handle(stream)), "fic_encode")
+    out._keep = (img, ws)
+    return out
+
+
+def fic_encode_batch(imgs, plist, outs=None, workspace=None, stream=None):
+    imgs = [_as_image(t) for t in imgs]
+    n = len(imgs)
+    if isinstance(plist, Params):
+        plist = [plist] * n
+    Ws = [int(t.shape[1]) for t in imgs]
+    Hs = [int(t.shape[0]) for t in imgs]
+    outs = outs or [Stream(Ws[i], Hs[i], plist[i], imgs[i].device) for i in range(n)]
+    ws = workspace if workspace is not None else encode_workspace(Ws, Hs, plist, imgs[0].device)
+    ptrs = (ctypes.c_void_p * n)(*[t.data_ptr() for t in imgs])
+    Pa = (Params * n)(*plist)
+    Sa = (StreamC * n)(*[o.c for o in outs])
+    _check(lib().fic_encode_batch(ptrs, (ctypes.c_int * n)(*Ws), (ctypes.c_int * n)(*Hs), n, Pa, Sa,
+                                  _ptr(ws), ws.numel(), _stream_handle(stream)), "fic_encode_batch")
+    for i, o in enumerate(outs):
+        o.c = Sa[i]
+        o._keep = (imgs[i], ws)
+    return outs
+
+
+def fic_decode(st: Stream, iters: int, out: torch.Tensor | None = None, workspace=None, stream=None):
+    out = out if out is not None else torch.empty((st.height, st.width), dtype=torch.uint8,
+                                                  device=st.records.device)
+    ws = workspace if workspace is not None else decode_workspace([st.width], [st.height], out.device)
+    _check(lib().fic_decode(ctypes.byref(st.c), int(iters), _ptr(out), _ptr(ws), ws.numel(),
+                            _stream_handle(stream)), "fic_decode")
+    return out
+
+
+def fic_decode_batch(sts, iters: int, outs=None, workspace=None, stream=None):
+    n = len(sts)
+    dev = sts[0].records.device
+    outs = outs or [torch.empty((s.height, s.width), dtype=torch.uint8, device=dev) for s in sts]
+    ws = workspace if workspace is not None else decode_workspace([s.width for s in sts],
+                                                                  [s.height for s in sts], dev)
+    Sa = (StreamC * n)(*[s.c for s in sts])
+    ptrs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    _check(lib().fic_decode_batch(Sa, n, int(iters), ptrs, _ptr(ws), ws.numel(), _stream_handle(stream)),
+           "fic_decode_batch")
+    return outs
+
+
+class EncodePlan:
+    """Prepared batch encode: `run()` only enqueues kernels (graph-capturable)."""
+
+    def __init__(self, imgs, plist, outs=None, workspace=None, stream=None):
+        self.imgs = [_as_image(t) for t in imgs]
+        n = len(self.imgs)
+        if isinstance(plist, Params):
+            plist = [plist] * n
+        Ws = [int(t.shape[1]) for t in self.imgs]
+        Hs = [int(t.shape[0]) for t in self.imgs]
+        dev = self.imgs[0].device
+        self.outs = outs or [Stream(Ws[i], Hs[i], plist[i], dev) for i in range(n)]
+        self.ws = workspace if workspace is not None else encode_workspace(Ws, Hs, plist, dev)
+        ptrs = (ctypes.c_void_p * n)(*[t.data_ptr() for t in self.imgs])
+        Sa = (StreamC * n)(*[o.c for o in self.outs])
+        self.handle = ctypes.c_void_p()
+        _check(lib().fic_encode_plan_create(ptrs, (ctypes.c_int * n)(*Ws), (ctypes.c_int * n)(*Hs), n,
+                                            (Params * n)(*plist), Sa, _ptr(self.ws), self.ws.numel(),
+                                            _stream_handle(stream), ctypes.byref(self.handle)),
+               "fic_encode_plan_create")
+        for i, o in enumerate(self.outs):
+            o.c = Sa[i]
+
+    def run(self, stream=None):
+        _check(lib().fic_encode_plan_run(self.handle, _stream_handle(stream)), "fic_encode_plan_run")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.fic_plan_destroy(h)
+            self.handle = None
+
+
+class DecodePlan:
+    def __init__(self, sts, outs=None, workspace=None, stream=None):
+        n = len(sts)
+        dev = sts[0].records.device
+        self.sts = sts
+        self.outs = outs or [torch.empty((s.height, s.width), dtype=torch.uint8, device=dev) for s in sts]
+        self.ws = workspace if workspace is not None else decode_workspace([s.width for s in sts],
+                                                                           [s.height for s in sts], dev)
+        Sa = (StreamC * n)(*[s.c for s in sts])
+        ptrs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outs])
+        self.handle = ctypes.c_void_p()
+        _check(lib().fic_decode_plan_create(Sa, n, ptrs, _ptr(self.ws), self.ws.numel(), _stream_handle(stream),
+                                            ctypes.byref(self.handle)), "fic_decode_plan_create")
+
+    def run(self, iters: int, stream=None):
+        _check(lib().fic_decode_plan_run(self.handle, int(iters), _stream_handle(stream)), "fic_decode_plan_run")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.fic_plan_destroy(h)
+            self.handle = None
+
+
+def validate(width: int, height: int, p: Params) -> int:
+    return int(lib().fic_validate(int(width), int(height), ctypes.byref(p)))
