@@ -228,12 +228,14 @@ __global__ void __launch_bounds__(kDecWarps * 32)
                 part[h] += (int)((s2 & 0xffffu) + (s2 >> 16));
             }
         }
-        // ---- Sd4 per transform: halves of one lane first (side >= 8), then lane groups
+        // ---- Sd4 per transform: halves of one lane first (side >= 8), then the
+        // lane group of the transform; every lane runs the same shuffles
         int sd4[2];
-        if (t_lg[0] >= 3) {
-            int v = part[0] + part[1];
+        {
+            const bool big = t_lg[0] >= 3;  // a transform of side >= 8 covers both halves
             const int B = 1 << t_lg[0];
-            const int gx = B / 8, gy = B / 4;
+            const int gx = big ? B / 8 : 1, gy = big ? B / 4 : 1;
+            int v = part[0] + part[1];
 #pragma unroll
             for (int m = 1; m < 4; m <<= 1) {
                 const int o = __shfl_xor_sync(FULL, v, m);
@@ -244,15 +246,8 @@ __global__ void __launch_bounds__(kDecWarps * 32)
                 const int o = __shfl_xor_sync(FULL, v, (m * PC) & 31);
                 if (m < gy && m * PC < 32) v += o;
             }
-            sd4[0] = sd4[1] = v;
-        } else {
-            // 4x4 transforms stay inside the lane; still take part in the shuffles
-#pragma unroll
-            for (int m = 1; m < 4; m <<= 1) (void)__shfl_xor_sync(FULL, 0, m);
-#pragma unroll
-            for (int m = 1; m < 8; m <<= 1) (void)__shfl_xor_sync(FULL, 0, (m * PC) & 31);
-            sd4[0] = part[0];
-            sd4[1] = part[1];
+            sd4[0] = big ? v : part[0];
+            sd4[1] = big ? v : part[1];
         }
         if (first) {
             sd4[0] = 512 << (2 * t_lg[0]);
@@ -268,7 +263,7 @@ __global__ void __launch_bounds__(kDecWarps * 32)
                 for (int h = 0; h < 2; ++h) {
                     const int lg2n = 2 * t_lg[h];
                     const int n = 1 << lg2n;
-                    const int base = (t_O[h] << (9 + lg2n)) + (n << 8) - t_c[h] * sd4[h];
+                    const int base = t_O[h] * (1 << (9 + lg2n)) + (n << 8) - t_c[h] * sd4[h];
                     uint32_t w = 0;
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {

@@ -182,8 +182,9 @@ __device__ __forceinline__ void patch_moments(const uint32_t *d4e, int c, int rr
     const uint32_t *base = d4e + rr * NP + (c >> 1);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const uint2 lo = *reinterpret_cast<const uint2 *>(base + i * NP);
-        const uint2 hi = *reinterpret_cast<const uint2 *>(base + i * NP + 2);
+        // 32-bit loads: for 8x8 blocks the window starts at an odd word
+        const uint2 lo = make_uint2(base[i * NP], base[i * NP + 1]);
+        const uint2 hi = make_uint2(base[i * NP + 2], base[i * NP + 3]);
         a_dr = dp2a_lo(lo.x, rw[i].x, a_dr);
         a_dr = dp2a_hi(lo.y, rw[i].x, a_dr);
         a_dr = dp2a_lo(hi.x, rw[i].y, a_dr);
@@ -507,7 +508,6 @@ __global__ void __launch_bounds__(kWarps * 32)
                 if (ok) st_volatile(st, kIncl | (prefix + (uint32_t)cnt));
                 else raise_error(D.info, FIC_DEVERR_TIMEOUT);
             }
-            fits = fits;  // lane 0's own count is folded in below
         }
         ok = __shfl_sync(FULL, ok, 0);
         prefix = __shfl_sync(FULL, prefix, 0);
