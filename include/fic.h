@@ -209,6 +209,30 @@ FIC_API int fic_decode_plan_run(const fic_plan *plan, int iters, void *stream);
 
 FIC_API void fic_plan_destroy(fic_plan *plan);
 
+/* ---- Allocation-free encode ----
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory -- code inside a host application that owns
+ * the whole device heap and offers no allocator, or code on a latency-
+ * critical path where a device allocation (which may synchronise the
+ * device) is not allowed.  It encodes one image exactly like fic_encode,
+ * but keeps the encoder's scratch (image descriptor, look-back status of the
+ * stream packer, ticket) in a static device array of the library instead of
+ * a caller workspace; the caller still passes the image and the stream's
+ * buffers.  It calls no cudaMalloc/cudaFree.
+ *   - Limit: at most FIC_NOALLOC_MAX_STRIPS strips of 1024 pixels, i.e. 64 Mi
+ *     pixels (e.g. 8192 x 8192); larger images return FIC_EBADSIZE.
+ *   - Every GPU that loads the library holds the array (about 256 KiB) until
+ *     the process exits.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, once per device, with that device current); make
+ *     that first call before any stream capture.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (e.g. on two streams without ordering) race and corrupt each other's
+ *     streams.  Each call clears the parts that must start at zero.  */
+#define FIC_NOALLOC_MAX_STRIPS 65536
+FIC_API int fic_encode_noalloc(const uint8_t *d_img, int width, int height, const fic_params *p,
+                               fic_stream *out, void *stream);
+
 /* Human-readable name of a return code. */
 FIC_API const char *fic_strerror(int code);
 

@@ -16,6 +16,7 @@ from .fic import (  # noqa: F401
     fic_decode_batch,
     fic_encode,
     fic_encode_batch,
+    fic_encode_noalloc,
     lib,
     params,
     validate,

@@ -598,3 +598,111 @@ cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int t
 }
 
 }  // namespace fic
+
+// ---------------------------------------------------------------------------
+// Allocation-free encode entry point.
+//
+// Some callers cannot allocate device memory at all: code embedded in a host
+// application that owns the whole device heap and hands out no allocator,
+// or code on a latency-critical path where a device allocation (which can
+// synchronise the device) is not allowed.  For them fic_encode_noalloc keeps
+// the encoder's scratch -- the image descriptor, the look-back status words
+// of the stream packer and the ticket counter -- in this file-scope device
+// array instead of a caller workspace.  Every GPU that loads the library
+// holds the array (about 256 KiB) until the process exits.
+#include <mutex>
+
+namespace {
+
+struct NoAllocScratch {
+    fic::EncDesc desc;
+    uint32_t ticket;
+    uint32_t pad[63];
+    uint32_t status[FIC_NOALLOC_MAX_STRIPS];
+};
+
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+NoAllocScratch *g_noalloc_addr[kMaxDevices] = {};
+
+// The array's name is only a host-side stand-in: the device address must be
+// asked for, once per device, with that device current.
+int noalloc_scratch_for_current_device(NoAllocScratch **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FIC_ECUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FIC_ECUDA;
+        g_noalloc_addr[dev] = static_cast<NoAllocScratch *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return FIC_OK;
+}
+
+}  // namespace
+
+extern "C" int fic_encode_noalloc(const uint8_t *d_img, int width, int height, const fic_params *p,
+                                  fic_stream *out, void *stream) {
+    using namespace fic;
+    int rc = fic_validate(width, height, p);
+    if (rc) return rc;
+    if (!d_img || (reinterpret_cast<uintptr_t>(d_img) & 15) || !out) return FIC_EBADPARAM;
+    if (!out->records || !out->tile_offsets || !out->split || !out->info || out->capacity <= 0)
+        return FIC_EBADPARAM;
+    if ((reinterpret_cast<uintptr_t>(out->records) & 15) || (reinterpret_cast<uintptr_t>(out->info) & 7))
+        return FIC_EBADPARAM;
+    const int bmax = p->bmax;
+    const int tops = mns_strip_width(bmax) / bmax;
+    const int tw = width / bmax, th = height / bmax;
+    const int spr = (tw + tops - 1) / tops;
+    const long long nstrips = (long long)spr * th;
+    if (nstrips > FIC_NOALLOC_MAX_STRIPS) return FIC_EBADSIZE;  // larger than the static scratch
+    NoAllocScratch *scr = nullptr;
+    rc = noalloc_scratch_for_current_device(&scr);
+    if (rc) return rc;
+
+    int L = 1;
+    for (int b = p->bmax; b > p->bmin; b >>= 1) ++L;
+    EncDesc d;
+    memset(&d, 0, sizeof(d));
+    d.img = d_img;
+    d.rec = out->records;
+    d.tile_off = out->tile_offsets;
+    d.split = out->split;
+    d.info = out->info;
+    for (int j = 0; j < 4; ++j) {
+        const double t = p->thr_rms[j < L ? j : L - 1];
+        d.t2q[j] = (int64_t)(t * t * 256.0 + 0.5);
+    }
+    d.W = width;
+    d.H = height;
+    d.tw = tw;
+    d.th = th;
+    d.spr = spr;
+    d.strip_base = 0;
+    d.nstrips = (int)nstrips;
+    d.capacity = out->capacity;
+    d.mode = p->mode;
+    d.bmin = p->bmin;
+    d.L = L;
+    d.phase2 = p->phase2 ? 1 : 0;
+    d.s_bits = p->s_bits;
+    d.o_bits = p->o_bits;
+    d.local_radius = p->local_radius;
+    d.local_step = p->local_step;
+    out->width = width;
+    out->height = height;
+    out->params = *p;
+    out->ntop = tw * th;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // The descriptor is staged from host memory; the status words, the ticket
+    // and the stream's info block are cleared by the init kernel of the launch.
+    if (cudaMemcpyAsync(&scr->desc, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess) return FIC_ECUDA;
+    return launch_mns_encode(bmax, &scr->desc, 1, (int)nstrips, scr->status, &scr->ticket, st) == cudaSuccess
+               ? FIC_OK
+               : FIC_ECUDA;
+}

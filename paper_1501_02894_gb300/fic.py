@@ -104,6 +104,7 @@ def lib():
         L.fic_decode_plan_run.argtypes = [vp, ctypes.c_int, vp]
         L.fic_plan_destroy.argtypes = [vp]
         L.fic_plan_destroy.restype = None
+        L.fic_encode_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, P(Params), P(StreamC), vp]
         L.fic_strerror.argtypes = [ctypes.c_int]
         L.fic_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -199,6 +200,20 @@ def fic_encode(img: torch.Tensor, p: Params, out: Stream | None = None, workspac
     _check(lib().fic_encode(_ptr(img), W, H, ctypes.byref(p), ctypes.byref(out.c), _ptr(ws), ws.numel(),
                             _stream_handle(stream)), "fic_encode")
     out._keep = (img, ws)
+    return out
+
+
+def fic_encode_noalloc(img: torch.Tensor, p: Params, out: Stream | None = None, stream=None) -> Stream:
+    """Encode one image without any workspace: for callers that cannot
+    allocate device memory, the library keeps the encoder's scratch in a
+    static device array (images up to 64 Mi pixels).  Calls whose work
+    overlaps on the GPU must not be issued (they share that array)."""
+    img = _as_image(img)
+    H, W = img.shape
+    out = out or Stream(W, H, p, img.device)
+    _check(lib().fic_encode_noalloc(_ptr(img), W, H, ctypes.byref(p), ctypes.byref(out.c), _stream_handle(stream)),
+           "fic_encode_noalloc")
+    out._keep = (img,)
     return out
 
 
