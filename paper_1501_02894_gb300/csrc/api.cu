@@ -12,8 +12,9 @@
 namespace fic {
 cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int total_strips, uint32_t *status,
                               uint32_t *ticket, cudaStream_t st);
-cudaError_t launch_decode_iter(int bmax, const DecDesc *d_descs, int count, int total_strips, int src_sel,
-                               int first, cudaStream_t st);
+cudaError_t launch_decode(int bmax, const DecDesc *d_descs, int count, int total_strips, void *tables, int iters,
+                          cudaStream_t st);
+size_t decode_table_bytes_per_strip();
 int mns_strip_width(int bmax);
 }  // namespace fic
 
@@ -80,6 +81,7 @@ struct fic_plan {
     uint32_t *status;
     uint32_t *ticket;
     std::vector<DecDesc> hdec;  // decode: host copy (buffers per image)
+    void *dec_tables;           // decode: per-strip transform tables
     std::vector<uint8_t *> outs;
     std::vector<size_t> out_bytes;
 };
@@ -232,11 +234,19 @@ int fic_encode(const uint8_t *d_img, int width, int height, const fic_params *p,
 size_t fic_decode_workspace_bytes(int count, const int *widths, const int *heights) {
     if (count <= 0 || !widths || !heights) return 0;
     size_t b = align_up(sizeof(DecDesc) * (size_t)count);
+    size_t strips = 0;
     for (int i = 0; i < count; ++i) {
         if (widths[i] <= 0 || heights[i] <= 0) return 0;
         b += align_up((size_t)widths[i] * (size_t)heights[i]);
+        // strip count for the bmax that needs the most (the plan knows bmax)
+        size_t most = 0;
+        for (int bm = 8; bm <= 32; bm *= 2) {
+            const size_t n = (size_t)strips_per_row(widths[i], bm) * (size_t)(heights[i] / bm);
+            if (n > most) most = n;
+        }
+        strips += most;
     }
-    return b;
+    return b + align_up(strips * decode_table_bytes_per_strip());
 }
 
 int fic_decode_plan_create(const fic_stream *sts, int count, uint8_t *const *d_outs, void *d_workspace,
@@ -296,6 +306,7 @@ int fic_decode_plan_create(const fic_stream *sts, int count, uint8_t *const *d_o
     pl->count = count;
     pl->bmax = bmax;
     pl->total_strips = strips;
+    pl->dec_tables = scratch;  // after the per-image iterate buffers
     pl->ws = d_workspace;
     pl->ws_bytes = ws_bytes;
     pl->d_dec = reinterpret_cast<DecDesc *>(w);
@@ -320,12 +331,7 @@ int fic_decode_plan_run(const fic_plan *pl, int iters, void *stream) {
         }
         return FIC_OK;
     }
-    for (int it = 0; it < iters; ++it) {
-        const int src_sel = (iters - it) & 1;  // the last iteration writes buf[0] (the output)
-        cudaError_t e = launch_decode_iter(pl->bmax, pl->d_dec, pl->count, pl->total_strips, src_sel, it == 0, st);
-        if (e != cudaSuccess) return FIC_ECUDA;
-    }
-    return FIC_OK;
+    return cuda_rc(launch_decode(pl->bmax, pl->d_dec, pl->count, pl->total_strips, pl->dec_tables, iters, st));
 }
 
 int fic_decode_batch(const fic_stream *sts, int count, int iters, uint8_t *const *d_outs, void *d_workspace,

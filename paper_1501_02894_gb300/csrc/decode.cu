@@ -10,13 +10,18 @@
 // of the domain.  512 n is a power of two, so the division is a shift.
 //
 // GPU design: the same strip / patch geometry as the encoder (one warp per
-// 1024-pixel strip, lane = 8x4 patch).  Per launch (= one iteration) a warp
-// stages its strip's records and the decimated window of the previous
-// iterate in shared memory, finds the transform covering each 4x4 half-patch
-// by binary search over the canonical keys, reduces Sd4 over the lanes of
-// each transform with xor shuffles and writes 8 pixels per row with one
-// 8-byte store.  Domains that do not lie in the staged window (local and
-// exhaustive search, isometries) are read from global memory instead.
+// 1024-pixel strip, lane = 8x4 patch, two 4x4 half-patches per lane).
+//   * decode_setup_kernel (once per decode): for every half-patch, the
+//     transform that covers it (binary search over the strip's canonical
+//     record keys) packed into one word: window column/row of its domain
+//     values, block side, contrast byte, luminance; plus a per-strip word.
+//   * decode_iter_kernel (once per iteration): stage the decimated window of
+//     the previous iterate in shared memory (packed 2x2 sums), read 16 domain
+//     values per half-patch, reduce Sd4 per transform with xor shuffles, then
+//     per pixel one dp2a (select + multiply + offset), one shift and half of
+//     a saturating pack; 8 pixels per row with one 8-byte store.
+// Domains that are not centred (local / exhaustive search, isometries) are
+// read from global memory instead of the staged window.
 #include "fic_internal.cuh"
 
 namespace fic {
@@ -29,7 +34,7 @@ struct DGeom {
     static constexpr int TOPS = SW / BMAX;
     static constexpr int NP = BMAX == 32 ? 16 : (BMAX == 16 ? 24 : 40);
     static constexpr int WORDS = BMAX * NP;
-    static constexpr int PER_WARP = 2 * WORDS + 64 * 4 + 16;  // d4e, d4o, 64 records, 64 keys
+    static constexpr int UPR = BMAX == 32 ? 4 : (BMAX == 16 ? 8 : 16);
 };
 
 constexpr int kDecWarps = 8;
@@ -59,28 +64,63 @@ __device__ __forceinline__ void iso_src(int iso, int B, int u, int v, int &su, i
     }
 }
 
+// Clamp two signed values to [0, 255] and pack them, with the upper half
+// taken from `hi`: result bytes (b, a, hi.byte0, hi.byte1).
+__device__ __forceinline__ uint32_t pack_sat_u8(int a, int b, uint32_t hi) {
+    uint32_t d;
+    asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(hi));
+    return d;
+}
+
+// Four output pixels of one row: p = (c * d4 + K) >> 9, clamped, packed.
+// dp2a with the contrast in one byte of the second operand picks one 16-bit
+// d4 of the pair and multiplies-adds it in one instruction.
+__device__ __forceinline__ uint32_t row_pixels(uint32_t p01, uint32_t p23, int cb0, int cb1, int K) {
+    const int m0 = __dp2a_lo((int)p01, cb0, K) >> 9;
+    const int m1 = __dp2a_lo((int)p01, cb1, K) >> 9;
+    const int m2 = __dp2a_lo((int)p23, cb0, K) >> 9;
+    const int m3 = __dp2a_lo((int)p23, cb1, K) >> 9;
+    return pack_sat_u8(m1, m0, pack_sat_u8(m3, m2, 0u));
+}
+
+// Per-strip word of the decode tables.
+struct StripInfo {
+    const uint8_t *buf[2];
+    int32_t W;
+    uint32_t sxy;    // sx0 | sy0 << 16
+    uint32_t axy;    // ax0 | ry0 << 16   (window origin, pixels)
+    uint32_t misc;   // upr | nvalid << 8 | centred << 16
+};
+
+// Per-half-patch words: fast word (c | rr << 8 | lg << 16 | cbyte << 24, O)
+// and, for domains outside the window, (dx | dy << 16, u0 | v0 << 8 | iso << 16).
+__device__ __forceinline__ uint32_t fast_word(int c, int rr, int lg, int cc) {
+    return (uint32_t)c | ((uint32_t)rr << 8) | ((uint32_t)lg << 16) | ((uint32_t)(cc & 0xff) << 24);
+}
+
 template <int BMAX>
 __global__ void __launch_bounds__(kDecWarps * 32)
-    decode_iter_kernel(const DecDesc *__restrict__ descs, int count, int total_strips, int src_sel,
-                       int first) {
+    decode_setup_kernel(const DecDesc *__restrict__ descs, int count, int total_strips, StripInfo *sinfo,
+                        uint4 *tfw, uint4 *tgw) {
     using G = DGeom<BMAX>;
-    constexpr int PC = G::PC, NP = G::NP;
-    extern __shared__ __align__(16) uint32_t smem[];
+    constexpr int PC = G::PC;
+    __shared__ int s_base[kImgTable];
+    __shared__ uint4 s_recs[kDecWarps][64];
+    __shared__ uint8_t s_keys[kDecWarps][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *d4e = smem + warp * G::PER_WARP;
-    uint32_t *d4o = d4e + G::WORDS;
-    uint4 *recs = reinterpret_cast<uint4 *>(d4o + G::WORDS);
-    uint8_t *keys = reinterpret_cast<uint8_t *>(recs + 64);
+    uint4 *recs = s_recs[warp];
+    uint8_t *keys = s_keys[warp];
     const int pr = lane / PC, pc = lane % PC;
-    const unsigned FULL = 0xffffffffu;
+    if (count <= kImgTable)
+        for (int i = threadIdx.x; i < count; i += blockDim.x) s_base[i] = descs[i].strip_base;
+    __syncthreads();
     const int gwarps = gridDim.x * kDecWarps;
-
     for (int g = blockIdx.x * kDecWarps + warp; g < total_strips; g += gwarps) {
-        const int img = find_image(descs, count, g);
+        const int img = find_image_s(s_base, descs, count, g);
         const DecDesc &D = descs[img];
         const int W = D.W, H = D.H, tw = D.tw;
         const int s = g - D.strip_base;
-        const int row = s / D.spr, sc = s % D.spr;
+        const int row = s / D.spr, sc = s - row * D.spr;
         const int sy0 = row * BMAX, sx0 = sc * G::SW;
         const int top0 = row * tw + sc * G::TOPS;
         const int nvalid = min(G::TOPS, tw - sc * G::TOPS);
@@ -88,66 +128,35 @@ __global__ void __launch_bounds__(kDecWarps * 32)
         const bool valid = lane_top < nvalid;
         const int bmin = D.bmin;
         const int cpt_side = BMAX / bmin, cpt = cpt_side * cpt_side;
-        const uint8_t *src = D.buf[src_sel];
-        uint8_t *dst = D.buf[src_sel ^ 1];
         const bool centred = (D.mode == FIC_NOSEARCH || D.mode == FIC_MNS);
         const int ko1 = (1 << D.o_bits) - 1;
+        const int rx0 = clampi(sx0 - BMAX / 2, 0, W - 2 * BMAX);
+        const int xl = sx0 + (nvalid - 1) * BMAX;
+        const int rx1 = clampi(xl - BMAX / 2, 0, W - 2 * BMAX) + 2 * BMAX;
+        const int ax0 = rx0 & ~15, ax1 = (rx1 + 15) & ~15;
+        const int ry0 = clampi(sy0 - BMAX / 2, 0, H - 2 * BMAX);
+        const int c_base = ax0 >> 1, r_base = ry0 >> 1;
 
-        // ---- records of the strip (at most 64) with their canonical keys
         const uint32_t rbeg = D.tile_off[top0], rend = D.tile_off[top0 + nvalid];
-        const int nrec = (int)(rend - rbeg);
+        const int nrec = min((int)(rend - rbeg), 64);
         __syncwarp();
-        for (int i = lane; i < nrec && i < 64; i += 32) {
+        for (int i = lane; i < nrec; i += 32) {
             const uint4 r = *reinterpret_cast<const uint4 *>(D.rec + rbeg + i);
             recs[i] = r;
             const int x = (int)(r.x & 0xffffu), y = (int)(r.x >> 16);
             const int lt = x / BMAX - sc * G::TOPS;
             keys[i] = (uint8_t)(lt * cpt + (int)dmorton3((x % BMAX) / bmin, (y % BMAX) / bmin));
         }
-        // ---- decimated window of the previous iterate
-        int c_base = 0, r_base = 0;
-        if (!first && centred) {
-            const int rx0 = clampi(sx0 - BMAX / 2, 0, W - 2 * BMAX);
-            const int xl = sx0 + (nvalid - 1) * BMAX;
-            const int rx1 = clampi(xl - BMAX / 2, 0, W - 2 * BMAX) + 2 * BMAX;
-            const int ax0 = rx0 & ~15, ax1 = (rx1 + 15) & ~15;
-            const int ry0 = clampi(sy0 - BMAX / 2, 0, H - 2 * BMAX);
-            c_base = ax0 >> 1;
-            r_base = ry0 >> 1;
-            const int upr = (ax1 - ax0) >> 4, npairs = upr * 4;
-            for (int u = lane; u < BMAX * upr; u += 32) {
-                const int r = u / upr, cu = u - r * upr;
-                const uint8_t *p = src + (size_t)(ry0 + 2 * r) * W + ax0 + 16 * cu;
-                const uint4 a = *reinterpret_cast<const uint4 *>(p);
-                const uint4 b = *reinterpret_cast<const uint4 *>(p + W);
-                uint4 o;
-                o.x = d4_pair(a.x, b.x);
-                o.y = d4_pair(a.y, b.y);
-                o.z = d4_pair(a.z, b.z);
-                o.w = d4_pair(a.w, b.w);
-                *reinterpret_cast<uint4 *>(d4e + r * NP + 4 * cu) = o;
-            }
-            __syncwarp();
-            for (int i = lane; i < BMAX * npairs; i += 32) {
-                const int r = i / npairs, c = i - r * npairs;
-                const uint32_t a = d4e[r * NP + c];
-                const uint32_t b = (c + 1 < npairs) ? d4e[r * NP + c + 1] : 0u;
-                d4o[r * NP + c] = __byte_perm(a, b, 0x5432);
-            }
-        }
         __syncwarp();
-
-        // ---- transform of each half-patch
-        int t_x[2], t_y[2], t_lg[2], t_dx[2], t_dy[2], t_c[2], t_O[2], t_iso[2];
+        uint32_t fw[2] = {0u, 0u}, gw[2] = {0u, 0u}, hw[2] = {0u, 0u};
+        int Ow[2] = {0, 0};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            t_x[h] = t_y[h] = t_dx[h] = t_dy[h] = t_c[h] = t_O[h] = t_iso[h] = 0;
-            t_lg[h] = 2;
             if (!valid || nrec <= 0) continue;
             const int px = 8 * pc + 4 * h, py = 4 * pr;  // in strip
             const int tx = px - lane_top * BMAX;
             const int key = lane_top * cpt + (int)dmorton3(tx / bmin, py / bmin);
-            int lo = 0, hi = min(nrec, 64) - 1;
+            int lo = 0, hi = nrec - 1;
             while (lo < hi) {  // last record with keys[i] <= key
                 const int mid = (lo + hi + 1) >> 1;
                 if ((int)keys[mid] <= key) lo = mid;
@@ -159,15 +168,16 @@ __global__ void __launch_bounds__(kDecWarps * 32)
             const int k = (int)((r.y >> 16) & 0xffu), q = (int)(r.y >> 24);
             const int B = BMAX >> (level - 1);
             const int Oi = (510 * q + ko1) / (2 * ko1);
+            int t_x, t_y, t_lg, t_dx, t_dy, t_c, t_O, t_iso;
             if (phase == 1) {
-                t_x[h] = x;
-                t_y[h] = y;
-                t_lg[h] = 31 - __clz(B);
-                t_dx[h] = (int)(r.w & 0xffffu);
-                t_dy[h] = (int)(r.w >> 16);
-                t_c[h] = contrast_code(k, D.s_bits);
-                t_O[h] = Oi;
-                t_iso[h] = (int)(r.z >> 24);
+                t_x = x;
+                t_y = y;
+                t_lg = 31 - __clz(B);
+                t_dx = (int)(r.w & 0xffffu);
+                t_dy = (int)(r.w >> 16);
+                t_c = contrast_code(k, D.s_bits);
+                t_O = Oi;
+                t_iso = (int)(r.z >> 24);
             } else {
                 const int hb = B >> 1;
                 const int ax = sx0 + px, ay = sy0 + py;
@@ -176,64 +186,138 @@ __global__ void __launch_bounds__(kDecWarps * 32)
                           d2 = (int)(int8_t)((r.z >> 16) & 0xffu);
                 const int O0 = Oi + d0, O1 = Oi + d1, O2 = Oi + d2;
                 const int O3 = 4 * Oi - (O0 + O1 + O2);  // eq. (1)
-                const int Os = sb == 0 ? O0 : (sb == 1 ? O1 : (sb == 2 ? O2 : O3));
-                t_x[h] = x + (sb & 1) * hb;
-                t_y[h] = y + (sb >> 1) * hb;
-                t_lg[h] = 31 - __clz(hb);
-                t_dx[h] = centred_origin(t_x[h], hb, W);
-                t_dy[h] = centred_origin(t_y[h], hb, H);
-                t_c[h] = phase2_code(level, (k >> sb) & 1);
-                t_O[h] = Os;
-                t_iso[h] = 0;
+                t_O = sb == 0 ? O0 : (sb == 1 ? O1 : (sb == 2 ? O2 : O3));
+                t_x = x + (sb & 1) * hb;
+                t_y = y + (sb >> 1) * hb;
+                t_lg = 31 - __clz(hb);
+                t_dx = centred_origin(t_x, hb, W);
+                t_dy = centred_origin(t_y, hb, H);
+                t_c = phase2_code(level, (k >> sb) & 1);
+                t_iso = 0;
             }
+            const int u0 = sx0 + px - t_x, v0 = sy0 + py - t_y;
+            const int c = centred ? (t_dx >> 1) + u0 - c_base : 0;
+            const int rr = centred ? (t_dy >> 1) + v0 - r_base : 0;
+            fw[h] = fast_word(c, rr, t_lg, t_c);
+            Ow[h] = t_O;
+            gw[h] = (uint32_t)t_dx | ((uint32_t)t_dy << 16);
+            hw[h] = (uint32_t)u0 | ((uint32_t)v0 << 8) | ((uint32_t)t_iso << 16);
         }
+        tfw[(size_t)g * 32 + lane] = make_uint4(fw[0], (uint32_t)Ow[0], fw[1], (uint32_t)Ow[1]);
+        if (!centred) tgw[(size_t)g * 32 + lane] = make_uint4(gw[0], hw[0], gw[1], hw[1]);
+        if (lane == 0) {
+            StripInfo si;
+            si.buf[0] = D.buf[0];
+            si.buf[1] = D.buf[1];
+            si.W = W;
+            si.sxy = (uint32_t)sx0 | ((uint32_t)sy0 << 16);
+            si.axy = (uint32_t)ax0 | ((uint32_t)ry0 << 16);
+            si.misc = (uint32_t)((ax1 - ax0) >> 4) | ((uint32_t)nvalid << 8) | ((centred ? 1u : 0u) << 16);
+            sinfo[g] = si;
+        }
+    }
+}
+
+template <int BMAX>
+__global__ void __launch_bounds__(kDecWarps * 32, 4)
+    decode_iter_kernel(const StripInfo *__restrict__ sinfo, const uint4 *__restrict__ tfw,
+                       const uint4 *__restrict__ tgw, int total_strips, int src_sel, int first) {
+    using G = DGeom<BMAX>;
+    constexpr int PC = G::PC, NP = G::NP;
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *d4e = smem + warp * G::WORDS;
+    const int pr = lane / PC, pc = lane % PC;
+    const unsigned FULL = 0xffffffffu;
+    const int gwarps = gridDim.x * kDecWarps;
+
+    for (int g = blockIdx.x * kDecWarps + warp; g < total_strips; g += gwarps) {
+        const StripInfo si = sinfo[g];
+        const uint4 tf = tfw[(size_t)g * 32 + lane];
+        const int W = si.W;
+        const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
+        const int nvalid = (int)((si.misc >> 8) & 0xffu);
+        const bool centred = (si.misc >> 16) & 1u;
+        const bool valid = (8 * pc) / BMAX < nvalid;
+        const uint8_t *src = si.buf[src_sel];
+        uint8_t *dst = const_cast<uint8_t *>(si.buf[src_sel ^ 1]);
+        uint8_t *out = dst + (size_t)(sy0 + 4 * pr) * W + sx0 + 8 * pc;
+        const uint32_t fw[2] = {tf.x, tf.z};
+        const int Ov[2] = {(int)tf.y, (int)tf.w};
+
+        if (first) {
+            // x0 = 128 everywhere: d4 - mean d4 = 0, every pixel is its luminance
+            if (valid) {
+                const uint32_t w0 = pack_sat_u8(Ov[0], Ov[0], pack_sat_u8(Ov[0], Ov[0], 0u));
+                const uint32_t w1 = pack_sat_u8(Ov[1], Ov[1], pack_sat_u8(Ov[1], Ov[1], 0u));
+#pragma unroll
+                for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(out + (size_t)i * W) = make_uint2(w0, w1);
+            }
+            continue;
+        }
+        __syncwarp();
+        if (centred)
+            stage_window<BMAX, G::UPR, NP>(src, W, (int)(si.axy >> 16), (int)(si.axy & 0xffffu), (int)(si.misc & 0xffu),
+                                           d4e, lane);
+        __syncwarp();
 
         // ---- decimated domain values of the half-patches (16 each) and partial Sd4
         uint32_t dv[2][4][2];  // [half][row][pair]
         int part[2] = {0, 0};
+        int lg[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
+            lg[h] = (int)((fw[h] >> 16) & 0xffu);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) dv[h][i][0] = dv[h][i][1] = 0x02000200u;  // 512, 512
-            if (!valid || first) continue;
-            const int ax = sx0 + 8 * pc + 4 * h, ay = sy0 + 4 * pr;
-            const int u0 = ax - t_x[h], v0 = ay - t_y[h];
-            if (centred && t_iso[h] == 0) {
-                const int c = (t_dx[h] >> 1) + u0 - c_base, rr = (t_dy[h] >> 1) + v0 - r_base;
-                const uint32_t *base = (c & 1) ? d4o + rr * NP + ((c - 1) >> 1) : d4e + rr * NP + (c >> 1);
+            for (int i = 0; i < 4; ++i) dv[h][i][0] = dv[h][i][1] = 0u;
+            if (!valid) continue;
+            if (centred) {
+                const int c = (int)(fw[h] & 0xffu), rr = (int)((fw[h] >> 8) & 0xffu);
+                const uint32_t *base = d4e + rr * NP + (c >> 1);
+                const bool odd = c & 1;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    dv[h][i][0] = base[i * NP];
-                    dv[h][i][1] = base[i * NP + 1];
+                    const uint32_t e0 = base[i * NP], e1 = base[i * NP + 1];
+                    if (odd) {
+                        const uint32_t e2 = base[i * NP + 2];
+                        dv[h][i][0] = __funnelshift_r(e0, e1, 16);
+                        dv[h][i][1] = __funnelshift_r(e1, e2, 16);
+                    } else {
+                        dv[h][i][0] = e0;
+                        dv[h][i][1] = e1;
+                    }
                 }
             } else {
-                const int B = 1 << t_lg[h];
+                const uint4 gg = tgw[(size_t)g * 32 + lane];
+                const uint32_t gd = h ? gg.z : gg.x, ge = h ? gg.w : gg.y;
+                const int dx = (int)(gd & 0xffffu), dy = (int)(gd >> 16);
+                const int u0 = (int)(ge & 0xffu), v0 = (int)((ge >> 8) & 0xffu), iso = (int)((ge >> 16) & 0xffu);
+                const int B = 1 << lg[h];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     uint32_t vals[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         int su, sv;
-                        iso_src(t_iso[h], B, u0 + e, v0 + i, su, sv);
-                        const uint8_t *p = src + (size_t)(t_dy[h] + 2 * sv) * W + t_dx[h] + 2 * su;
+                        iso_src(iso, B, u0 + e, v0 + i, su, sv);
+                        const uint8_t *p = src + (size_t)(dy + 2 * sv) * W + dx + 2 * su;
                         vals[e] = (uint32_t)p[0] + p[1] + p[W] + p[W + 1];
                     }
                     dv[h][i][0] = vals[0] | (vals[1] << 16);
                     dv[h][i][1] = vals[2] | (vals[3] << 16);
                 }
             }
+            uint32_t pk = 0;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint32_t s2 = dv[h][i][0] + dv[h][i][1];
-                part[h] += (int)((s2 & 0xffffu) + (s2 >> 16));
-            }
+            for (int i = 0; i < 4; ++i) pk += dv[h][i][0] + dv[h][i][1];
+            part[h] = (int)((pk & 0xffffu) + (pk >> 16));
         }
         // ---- Sd4 per transform: halves of one lane first (side >= 8), then the
         // lane group of the transform; every lane runs the same shuffles
         int sd4[2];
         {
-            const bool big = t_lg[0] >= 3;  // a transform of side >= 8 covers both halves
-            const int B = 1 << t_lg[0];
+            const bool big = lg[0] >= 3;  // a transform of side >= 8 covers both halves
+            const int B = 1 << lg[0];
             const int gx = big ? B / 8 : 1, gy = big ? B / 4 : 1;
             int v = part[0] + part[1];
 #pragma unroll
@@ -249,71 +333,84 @@ __global__ void __launch_bounds__(kDecWarps * 32)
             sd4[0] = big ? v : part[0];
             sd4[1] = big ? v : part[1];
         }
-        if (first) {
-            sd4[0] = 512 << (2 * t_lg[0]);
-            sd4[1] = 512 << (2 * t_lg[1]);
-        }
 
-        // ---- output pixels
+        // ---- output pixels: p = (c d4 + K) >> 9 with K = floor((512 n O - c Sd4 + 256 n) / n)
         if (valid) {
+            int K[2], cb0[2], cb1[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int lg2n = 2 * lg[h];
+                const int c = (int)(int8_t)(fw[h] >> 24);
+                K[h] = (Ov[h] * (1 << (9 + lg2n)) + (1 << (8 + lg2n)) - c * sd4[h]) >> lg2n;
+                cb0[h] = (int)(fw[h] >> 24);
+                cb1[h] = (int)((fw[h] >> 24) << 8);
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                uint32_t wout[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int lg2n = 2 * t_lg[h];
-                    const int n = 1 << lg2n;
-                    const int base = t_O[h] * (1 << (9 + lg2n)) + (n << 8) - t_c[h] * sd4[h];
-                    uint32_t w = 0;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const uint32_t pair = dv[h][i][e >> 1];
-                        const int d = (int)((e & 1) ? (pair >> 16) : (pair & 0xffffu));
-                        int p = (base + t_c[h] * (d << lg2n)) >> (9 + lg2n);
-                        p = clampi(p, 0, 255);
-                        w |= (uint32_t)p << (8 * e);
-                    }
-                    wout[h] = w;
-                }
-                *reinterpret_cast<uint2 *>(dst + (size_t)(sy0 + 4 * pr + i) * W + sx0 + 8 * pc) =
-                    make_uint2(wout[0], wout[1]);
+                const uint32_t w0 = row_pixels(dv[0][i][0], dv[0][i][1], cb0[0], cb1[0], K[0]);
+                const uint32_t w1 = row_pixels(dv[1][i][0], dv[1][i][1], cb0[1], cb1[1], K[1]);
+                *reinterpret_cast<uint2 *>(out + (size_t)i * W) = make_uint2(w0, w1);
             }
         }
     }
 }
 
+size_t decode_table_bytes_per_strip() { return sizeof(StripInfo) + 2 * 32 * sizeof(uint4); }
+
 size_t decode_smem_bytes(int bmax) {
-    int words = bmax == 32 ? DGeom<32>::PER_WARP : (bmax == 16 ? DGeom<16>::PER_WARP : DGeom<8>::PER_WARP);
+    int words = bmax == 32 ? DGeom<32>::WORDS : (bmax == 16 ? DGeom<16>::WORDS : DGeom<8>::WORDS);
     return (size_t)kDecWarps * words * sizeof(uint32_t);
 }
 
-template <int BMAX>
-static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, int src_sel, int first,
-                             cudaStream_t st) {
-    static int grid_cache = 0;
-    const size_t smem = decode_smem_bytes(BMAX);
-    if (grid_cache == 0) {
-        cudaError_t e = cudaFuncSetAttribute(decode_iter_kernel<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
+static int grid_for(const void *fn, size_t smem, int &cache) {
+    if (cache == 0) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, decode_iter_kernel<BMAX>, kDecWarps * 32, smem);
-        grid_cache = sms * (per > 0 ? per : 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kDecWarps * 32, smem);
+        cache = sms * (per > 0 ? per : 1);
     }
-    const int need = (total_strips + kDecWarps - 1) / kDecWarps;
-    const int grid = need < grid_cache ? need : grid_cache;
-    decode_iter_kernel<BMAX><<<grid, kDecWarps * 32, smem, st>>>(descs, count, total_strips, src_sel, first);
-    return cudaGetLastError();
+    return cache;
 }
 
-cudaError_t launch_decode_iter(int bmax, const DecDesc *d_descs, int count, int total_strips, int src_sel,
-                               int first, cudaStream_t st) {
+template <int BMAX>
+static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, void *tables, int iters,
+                             cudaStream_t st) {
+    static int grid_setup = 0, grid_iter = 0;
+    static bool attr = false;
+    const size_t smem = decode_smem_bytes(BMAX);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(decode_iter_kernel<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    StripInfo *sinfo = static_cast<StripInfo *>(tables);
+    uint4 *tfw = reinterpret_cast<uint4 *>(sinfo + total_strips);
+    uint4 *tgw = tfw + (size_t)total_strips * 32;
+    const int need = (total_strips + kDecWarps - 1) / kDecWarps;
+    const int gs = grid_for((const void *)decode_setup_kernel<BMAX>, 0, grid_setup);
+    decode_setup_kernel<BMAX><<<need < gs ? need : gs, kDecWarps * 32, 0, st>>>(descs, count, total_strips, sinfo,
+                                                                              tfw, tgw);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int gi = grid_for((const void *)decode_iter_kernel<BMAX>, smem, grid_iter);
+    const int grid = need < gi ? need : gi;
+    for (int it = 0; it < iters; ++it) {
+        const int src_sel = (iters - it) & 1;  // the last iteration writes buf[0] (the output)
+        decode_iter_kernel<BMAX><<<grid, kDecWarps * 32, smem, st>>>(sinfo, tfw, tgw, total_strips, src_sel, it == 0);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_decode(int bmax, const DecDesc *d_descs, int count, int total_strips, void *tables, int iters,
+                          cudaStream_t st) {
     switch (bmax) {
-    case 32: return dlaunch_t<32>(d_descs, count, total_strips, src_sel, first, st);
-    case 16: return dlaunch_t<16>(d_descs, count, total_strips, src_sel, first, st);
-    case 8: return dlaunch_t<8>(d_descs, count, total_strips, src_sel, first, st);
+    case 32: return dlaunch_t<32>(d_descs, count, total_strips, tables, iters, st);
+    case 16: return dlaunch_t<16>(d_descs, count, total_strips, tables, iters, st);
+    case 8: return dlaunch_t<8>(d_descs, count, total_strips, tables, iters, st);
     default: return cudaErrorInvalidValue;
     }
 }

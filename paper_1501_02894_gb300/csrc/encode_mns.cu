@@ -10,8 +10,8 @@
 // (consecutive in the stream's raster order).  Everything the quadtree of
 // those blocks can touch lies inside the union of their level-1 domains, so
 // the warp decimates that window once into shared memory (2x2 sums packed as
-// 16-bit pairs, at even and at odd alignment) and then runs all levels out of
-// registers and shared memory:
+// 16-bit pairs; windows that start at an odd column are realigned with funnel
+// shifts) and then runs all levels out of registers and shared memory:
 //   * lane l owns an 8x4-pixel patch of the strip; every quadtree block of
 //     side >= 8 is a power-of-two group of lanes, a 4x4 block is half a patch;
 //   * moments per level: sum r*d4 and sum d4^2 by dp2a on packed operands,
@@ -38,7 +38,7 @@ struct Geom {
     static constexpr int TOPS = SW / BMAX;  // top-level blocks per strip
     // words per row of each packed decimated array (pairs of 2x2 sums)
     static constexpr int NP = BMAX == 32 ? 16 : (BMAX == 16 ? 24 : 40);
-    static constexpr int WORDS = BMAX * NP;
+    static constexpr int WORDS = BMAX * NP;  // one packed decimated window per warp
 };
 
 constexpr int kWarps = 8;
@@ -202,15 +202,22 @@ __device__ __forceinline__ void patch_moments(const uint32_t *d4e, int c, int rr
 
 // Moments of one 4x4 block (one half of the patch): 4 rows x 4 pixels (word
 // `h` of each row) against 4 x 4 decimated values starting at column c of
-// either parity.
+// either parity (an odd start is realigned from three even pairs).
 template <int NP>
-__device__ __forceinline__ void half_moments(const uint32_t *d4e, const uint32_t *d4o, int c, int rr,
-                                             const uint2 *rw, int h, int &sd, int &sdd, int &sdr) {
+__device__ __forceinline__ void half_moments(const uint32_t *d4e, int c, int rr, const uint2 *rw, int h,
+                                             int &sd, int &sdd, int &sdr) {
     unsigned a_dr = 0, pk = 0, ql = 0, qh = 0;
-    const uint32_t *base = (c & 1) ? d4o + rr * NP + ((c - 1) >> 1) : d4e + rr * NP + (c >> 1);
+    const uint32_t *base = d4e + rr * NP + (c >> 1);
+    const bool odd = c & 1;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const uint32_t p0 = base[i * NP], p1 = base[i * NP + 1];
+        const uint32_t e0 = base[i * NP], e1 = base[i * NP + 1];
+        uint32_t p0 = e0, p1 = e1;
+        if (odd) {
+            const uint32_t e2 = base[i * NP + 2];
+            p0 = __funnelshift_r(e0, e1, 16);
+            p1 = __funnelshift_r(e1, e2, 16);
+        }
         const uint32_t r = h ? rw[i].y : rw[i].x;
         a_dr = dp2a_lo(p0, r, a_dr);
         a_dr = dp2a_hi(p1, r, a_dr);
@@ -223,29 +230,42 @@ __device__ __forceinline__ void half_moments(const uint32_t *d4e, const uint32_t
     sdr = (int)a_dr;
 }
 
+// Phase-1 summary of a block that the level loop carries forward.
+struct Code {
+    int k, q;
+    bool pass;
+};
+
 template <int BMAX>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, 3)
     mns_encode_kernel(const EncDesc *__restrict__ descs, int count, int total_strips,
                       uint32_t *__restrict__ status, uint32_t *__restrict__ ticket) {
     using G = Geom<BMAX>;
     constexpr int PC = G::PC, NP = G::NP;
+    constexpr int UPR = BMAX == 32 ? 4 : (BMAX == 16 ? 8 : 16);
     extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int s_base[kImgTable];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *d4e = smem + warp * 2 * G::WORDS;
-    uint32_t *d4o = d4e + G::WORDS;
+    uint32_t *d4e = smem + warp * G::WORDS;
     const int pr = lane / PC, pc = lane % PC;
     const unsigned FULL = 0xffffffffu;
+    if (count <= kImgTable)
+        for (int i = threadIdx.x; i < count; i += blockDim.x) s_base[i] = descs[i].strip_base;
+    __syncthreads();
 
+    int g_next = 0;
+    if (lane == 0) g_next = (int)atomicAdd(ticket, 1u);
+    g_next = __shfl_sync(FULL, g_next, 0);
     for (;;) {
-        int g = 0;
-        if (lane == 0) g = (int)atomicAdd(ticket, 1u);
-        g = __shfl_sync(FULL, g, 0);
+        const int g = g_next;
         if (g >= total_strips) break;
-        const int img = find_image(descs, count, g);
+        // fetch the following ticket now; its latency hides behind this strip
+        if (lane == 0) g_next = (int)atomicAdd(ticket, 1u);
+        const int img = find_image_s(s_base, descs, count, g);
         const EncDesc &D = descs[img];
         const int W = D.W, H = D.H, tw = D.tw;
         const int s = g - D.strip_base;
-        const int row = s / D.spr, sc = s % D.spr;
+        const int row = s / D.spr, sc = s - row * D.spr;
         const int sy0 = row * BMAX, sx0 = sc * G::SW;
         const int top0 = row * tw + sc * G::TOPS;
         const int nvalid = min(G::TOPS, tw - sc * G::TOPS);
@@ -257,6 +277,12 @@ __global__ void __launch_bounds__(kWarps * 32)
         const float qscale = (float)ko1 / 255.f;
         const bool ph2 = (D.mode == FIC_MNS) && D.phase2;
 
+        // ---- the lane's range pixels (4 rows x 8), issued first
+        uint2 rw[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            rw[i] = valid ? __ldg(reinterpret_cast<const uint2 *>(D.img + (size_t)(sy0 + 4 * pr + i) * W + sx0 + 8 * pc))
+                          : make_uint2(0u, 0u);
         // ---- decimated domain window of the strip -> shared memory
         const int rx0 = clampi(sx0 - BMAX / 2, 0, W - 2 * BMAX);
         const int xl = sx0 + (nvalid - 1) * BMAX;
@@ -264,58 +290,32 @@ __global__ void __launch_bounds__(kWarps * 32)
         const int ax0 = rx0 & ~15, ax1 = (rx1 + 15) & ~15;
         const int ry0 = clampi(sy0 - BMAX / 2, 0, H - 2 * BMAX);
         const int c_base = ax0 >> 1, r_base = ry0 >> 1;
-        const int upr = (ax1 - ax0) >> 4;  // 16-pixel units per decimated row
-        const int npairs = upr * 4;
         __syncwarp();
-        for (int u = lane; u < BMAX * upr; u += 32) {
-            const int r = u / upr, cu = u - r * upr;
-            const uint8_t *p = D.img + (size_t)(ry0 + 2 * r) * W + ax0 + 16 * cu;
-            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
-            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(p + W));
-            uint4 o;
-            o.x = d4_pair(a.x, b.x);
-            o.y = d4_pair(a.y, b.y);
-            o.z = d4_pair(a.z, b.z);
-            o.w = d4_pair(a.w, b.w);
-            *reinterpret_cast<uint4 *>(d4e + r * NP + 4 * cu) = o;
-        }
-        __syncwarp();
-        for (int i = lane; i < BMAX * npairs; i += 32) {
-            const int r = i / npairs, c = i - r * npairs;
-            const uint32_t a = d4e[r * NP + c];
-            const uint32_t b = (c + 1 < npairs) ? d4e[r * NP + c + 1] : 0u;
-            d4o[r * NP + c] = __byte_perm(a, b, 0x5432);
-        }
-        __syncwarp();
-
-        // ---- the lane's range pixels (4 rows x 8)
-        uint2 rw[4];
+        stage_window<BMAX, UPR, NP>(D.img, W, ry0, ax0, (ax1 - ax0) >> 4, d4e, lane);
         int sr_h[2] = {0, 0}, srr_h[2] = {0, 0};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            rw[i] = valid ? __ldg(reinterpret_cast<const uint2 *>(D.img + (size_t)(sy0 + 4 * pr + i) * W +
-                                                                   sx0 + 8 * pc))
-                          : make_uint2(0u, 0u);
             sr_h[0] += (int)__dp4a(rw[i].x, 0x01010101u, 0u);
             sr_h[1] += (int)__dp4a(rw[i].y, 0x01010101u, 0u);
             srr_h[0] += (int)__dp4a(rw[i].x, rw[i].x, 0u);
             srr_h[1] += (int)__dp4a(rw[i].y, rw[i].y, 0u);
         }
+        __syncwarp();
 
         // ---- quadtree, level by level
         Leaf leaf[2];
         leaf[0].pos = -1;
         leaf[1].pos = -1;
         uint32_t splitbits = 0;
-        unsigned long long fits = 0;
+        unsigned fits = 0;
         const int cpt_side = BMAX / bmin;  // bmin cells per top side
         const int cpt = cpt_side * cpt_side;
         bool act = valid;
-        Fit cur;  // level j result (blocks of side >= 8)
-        Fit cur4[2];
+        Code cur;       // phase-1 codes of the lane's level-j block (side >= 8)
+        Code cur4[2];   // the two 4x4 blocks of the last level
+        Fit ch[2];      // children's fits (ch[0] for side >= 8, both for the 4x4 halves)
         int B = BMAX;
         {
-            // level 1 (B = BMAX >= 8)
             const int gx = B / 8, gy = B / 4;
             const int bx = (8 * pc) / B, by = (4 * pr) / B;
             const int xa = sx0 + bx * B, ya = sy0 + by * B;
@@ -323,17 +323,19 @@ __global__ void __launch_bounds__(kWarps * 32)
             const int u0 = 8 * pc - bx * B, v0 = 4 * pr - by * B;
             int sd = 0, sdd = 0, sdr = 0;
             if (valid) patch_moments<NP>(d4e, (dxa >> 1) + u0 - c_base, (dya >> 1) + v0 - r_base, rw, sd, sdd, sdr);
-            int sr = group_sum<PC>(sr_h[0] + sr_h[1], gx, gy);
-            int srr = group_sum<PC>(srr_h[0] + srr_h[1], gx, gy);
+            const int sr = group_sum<PC>(sr_h[0] + sr_h[1], gx, gy);
+            const int srr = group_sum<PC>(srr_h[0] + srr_h[1], gx, gy);
             sd = group_sum<PC>(sd, gx, gy);
             sdd = group_sum<PC>(sdd, gx, gy);
             sdr = group_sum<PC>(sdr, gx, gy);
             const int lg2n = 2 * (31 - __clz(B));
-            fit_phase1(sr, srr, sd, sdd, sdr, lg2n, s_bits, ko1, magic, qscale,
-                       D.t2q[0] << (2 * lg2n + 10), cur);
+            Fit f;
+            fit_phase1(sr, srr, sd, sdd, sdr, lg2n, s_bits, ko1, magic, qscale, D.t2q[0] << (2 * lg2n + 10), f);
+            cur.k = f.k;
+            cur.q = f.q;
+            cur.pass = f.pass;
         }
         for (int j = 1; j <= L; ++j, B >>= 1) {
-            // blocks of level j: side B; the lane's block (B >= 8) or two halves (B == 4)
             if (B >= 8) {
                 const int gx = B / 8, gy = B / 4;
                 const int bx = (8 * pc) / B, by = (4 * pr) / B;
@@ -342,7 +344,6 @@ __global__ void __launch_bounds__(kWarps * 32)
                 const bool rep = act && u0 == 0 && v0 == 0;
                 if (rep) fits += 1;
                 const int tx = bx * B - lane_top * BMAX, ty = by * B;  // inside the top block
-                const uint32_t z = morton3(tx / B, ty / B);
                 const int pos = lane_top * cpt + (int)morton3(tx / bmin, ty / bmin);
                 const int dxa = centred_origin(xa, B, W), dya = centred_origin(ya, B, H);
                 if (j == L) {
@@ -357,7 +358,6 @@ __global__ void __launch_bounds__(kWarps * 32)
                 const int lg2c = 2 * (31 - __clz(Bc));
                 const long long thr_c = D.t2q[j] << (2 * lg2c + 10);     // children as level-(j+1) blocks
                 const long long thr_p2 = D.t2q[j - 1] << (2 * lg2c + 10); // sub-blocks coded at level j
-                Fit nxt;
                 if (Bc >= 8) {
                     const int cgx = Bc / 8, cgy = Bc / 4;
                     const int cbx = (8 * pc) / Bc, cby = (4 * pr) / Bc;
@@ -366,25 +366,21 @@ __global__ void __launch_bounds__(kWarps * 32)
                     const int cu0 = 8 * pc - cbx * Bc, cv0 = 4 * pr - cby * Bc;
                     int sd = 0, sdd = 0, sdr = 0;
                     if (valid)
-                        patch_moments<NP>(d4e, (cdx >> 1) + cu0 - c_base, (cdy >> 1) + cv0 - r_base, rw, sd,
-                                          sdd, sdr);
-                    int sr = group_sum<PC>(sr_h[0] + sr_h[1], cgx, cgy);
-                    int srr = group_sum<PC>(srr_h[0] + srr_h[1], cgx, cgy);
+                        patch_moments<NP>(d4e, (cdx >> 1) + cu0 - c_base, (cdy >> 1) + cv0 - r_base, rw, sd, sdd, sdr);
+                    const int sr = group_sum<PC>(sr_h[0] + sr_h[1], cgx, cgy);
+                    const int srr = group_sum<PC>(srr_h[0] + srr_h[1], cgx, cgy);
                     sd = group_sum<PC>(sd, cgx, cgy);
                     sdd = group_sum<PC>(sdd, cgx, cgy);
                     sdr = group_sum<PC>(sdr, cgx, cgy);
-                    fit_phase1(sr, srr, sd, sdd, sdr, lg2c, s_bits, ko1, magic, qscale, thr_c, nxt);
+                    fit_phase1(sr, srr, sd, sdd, sdr, lg2c, s_bits, ko1, magic, qscale, thr_c, ch[0]);
                 } else {
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int cxa = sx0 + 8 * pc + 4 * h, cya = sy0 + 4 * pr;
                         const int cdx = centred_origin(cxa, 4, W), cdy = centred_origin(cya, 4, H);
                         int sd = 0, sdd = 0, sdr = 0;
-                        if (valid)
-                            half_moments<NP>(d4e, d4o, (cdx >> 1) - c_base, (cdy >> 1) - r_base, rw, h, sd, sdd,
-                                             sdr);
-                        fit_phase1(sr_h[h], srr_h[h], sd, sdd, sdr, 4, s_bits, ko1, magic, qscale, thr_c,
-                                   cur4[h]);
+                        if (valid) half_moments<NP>(d4e, (cdx >> 1) - c_base, (cdy >> 1) - r_base, rw, h, sd, sdd, sdr);
+                        fit_phase1(sr_h[h], srr_h[h], sd, sdd, sdr, 4, s_bits, ko1, magic, qscale, thr_c, ch[h]);
                     }
                 }
                 // ---- phase 2 of the level-j blocks that failed phase 1 (Sections 3.1-3.3)
@@ -395,24 +391,23 @@ __global__ void __launch_bounds__(kWarps * 32)
                     if (rep && need) fits += 4;
                     const int lg2n4 = lg2c;
                     const int Oi = lum(cur.q, ko1, magic);
-                    // the four children's pixel sums
                     int csr[4];
                     if (Bc >= 8) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             const int cbx = 2 * bx + (k & 1), cby = 2 * by + (k >> 1);
                             const int src = (cby * Bc / 4) * PC + (cbx * Bc / 8);
-                            csr[k] = __shfl_sync(FULL, nxt.sr, src & 31);
+                            csr[k] = __shfl_sync(FULL, ch[0].sr, src & 31);
                         }
                     } else {
                         // B == 8: the top patch holds TL, TR, the bottom patch BL, BR
-                        const int o0 = __shfl_xor_sync(FULL, cur4[0].sr, PC);
-                        const int o1 = __shfl_xor_sync(FULL, cur4[1].sr, PC);
+                        const int o0 = __shfl_xor_sync(FULL, ch[0].sr, PC);
+                        const int o1 = __shfl_xor_sync(FULL, ch[1].sr, PC);
                         const bool top = (pr & 1) == 0;
-                        csr[0] = top ? cur4[0].sr : o0;
-                        csr[1] = top ? cur4[1].sr : o1;
-                        csr[2] = top ? o0 : cur4[0].sr;
-                        csr[3] = top ? o1 : cur4[1].sr;
+                        csr[0] = top ? ch[0].sr : o0;
+                        csr[1] = top ? ch[1].sr : o1;
+                        csr[2] = top ? o0 : ch[0].sr;
+                        csr[3] = top ? o1 : ch[1].sr;
                     }
                     const int dmax = (j == 1) ? 15 : 31;
                     bool inrange = true;
@@ -433,7 +428,7 @@ __global__ void __launch_bounds__(kWarps * 32)
                         const int cbx = (8 * pc) / Bc, cby = (4 * pr) / Bc;
                         const int kk = (cbx & 1) | ((cby & 1) << 1);
                         int bit;
-                        ok_lane = fit_phase2_sub(nxt, lg2n4, O[kk], c0, c1, thr_p2, bit);
+                        ok_lane = fit_phase2_sub(ch[0], lg2n4, O[kk], c0, c1, thr_p2, bit);
                         const uint32_t bits = __ballot_sync(FULL, bit);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
@@ -444,8 +439,8 @@ __global__ void __launch_bounds__(kWarps * 32)
                     } else {
                         const bool top = (pr & 1) == 0;
                         int b0, b1;
-                        const bool ok0 = fit_phase2_sub(cur4[0], 4, O[top ? 0 : 2], c0, c1, thr_p2, b0);
-                        const bool ok1 = fit_phase2_sub(cur4[1], 4, O[top ? 1 : 3], c0, c1, thr_p2, b1);
+                        const bool ok0 = fit_phase2_sub(ch[0], 4, O[top ? 0 : 2], c0, c1, thr_p2, b0);
+                        const bool ok1 = fit_phase2_sub(ch[1], 4, O[top ? 1 : 3], c0, c1, thr_p2, b1);
                         ok_lane = ok0 && ok1;
                         const int my = b0 | (b1 << 1);
                         const int other = __shfl_xor_sync(FULL, my, PC);
@@ -457,9 +452,23 @@ __global__ void __launch_bounds__(kWarps * 32)
                 }
                 if (rep && p2) make_leaf(leaf[0], xa, ya, j, 2, sbits, cur.q, d[0], d[1], d[2], dxa, dya, pos);
                 const bool split = need && !p2;
-                if (rep && split) splitbits |= 1u << (((1u << (2 * (j - 1))) - 1) / 3 + z);
+                if (rep && split) {
+                    const uint32_t z = morton3(tx / B, ty / B);
+                    splitbits |= 1u << (((1u << (2 * (j - 1))) - 1) / 3 + z);
+                }
                 act = split;
-                if (Bc >= 8) cur = nxt;
+                if (Bc >= 8) {
+                    cur.k = ch[0].k;
+                    cur.q = ch[0].q;
+                    cur.pass = ch[0].pass;
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        cur4[h].k = ch[h].k;
+                        cur4[h].q = ch[h].q;
+                        cur4[h].pass = ch[h].pass;
+                    }
+                }
             } else {
                 // B == 4: last level, forced acceptance (two leaves per lane)
 #pragma unroll
@@ -484,37 +493,44 @@ __global__ void __launch_bounds__(kWarps * 32)
         const uint32_t mhi = __reduce_or_sync(FULL, (uint32_t)(mine >> 32));
         const unsigned long long mask = ((unsigned long long)mhi << 32) | mlo;
         const int cnt = __popcll(mask);
+        // decoupled look-back, 32 predecessors per round (one per lane)
         uint32_t prefix = 0;
         int ok = 1;
-        if (lane == 0) {
-            uint32_t *st = status + g;
-            if (s == 0) {
-                st_volatile(st, kIncl | (uint32_t)cnt);
-            } else {
-                st_volatile(st, kAgg | (uint32_t)cnt);
-                int p = g - 1;
-                for (;;) {
-                    uint32_t v = 0;
-                    unsigned it = 0;
-                    while ((v = ld_volatile(status + p)) == 0u && ++it < kSpinLimit) __nanosleep(64);
-                    if (v == 0u) {
-                        ok = 0;
-                        break;
-                    }
-                    prefix += v & kValMask;
-                    if ((v & ~kValMask) == kIncl) break;
-                    --p;
+        if (s == 0) {
+            if (lane == 0) st_volatile(status + g, kIncl | (uint32_t)cnt);
+        } else {
+            if (lane == 0) st_volatile(status + g, kAgg | (uint32_t)cnt);
+            int p = g - 1;
+            for (;;) {
+                const int idx = p - lane;
+                const bool in = idx >= D.strip_base;
+                uint32_t v = in ? ld_volatile(status + idx) : kIncl;
+                unsigned it = 0;
+                while (!__all_sync(FULL, v != 0u) && ++it < kSpinLimit) {
+                    __nanosleep(32);
+                    if (v == 0u) v = ld_volatile(status + idx);
                 }
-                if (ok) st_volatile(st, kIncl | (prefix + (uint32_t)cnt));
+                if (!__all_sync(FULL, v != 0u)) {
+                    ok = 0;
+                    break;
+                }
+                const uint32_t incl = __ballot_sync(FULL, (v & ~kValMask) == kIncl);
+                const int first = incl ? __ffs(incl) - 1 : 32;
+                uint32_t val = (lane <= first) ? (v & kValMask) : 0u;
+                val = __reduce_add_sync(FULL, val);
+                prefix += val;
+                if (incl) break;
+                p -= 32;
+            }
+            if (lane == 0) {
+                if (ok) st_volatile(status + g, kIncl | (prefix + (uint32_t)cnt));
                 else raise_error(D.info, FIC_DEVERR_TIMEOUT);
             }
         }
-        ok = __shfl_sync(FULL, ok, 0);
-        prefix = __shfl_sync(FULL, prefix, 0);
-        // fits: warp total
-        unsigned long long ftot = fits;
-        for (int m = 16; m >= 1; m >>= 1) ftot += __shfl_xor_sync(FULL, ftot, m);
-        if (lane == 0 && ftot) atomicAdd(reinterpret_cast<unsigned long long *>(D.info + FIC_INFO_FITS_LO), ftot);
+        g_next = __shfl_sync(FULL, g_next, 0);
+        const unsigned ftot = __reduce_add_sync(FULL, fits);
+        if (lane == 0 && ftot)
+            atomicAdd(reinterpret_cast<unsigned long long *>(D.info + FIC_INFO_FITS_LO), (unsigned long long)ftot);
         if (!ok) continue;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -530,8 +546,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         splitbits = group_or<PC>(splitbits, BMAX / 8, BMAX / 4);
         if (valid && (8 * pc) % BMAX == 0 && pr == 0) {
             D.split[top0 + lane_top] = splitbits;
-            D.tile_off[top0 + lane_top] =
-                prefix + (uint32_t)__popcll(mask & ((1ull << (lane_top * cpt)) - 1ull));
+            D.tile_off[top0 + lane_top] = prefix + (uint32_t)__popcll(mask & ((1ull << (lane_top * cpt)) - 1ull));
         }
         if (lane == 0 && s == D.nstrips - 1) {
             D.tile_off[D.tw * D.th] = prefix + (uint32_t)cnt;
@@ -552,7 +567,7 @@ __global__ void encode_init_kernel(const EncDesc *__restrict__ descs, int count,
 
 size_t mns_smem_bytes(int bmax) {
     int words = bmax == 32 ? Geom<32>::WORDS : (bmax == 16 ? Geom<16>::WORDS : Geom<8>::WORDS);
-    return (size_t)kWarps * 2 * words * sizeof(uint32_t);
+    return (size_t)kWarps * words * sizeof(uint32_t);
 }
 
 int mns_strip_width(int bmax) { return 1024 / bmax; }

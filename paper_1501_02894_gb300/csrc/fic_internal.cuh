@@ -114,4 +114,51 @@ __device__ __forceinline__ int find_image(const D *descs, int count, int g) {
     return lo;
 }
 
+// Stage the decimated window of a strip: rows ry0.. of the image, columns
+// ax0..ax1 (16-aligned), as packed pairs of 2x2 sums, `upr` 16-pixel units
+// per row (at most UPR).  Every lane issues its four loads before using them.
+template <int BMAX, int UPR, int NP>
+__device__ __forceinline__ void stage_window(const uint8_t *__restrict__ img, int W, int ry0, int ax0, int upr,
+                                             uint32_t *d4e, int lane) {
+    constexpr int ITER = BMAX * UPR / 32;
+    uint4 a[ITER], b[ITER];
+#pragma unroll
+    for (int t = 0; t < ITER; ++t) {
+        const int u = lane + 32 * t;
+        const int r = u / UPR, cu = u % UPR;
+        if (cu < upr) {
+            const uint8_t *p = img + (size_t)(ry0 + 2 * r) * W + ax0 + 16 * cu;
+            a[t] = __ldg(reinterpret_cast<const uint4 *>(p));
+            b[t] = __ldg(reinterpret_cast<const uint4 *>(p + W));
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < ITER; ++t) {
+        const int u = lane + 32 * t;
+        const int r = u / UPR, cu = u % UPR;
+        if (cu < upr) {
+            uint4 o;
+            o.x = d4_pair(a[t].x, b[t].x);
+            o.y = d4_pair(a[t].y, b[t].y);
+            o.z = d4_pair(a[t].z, b[t].z);
+            o.w = d4_pair(a[t].w, b[t].w);
+            *reinterpret_cast<uint4 *>(d4e + r * NP + 4 * cu) = o;
+        }
+    }
+}
+
+constexpr int kImgTable = 1024;  // image strip bases kept in shared memory
+
+template <class Desc>
+__device__ __forceinline__ int find_image_s(const int *s_base, const Desc *descs, int count, int g) {
+    if (count > kImgTable) return find_image(descs, count, g);
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_base[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 }  // namespace fic
