@@ -245,7 +245,7 @@ def run_ours(args):
         with torch.cuda.graph(g_dec, stream=stream):
             dec.run(DECODE_ITERS, stream)
     stream.synchronize()
-    launches_per_step = 2 + 1 + DECODE_ITERS  # init + encoder, decode setup + one launch per iteration
+    launches_per_step = 2 + 1 + DECODE_ITERS  # encoder + pack, decode setup + one launch per iteration
 
     def step():
         g_enc.replay()

@@ -7,11 +7,47 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "fic_internal.cuh"
 
 namespace fic {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+int make_tma_map(TmaMap *out, const void *base, int W, int H, int boxw, int boxh) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return FIC_ECUDA;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    CUtensorMap m;
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)W};
+    const cuuint32_t box[2] = {(cuuint32_t)boxw, (cuuint32_t)boxh};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return FIC_ECUDA;
+    memcpy(out, &m, sizeof(TmaMap));
+    return FIC_OK;
+}
+
+int box_width(int bmax, int W) {
+    const int bw = bmax == 32 ? WinBox<32>::W : (bmax == 16 ? WinBox<16>::W : WinBox<8>::W);
+    return bw < W ? bw : W;
+}
+
 cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int total_strips, uint32_t *status,
                               uint32_t *ticket, cudaStream_t st);
+cudaError_t launch_mns_encode_slots(int bmax, const EncDesc *d_descs, int count, int total_strips, int total_chunks,
+                                    uint32_t *pack_status, cudaStream_t st);
 cudaError_t launch_decode(int bmax, const DecDesc *d_descs, int count, int total_strips, void *tables, int iters,
                           cudaStream_t st);
 size_t decode_table_bytes_per_strip();
@@ -74,6 +110,7 @@ struct fic_plan {
     int count;
     int bmax;
     int total_strips;
+    int total_chunks;
     void *ws;
     size_t ws_bytes;
     EncDesc *d_enc;
@@ -120,14 +157,34 @@ int fic_stream_sizes(int width, int height, const fic_params *p, int32_t *ntop, 
     return FIC_OK;
 }
 
+// Encoder workspace layout (each part 256-byte aligned): tensor maps, image
+// descriptors, per-strip (count, fits), pack look-back status (one word per
+// 32-strip chunk + 1), per-strip record slots (64 records = 1 KiB per strip).
+struct EncLayout {
+    size_t maps, descs, stats, pstatus, slots, total;
+};
+
+static EncLayout enc_layout(int count, size_t strips, size_t chunks) {
+    EncLayout L;
+    L.maps = 0;
+    L.descs = L.maps + align_up(sizeof(TmaMap) * (size_t)count);
+    L.stats = L.descs + align_up(sizeof(EncDesc) * (size_t)count);
+    L.pstatus = L.stats + align_up(8 * strips);
+    L.slots = L.pstatus + align_up(4 * (chunks + 1));
+    L.total = L.slots + align_up(sizeof(fic_record) * 64 * strips);
+    return L;
+}
+
 size_t fic_encode_workspace_bytes(int count, const int *widths, const int *heights, const fic_params *params) {
     if (count <= 0 || !widths || !heights || !params) return 0;
-    size_t strips = 0;
+    size_t strips = 0, chunks = 0;
     for (int i = 0; i < count; ++i) {
         if (fic_validate(widths[i], heights[i], &params[i])) return 0;
-        strips += (size_t)nstrips_of(widths[i], heights[i], params[i].bmax);
+        const size_t n = (size_t)nstrips_of(widths[i], heights[i], params[i].bmax);
+        strips += n;
+        chunks += (n + 31) / 32;
     }
-    return align_up(sizeof(EncDesc) * (size_t)count) + align_up(4 * strips) + kAlign;
+    return enc_layout(count, strips, chunks).total;
 }
 
 int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, const int *heights, int count,
@@ -138,7 +195,9 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
     *plan_out = nullptr;
     const int bmax = params[0].bmax;
     std::vector<EncDesc> h((size_t)count);
-    int strips = 0;
+    std::vector<TmaMap> maps((size_t)count);
+    const TmaMap *d_maps = static_cast<const TmaMap *>(d_workspace);
+    int strips = 0, chunks = 0;
     for (int i = 0; i < count; ++i) {
         const fic_params *p = &params[i];
         int rc = fic_validate(widths[i], heights[i], p);
@@ -179,9 +238,18 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
         d.o_bits = p->o_bits;
         d.local_radius = p->local_radius;
         d.local_step = p->local_step;
+        d.boxw = box_width(bmax, W);
+        d.bmax = bmax;
+        d.map = d_maps + i;
+        rc = make_tma_map(&maps[(size_t)i], d_imgs[i], W, H, d.boxw, 2 * bmax);
+        if (rc) return rc;
+        d.chunk_base = chunks;
+        d.nchunks = (d.nstrips + 31) / 32;
         strips += d.nstrips;
+        chunks += d.nchunks;
     }
-    const size_t need = align_up(sizeof(EncDesc) * (size_t)count) + align_up(4 * (size_t)strips) + kAlign;
+    const EncLayout lay = enc_layout(count, (size_t)strips, (size_t)chunks);
+    const size_t need = lay.total;
     if (ws_bytes < need || (reinterpret_cast<uintptr_t>(d_workspace) & (kAlign - 1))) return FIC_ENOMEM;
     fic_plan *pl = new (std::nothrow) fic_plan();
     if (!pl) return FIC_ENOMEM;
@@ -192,12 +260,24 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
     pl->total_strips = strips;
     pl->ws = d_workspace;
     pl->ws_bytes = ws_bytes;
-    pl->d_enc = reinterpret_cast<EncDesc *>(w);
-    pl->status = reinterpret_cast<uint32_t *>(w + align_up(sizeof(EncDesc) * (size_t)count));
-    pl->ticket = reinterpret_cast<uint32_t *>(w + align_up(sizeof(EncDesc) * (size_t)count) + align_up(4 * (size_t)strips));
+    pl->d_enc = reinterpret_cast<EncDesc *>(w + lay.descs);
+    pl->status = reinterpret_cast<uint32_t *>(w + lay.pstatus);
+    pl->ticket = nullptr;
+    pl->total_chunks = chunks;
     pl->d_dec = nullptr;
-    cudaError_t e = cudaMemcpyAsync(pl->d_enc, h.data(), sizeof(EncDesc) * (size_t)count, cudaMemcpyHostToDevice,
+    {
+        fic_record *slots = reinterpret_cast<fic_record *>(w + lay.slots);
+        uint2 *stats = reinterpret_cast<uint2 *>(w + lay.stats);
+        for (int i = 0; i < count; ++i) {
+            h[(size_t)i].slots = slots + (size_t)h[(size_t)i].strip_base * 64;
+            h[(size_t)i].stats = stats + h[(size_t)i].strip_base;
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(w, maps.data(), sizeof(TmaMap) * (size_t)count, cudaMemcpyHostToDevice,
                                     static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pl->d_enc, h.data(), sizeof(EncDesc) * (size_t)count, cudaMemcpyHostToDevice,
+                            static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         delete pl;
         return FIC_ECUDA;
@@ -208,8 +288,8 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
 
 int fic_encode_plan_run(const fic_plan *pl, void *stream) {
     if (!pl || pl->kind != 0) return FIC_EBADPARAM;
-    return cuda_rc(launch_mns_encode(pl->bmax, pl->d_enc, pl->count, pl->total_strips, pl->status, pl->ticket,
-                                     static_cast<cudaStream_t>(stream)));
+    return cuda_rc(launch_mns_encode_slots(pl->bmax, pl->d_enc, pl->count, pl->total_strips, pl->total_chunks,
+                                           pl->status, static_cast<cudaStream_t>(stream)));
 }
 
 void fic_plan_destroy(fic_plan *pl) { delete pl; }
@@ -231,9 +311,13 @@ int fic_encode(const uint8_t *d_img, int width, int height, const fic_params *p,
     return fic_encode_batch(&d_img, &width, &height, 1, p, out, d_workspace, workspace_bytes, stream);
 }
 
+// Decoder workspace layout (each part 256-byte aligned): image descriptors,
+// one scratch iterate per image, per-strip transform tables.
+static size_t dec_head_bytes(int count) { return align_up(sizeof(DecDesc) * (size_t)count); }
+
 size_t fic_decode_workspace_bytes(int count, const int *widths, const int *heights) {
     if (count <= 0 || !widths || !heights) return 0;
-    size_t b = align_up(sizeof(DecDesc) * (size_t)count);
+    size_t b = dec_head_bytes(count);
     size_t strips = 0;
     for (int i = 0; i < count; ++i) {
         if (widths[i] <= 0 || heights[i] <= 0) return 0;
@@ -266,7 +350,7 @@ int fic_decode_plan_create(const fic_stream *sts, int count, uint8_t *const *d_o
     if (!pl) return FIC_ENOMEM;
     pl->hdec.resize((size_t)count);
     uint8_t *w = static_cast<uint8_t *>(d_workspace);
-    uint8_t *scratch = w + align_up(sizeof(DecDesc) * (size_t)count);
+    uint8_t *scratch = w + dec_head_bytes(count);
     int strips = 0;
     for (int i = 0; i < count; ++i) {
         const fic_stream *s = &sts[i];

@@ -98,122 +98,258 @@ __device__ __forceinline__ uint32_t fast_word(int c, int rr, int lg, int cc) {
     return (uint32_t)c | ((uint32_t)rr << 8) | ((uint32_t)lg << 16) | ((uint32_t)(cc & 0xff) << 24);
 }
 
+// Transform words of one strip (the lookup of every half-patch's transform
+// in the strip's records), written to the decode tables.
+template <int BMAX>
+__device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, int count, const int *s_base, int g,
+                                            uint4 *recs, uint8_t *keys, StripInfo *sinfo, uint4 *tfw, uint4 *tgw,
+                                            int lane) {
+    using G = DGeom<BMAX>;
+    constexpr int PC = G::PC;
+    const int pr = lane / PC, pc = lane % PC;
+    const int img = find_image_s(s_base, descs, count, g);
+    const DecDesc &D = descs[img];
+    const int W = D.W, H = D.H, tw = D.tw;
+    const int s = g - D.strip_base;
+    const int row = s / D.spr, sc = s - row * D.spr;
+    const int sy0 = row * BMAX, sx0 = sc * G::SW;
+    const int top0 = row * tw + sc * G::TOPS;
+    const int nvalid = min(G::TOPS, tw - sc * G::TOPS);
+    const int lane_top = (8 * pc) / BMAX;
+    const bool valid = lane_top < nvalid;
+    const int bmin = D.bmin;
+    const int cpt_side = BMAX / bmin, cpt = cpt_side * cpt_side;
+    const bool centred = (D.mode == FIC_NOSEARCH || D.mode == FIC_MNS);
+    const int ko1 = (1 << D.o_bits) - 1;
+    const int rx0 = clampi(sx0 - BMAX / 2, 0, W - 2 * BMAX);
+    const int xl = sx0 + (nvalid - 1) * BMAX;
+    const int rx1 = clampi(xl - BMAX / 2, 0, W - 2 * BMAX) + 2 * BMAX;
+    const int ax0 = rx0 & ~15, ax1 = (rx1 + 15) & ~15;
+    const int ry0 = clampi(sy0 - BMAX / 2, 0, H - 2 * BMAX);
+    const int c_base = ax0 >> 1, r_base = ry0 >> 1;
+
+    const uint32_t rbeg = D.tile_off[top0], rend = D.tile_off[top0 + nvalid];
+    const int nrec = min((int)(rend - rbeg), 64);
+    __syncwarp();
+    for (int i = lane; i < nrec; i += 32) {
+        const uint4 r = *reinterpret_cast<const uint4 *>(D.rec + rbeg + i);
+        recs[i] = r;
+        const int x = (int)(r.x & 0xffffu), y = (int)(r.x >> 16);
+        const int lt = x / BMAX - sc * G::TOPS;
+        keys[i] = (uint8_t)(lt * cpt + (int)dmorton3((x % BMAX) / bmin, (y % BMAX) / bmin));
+    }
+    __syncwarp();
+    uint32_t fw[2] = {0u, 0u}, gw[2] = {0u, 0u}, hw[2] = {0u, 0u};
+    int Ow[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!valid || nrec <= 0) continue;
+        const int px = 8 * pc + 4 * h, py = 4 * pr;  // in strip
+        const int tx = px - lane_top * BMAX;
+        const int key = lane_top * cpt + (int)dmorton3(tx / bmin, py / bmin);
+        int lo = 0, hi = nrec - 1;
+        while (lo < hi) {  // last record with keys[i] <= key
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int)keys[mid] <= key) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint4 r = recs[lo];
+        const int x = (int)(r.x & 0xffffu), y = (int)(r.x >> 16);
+        const int level = (int)(r.y & 0xffu), phase = (int)((r.y >> 8) & 0xffu);
+        const int k = (int)((r.y >> 16) & 0xffu), q = (int)(r.y >> 24);
+        const int B = BMAX >> (level - 1);
+        const int Oi = (510 * q + ko1) / (2 * ko1);
+        int t_x, t_y, t_lg, t_dx, t_dy, t_c, t_O, t_iso;
+        if (phase == 1) {
+            t_x = x;
+            t_y = y;
+            t_lg = 31 - __clz(B);
+            t_dx = (int)(r.w & 0xffffu);
+            t_dy = (int)(r.w >> 16);
+            t_c = contrast_code(k, D.s_bits);
+            t_O = Oi;
+            t_iso = (int)(r.z >> 24);
+        } else {
+            const int hb = B >> 1;
+            const int ax = sx0 + px, ay = sy0 + py;
+            const int sb = (ax - x >= hb ? 1 : 0) | (ay - y >= hb ? 2 : 0);
+            const int d0 = (int)(int8_t)(r.z & 0xffu), d1 = (int)(int8_t)((r.z >> 8) & 0xffu),
+                      d2 = (int)(int8_t)((r.z >> 16) & 0xffu);
+            const int O0 = Oi + d0, O1 = Oi + d1, O2 = Oi + d2;
+            const int O3 = 4 * Oi - (O0 + O1 + O2);  // eq. (1)
+            t_O = sb == 0 ? O0 : (sb == 1 ? O1 : (sb == 2 ? O2 : O3));
+            t_x = x + (sb & 1) * hb;
+            t_y = y + (sb >> 1) * hb;
+            t_lg = 31 - __clz(hb);
+            t_dx = centred_origin(t_x, hb, W);
+            t_dy = centred_origin(t_y, hb, H);
+            t_c = phase2_code(level, (k >> sb) & 1);
+            t_iso = 0;
+        }
+        const int u0 = sx0 + px - t_x, v0 = sy0 + py - t_y;
+        const int c = centred ? (t_dx >> 1) + u0 - c_base : 0;
+        const int rr = centred ? (t_dy >> 1) + v0 - r_base : 0;
+        fw[h] = fast_word(c, rr, t_lg, t_c);
+        Ow[h] = t_O;
+        gw[h] = (uint32_t)t_dx | ((uint32_t)t_dy << 16);
+        hw[h] = (uint32_t)u0 | ((uint32_t)v0 << 8) | ((uint32_t)t_iso << 16);
+    }
+    tfw[(size_t)g * 32 + lane] = make_uint4(fw[0], (uint32_t)Ow[0], fw[1], (uint32_t)Ow[1]);
+    if (!centred) tgw[(size_t)g * 32 + lane] = make_uint4(gw[0], hw[0], gw[1], hw[1]);
+    if (lane == 0) {
+        StripInfo si;
+        si.buf[0] = D.buf[0];
+        si.buf[1] = D.buf[1];
+        si.W = W;
+        si.sxy = (uint32_t)sx0 | ((uint32_t)sy0 << 16);
+        si.axy = (uint32_t)ax0 | ((uint32_t)ry0 << 16);
+        si.misc = (uint32_t)((ax1 - ax0) >> 4) | ((uint32_t)nvalid << 8) | ((centred ? 1u : 0u) << 16);
+        sinfo[g] = si;
+    }
+}
+
 template <int BMAX>
 __global__ void __launch_bounds__(kDecWarps * 32)
     decode_setup_kernel(const DecDesc *__restrict__ descs, int count, int total_strips, StripInfo *sinfo,
                         uint4 *tfw, uint4 *tgw) {
-    using G = DGeom<BMAX>;
-    constexpr int PC = G::PC;
     __shared__ int s_base[kImgTable];
     __shared__ uint4 s_recs[kDecWarps][64];
     __shared__ uint8_t s_keys[kDecWarps][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint4 *recs = s_recs[warp];
-    uint8_t *keys = s_keys[warp];
-    const int pr = lane / PC, pc = lane % PC;
     if (count <= kImgTable)
         for (int i = threadIdx.x; i < count; i += blockDim.x) s_base[i] = descs[i].strip_base;
     __syncthreads();
     const int gwarps = gridDim.x * kDecWarps;
-    for (int g = blockIdx.x * kDecWarps + warp; g < total_strips; g += gwarps) {
-        const int img = find_image_s(s_base, descs, count, g);
-        const DecDesc &D = descs[img];
-        const int W = D.W, H = D.H, tw = D.tw;
-        const int s = g - D.strip_base;
-        const int row = s / D.spr, sc = s - row * D.spr;
-        const int sy0 = row * BMAX, sx0 = sc * G::SW;
-        const int top0 = row * tw + sc * G::TOPS;
-        const int nvalid = min(G::TOPS, tw - sc * G::TOPS);
-        const int lane_top = (8 * pc) / BMAX;
-        const bool valid = lane_top < nvalid;
-        const int bmin = D.bmin;
-        const int cpt_side = BMAX / bmin, cpt = cpt_side * cpt_side;
-        const bool centred = (D.mode == FIC_NOSEARCH || D.mode == FIC_MNS);
-        const int ko1 = (1 << D.o_bits) - 1;
-        const int rx0 = clampi(sx0 - BMAX / 2, 0, W - 2 * BMAX);
-        const int xl = sx0 + (nvalid - 1) * BMAX;
-        const int rx1 = clampi(xl - BMAX / 2, 0, W - 2 * BMAX) + 2 * BMAX;
-        const int ax0 = rx0 & ~15, ax1 = (rx1 + 15) & ~15;
-        const int ry0 = clampi(sy0 - BMAX / 2, 0, H - 2 * BMAX);
-        const int c_base = ax0 >> 1, r_base = ry0 >> 1;
+    for (int g = blockIdx.x * kDecWarps + warp; g < total_strips; g += gwarps)
+        setup_strip<BMAX>(descs, count, s_base, g, s_recs[warp], s_keys[warp], sinfo, tfw, tgw, lane);
+}
 
-        const uint32_t rbeg = D.tile_off[top0], rend = D.tile_off[top0 + nvalid];
-        const int nrec = min((int)(rend - rbeg), 64);
-        __syncwarp();
-        for (int i = lane; i < nrec; i += 32) {
-            const uint4 r = *reinterpret_cast<const uint4 *>(D.rec + rbeg + i);
-            recs[i] = r;
-            const int x = (int)(r.x & 0xffffu), y = (int)(r.x >> 16);
-            const int lt = x / BMAX - sc * G::TOPS;
-            keys[i] = (uint8_t)(lt * cpt + (int)dmorton3((x % BMAX) / bmin, (y % BMAX) / bmin));
+// First iteration from x0 = 128: d4 - mean d4 = 0, every pixel is its
+// transform's luminance (clamped).
+template <int BMAX>
+__device__ __forceinline__ void first_strip(const StripInfo &si, uint4 tf, int src_sel, int lane) {
+    using G = DGeom<BMAX>;
+    constexpr int PC = G::PC;
+    const int pr = lane / PC, pc = lane % PC;
+    const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
+    const int nvalid = (int)((si.misc >> 8) & 0xffu);
+    if ((8 * pc) / BMAX >= nvalid) return;
+    uint8_t *out = const_cast<uint8_t *>(si.buf[src_sel ^ 1]) + (size_t)(sy0 + 4 * pr) * si.W + sx0 + 8 * pc;
+    const int O0 = (int)tf.y, O1 = (int)tf.w;
+    const uint32_t w0 = pack_sat_u8(O0, O0, pack_sat_u8(O0, O0, 0u));
+    const uint32_t w1 = pack_sat_u8(O1, O1, pack_sat_u8(O1, O1, 0u));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(out + (size_t)i * si.W) = make_uint2(w0, w1);
+}
+
+// One strip of one iteration after the first; for centred domains the
+// decimated window of the previous iterate is already staged in d4e.
+template <int BMAX>
+__device__ __forceinline__ void iterate_strip(const StripInfo &si, uint4 tf, const uint4 *__restrict__ tgw_row,
+                                              int src_sel, const uint32_t *d4e, int lane) {
+    using G = DGeom<BMAX>;
+    constexpr int PC = G::PC, NP = G::NP;
+    const int pr = lane / PC, pc = lane % PC;
+    const unsigned FULL = 0xffffffffu;
+    const int W = si.W;
+    const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
+    const int nvalid = (int)((si.misc >> 8) & 0xffu);
+    const bool centred = (si.misc >> 16) & 1u;
+    const bool valid = (8 * pc) / BMAX < nvalid;
+    const uint8_t *src = si.buf[src_sel];
+    uint8_t *out = const_cast<uint8_t *>(si.buf[src_sel ^ 1]) + (size_t)(sy0 + 4 * pr) * W + sx0 + 8 * pc;
+    const uint32_t fw[2] = {tf.x, tf.z};
+    const int Ov[2] = {(int)tf.y, (int)tf.w};
+
+    // ---- decimated domain values of the half-patches (16 each) and partial Sd4
+    uint32_t dv[2][4][2];  // [half][row][pair]
+    int part[2] = {0, 0};
+    int lg[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        lg[h] = (int)((fw[h] >> 16) & 0xffu);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dv[h][i][0] = dv[h][i][1] = 0u;
+        if (!valid) continue;
+        if (centred) {
+            const int c = (int)(fw[h] & 0xffu), rr = (int)((fw[h] >> 8) & 0xffu);
+            const uint32_t *base = d4e + rr * NP + (c >> 1);
+            const bool odd = c & 1;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t e0 = base[i * NP], e1 = base[i * NP + 1];
+                if (odd) {
+                    const uint32_t e2 = base[i * NP + 2];
+                    dv[h][i][0] = __funnelshift_r(e0, e1, 16);
+                    dv[h][i][1] = __funnelshift_r(e1, e2, 16);
+                } else {
+                    dv[h][i][0] = e0;
+                    dv[h][i][1] = e1;
+                }
+            }
+        } else {
+            const uint4 gg = tgw_row[lane];
+            const uint32_t gd = h ? gg.z : gg.x, ge = h ? gg.w : gg.y;
+            const int dx = (int)(gd & 0xffffu), dy = (int)(gd >> 16);
+            const int u0 = (int)(ge & 0xffu), v0 = (int)((ge >> 8) & 0xffu), iso = (int)((ge >> 16) & 0xffu);
+            const int B = 1 << lg[h];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uint32_t vals[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    int su, sv;
+                    iso_src(iso, B, u0 + e, v0 + i, su, sv);
+                    const uint8_t *p = src + (size_t)(dy + 2 * sv) * W + dx + 2 * su;
+                    vals[e] = (uint32_t)p[0] + p[1] + p[W] + p[W + 1];
+                }
+                dv[h][i][0] = vals[0] | (vals[1] << 16);
+                dv[h][i][1] = vals[2] | (vals[3] << 16);
+            }
         }
-        __syncwarp();
-        uint32_t fw[2] = {0u, 0u}, gw[2] = {0u, 0u}, hw[2] = {0u, 0u};
-        int Ow[2] = {0, 0};
+        uint32_t pk = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pk += dv[h][i][0] + dv[h][i][1];
+        part[h] = (int)((pk & 0xffffu) + (pk >> 16));
+    }
+    // ---- Sd4 per transform: halves of one lane first (side >= 8), then the
+    // lane group of the transform; every lane runs the same shuffles
+    int sd4[2];
+    {
+        const bool big = lg[0] >= 3;  // a transform of side >= 8 covers both halves
+        const int B = 1 << lg[0];
+        const int gx = big ? B / 8 : 1, gy = big ? B / 4 : 1;
+        int v = part[0] + part[1];
+#pragma unroll
+        for (int m = 1; m < 4; m <<= 1) {
+            const int o = __shfl_xor_sync(FULL, v, m);
+            if (m < gx) v += o;
+        }
+#pragma unroll
+        for (int m = 1; m < 8; m <<= 1) {
+            const int o = __shfl_xor_sync(FULL, v, (m * PC) & 31);
+            if (m < gy && m * PC < 32) v += o;
+        }
+        sd4[0] = big ? v : part[0];
+        sd4[1] = big ? v : part[1];
+    }
+
+    // ---- output pixels: p = (c d4 + K) >> 9 with K = floor((512 n O - c Sd4 + 256 n) / n)
+    if (valid) {
+        int K[2], cb0[2], cb1[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            if (!valid || nrec <= 0) continue;
-            const int px = 8 * pc + 4 * h, py = 4 * pr;  // in strip
-            const int tx = px - lane_top * BMAX;
-            const int key = lane_top * cpt + (int)dmorton3(tx / bmin, py / bmin);
-            int lo = 0, hi = nrec - 1;
-            while (lo < hi) {  // last record with keys[i] <= key
-                const int mid = (lo + hi + 1) >> 1;
-                if ((int)keys[mid] <= key) lo = mid;
-                else hi = mid - 1;
-            }
-            const uint4 r = recs[lo];
-            const int x = (int)(r.x & 0xffffu), y = (int)(r.x >> 16);
-            const int level = (int)(r.y & 0xffu), phase = (int)((r.y >> 8) & 0xffu);
-            const int k = (int)((r.y >> 16) & 0xffu), q = (int)(r.y >> 24);
-            const int B = BMAX >> (level - 1);
-            const int Oi = (510 * q + ko1) / (2 * ko1);
-            int t_x, t_y, t_lg, t_dx, t_dy, t_c, t_O, t_iso;
-            if (phase == 1) {
-                t_x = x;
-                t_y = y;
-                t_lg = 31 - __clz(B);
-                t_dx = (int)(r.w & 0xffffu);
-                t_dy = (int)(r.w >> 16);
-                t_c = contrast_code(k, D.s_bits);
-                t_O = Oi;
-                t_iso = (int)(r.z >> 24);
-            } else {
-                const int hb = B >> 1;
-                const int ax = sx0 + px, ay = sy0 + py;
-                const int sb = (ax - x >= hb ? 1 : 0) | (ay - y >= hb ? 2 : 0);
-                const int d0 = (int)(int8_t)(r.z & 0xffu), d1 = (int)(int8_t)((r.z >> 8) & 0xffu),
-                          d2 = (int)(int8_t)((r.z >> 16) & 0xffu);
-                const int O0 = Oi + d0, O1 = Oi + d1, O2 = Oi + d2;
-                const int O3 = 4 * Oi - (O0 + O1 + O2);  // eq. (1)
-                t_O = sb == 0 ? O0 : (sb == 1 ? O1 : (sb == 2 ? O2 : O3));
-                t_x = x + (sb & 1) * hb;
-                t_y = y + (sb >> 1) * hb;
-                t_lg = 31 - __clz(hb);
-                t_dx = centred_origin(t_x, hb, W);
-                t_dy = centred_origin(t_y, hb, H);
-                t_c = phase2_code(level, (k >> sb) & 1);
-                t_iso = 0;
-            }
-            const int u0 = sx0 + px - t_x, v0 = sy0 + py - t_y;
-            const int c = centred ? (t_dx >> 1) + u0 - c_base : 0;
-            const int rr = centred ? (t_dy >> 1) + v0 - r_base : 0;
-            fw[h] = fast_word(c, rr, t_lg, t_c);
-            Ow[h] = t_O;
-            gw[h] = (uint32_t)t_dx | ((uint32_t)t_dy << 16);
-            hw[h] = (uint32_t)u0 | ((uint32_t)v0 << 8) | ((uint32_t)t_iso << 16);
+            const int lg2n = 2 * lg[h];
+            const int c = (int)(int8_t)(fw[h] >> 24);
+            K[h] = (Ov[h] * (1 << (9 + lg2n)) + (1 << (8 + lg2n)) - c * sd4[h]) >> lg2n;
+            cb0[h] = (int)(fw[h] >> 24);
+            cb1[h] = (int)((fw[h] >> 24) << 8);
         }
-        tfw[(size_t)g * 32 + lane] = make_uint4(fw[0], (uint32_t)Ow[0], fw[1], (uint32_t)Ow[1]);
-        if (!centred) tgw[(size_t)g * 32 + lane] = make_uint4(gw[0], hw[0], gw[1], hw[1]);
-        if (lane == 0) {
-            StripInfo si;
-            si.buf[0] = D.buf[0];
-            si.buf[1] = D.buf[1];
-            si.W = W;
-            si.sxy = (uint32_t)sx0 | ((uint32_t)sy0 << 16);
-            si.axy = (uint32_t)ax0 | ((uint32_t)ry0 << 16);
-            si.misc = (uint32_t)((ax1 - ax0) >> 4) | ((uint32_t)nvalid << 8) | ((centred ? 1u : 0u) << 16);
-            sinfo[g] = si;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t w0 = row_pixels(dv[0][i][0], dv[0][i][1], cb0[0], cb1[0], K[0]);
+            const uint32_t w1 = row_pixels(dv[1][i][0], dv[1][i][1], cb0[1], cb1[1], K[1]);
+            *reinterpret_cast<uint2 *>(out + (size_t)i * W) = make_uint2(w0, w1);
         }
     }
 }
@@ -223,135 +359,23 @@ __global__ void __launch_bounds__(kDecWarps * 32, 4)
     decode_iter_kernel(const StripInfo *__restrict__ sinfo, const uint4 *__restrict__ tfw,
                        const uint4 *__restrict__ tgw, int total_strips, int src_sel, int first) {
     using G = DGeom<BMAX>;
-    constexpr int PC = G::PC, NP = G::NP;
-    extern __shared__ __align__(16) uint32_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *d4e = smem + warp * G::WORDS;
-    const int pr = lane / PC, pc = lane % PC;
-    const unsigned FULL = 0xffffffffu;
+    uint32_t *d4e = reinterpret_cast<uint32_t *>(smem) + warp * G::WORDS;
     const int gwarps = gridDim.x * kDecWarps;
-
     for (int g = blockIdx.x * kDecWarps + warp; g < total_strips; g += gwarps) {
         const StripInfo si = sinfo[g];
         const uint4 tf = tfw[(size_t)g * 32 + lane];
-        const int W = si.W;
-        const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
-        const int nvalid = (int)((si.misc >> 8) & 0xffu);
-        const bool centred = (si.misc >> 16) & 1u;
-        const bool valid = (8 * pc) / BMAX < nvalid;
-        const uint8_t *src = si.buf[src_sel];
-        uint8_t *dst = const_cast<uint8_t *>(si.buf[src_sel ^ 1]);
-        uint8_t *out = dst + (size_t)(sy0 + 4 * pr) * W + sx0 + 8 * pc;
-        const uint32_t fw[2] = {tf.x, tf.z};
-        const int Ov[2] = {(int)tf.y, (int)tf.w};
-
         if (first) {
-            // x0 = 128 everywhere: d4 - mean d4 = 0, every pixel is its luminance
-            if (valid) {
-                const uint32_t w0 = pack_sat_u8(Ov[0], Ov[0], pack_sat_u8(Ov[0], Ov[0], 0u));
-                const uint32_t w1 = pack_sat_u8(Ov[1], Ov[1], pack_sat_u8(Ov[1], Ov[1], 0u));
-#pragma unroll
-                for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(out + (size_t)i * W) = make_uint2(w0, w1);
-            }
+            first_strip<BMAX>(si, tf, src_sel, lane);
             continue;
         }
         __syncwarp();
-        if (centred)
-            stage_window<BMAX, G::UPR, NP>(src, W, (int)(si.axy >> 16), (int)(si.axy & 0xffffu), (int)(si.misc & 0xffu),
-                                           d4e, lane);
+        if ((si.misc >> 16) & 1u)
+            stage_window<BMAX, G::UPR, G::NP>(si.buf[src_sel], si.W, (int)(si.axy >> 16), (int)(si.axy & 0xffffu),
+                                              (int)(si.misc & 0xffu), d4e, lane);
         __syncwarp();
-
-        // ---- decimated domain values of the half-patches (16 each) and partial Sd4
-        uint32_t dv[2][4][2];  // [half][row][pair]
-        int part[2] = {0, 0};
-        int lg[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            lg[h] = (int)((fw[h] >> 16) & 0xffu);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) dv[h][i][0] = dv[h][i][1] = 0u;
-            if (!valid) continue;
-            if (centred) {
-                const int c = (int)(fw[h] & 0xffu), rr = (int)((fw[h] >> 8) & 0xffu);
-                const uint32_t *base = d4e + rr * NP + (c >> 1);
-                const bool odd = c & 1;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const uint32_t e0 = base[i * NP], e1 = base[i * NP + 1];
-                    if (odd) {
-                        const uint32_t e2 = base[i * NP + 2];
-                        dv[h][i][0] = __funnelshift_r(e0, e1, 16);
-                        dv[h][i][1] = __funnelshift_r(e1, e2, 16);
-                    } else {
-                        dv[h][i][0] = e0;
-                        dv[h][i][1] = e1;
-                    }
-                }
-            } else {
-                const uint4 gg = tgw[(size_t)g * 32 + lane];
-                const uint32_t gd = h ? gg.z : gg.x, ge = h ? gg.w : gg.y;
-                const int dx = (int)(gd & 0xffffu), dy = (int)(gd >> 16);
-                const int u0 = (int)(ge & 0xffu), v0 = (int)((ge >> 8) & 0xffu), iso = (int)((ge >> 16) & 0xffu);
-                const int B = 1 << lg[h];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    uint32_t vals[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        int su, sv;
-                        iso_src(iso, B, u0 + e, v0 + i, su, sv);
-                        const uint8_t *p = src + (size_t)(dy + 2 * sv) * W + dx + 2 * su;
-                        vals[e] = (uint32_t)p[0] + p[1] + p[W] + p[W + 1];
-                    }
-                    dv[h][i][0] = vals[0] | (vals[1] << 16);
-                    dv[h][i][1] = vals[2] | (vals[3] << 16);
-                }
-            }
-            uint32_t pk = 0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) pk += dv[h][i][0] + dv[h][i][1];
-            part[h] = (int)((pk & 0xffffu) + (pk >> 16));
-        }
-        // ---- Sd4 per transform: halves of one lane first (side >= 8), then the
-        // lane group of the transform; every lane runs the same shuffles
-        int sd4[2];
-        {
-            const bool big = lg[0] >= 3;  // a transform of side >= 8 covers both halves
-            const int B = 1 << lg[0];
-            const int gx = big ? B / 8 : 1, gy = big ? B / 4 : 1;
-            int v = part[0] + part[1];
-#pragma unroll
-            for (int m = 1; m < 4; m <<= 1) {
-                const int o = __shfl_xor_sync(FULL, v, m);
-                if (m < gx) v += o;
-            }
-#pragma unroll
-            for (int m = 1; m < 8; m <<= 1) {
-                const int o = __shfl_xor_sync(FULL, v, (m * PC) & 31);
-                if (m < gy && m * PC < 32) v += o;
-            }
-            sd4[0] = big ? v : part[0];
-            sd4[1] = big ? v : part[1];
-        }
-
-        // ---- output pixels: p = (c d4 + K) >> 9 with K = floor((512 n O - c Sd4 + 256 n) / n)
-        if (valid) {
-            int K[2], cb0[2], cb1[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int lg2n = 2 * lg[h];
-                const int c = (int)(int8_t)(fw[h] >> 24);
-                K[h] = (Ov[h] * (1 << (9 + lg2n)) + (1 << (8 + lg2n)) - c * sd4[h]) >> lg2n;
-                cb0[h] = (int)(fw[h] >> 24);
-                cb1[h] = (int)((fw[h] >> 24) << 8);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint32_t w0 = row_pixels(dv[0][i][0], dv[0][i][1], cb0[0], cb1[0], K[0]);
-                const uint32_t w1 = row_pixels(dv[1][i][0], dv[1][i][1], cb0[1], cb1[1], K[1]);
-                *reinterpret_cast<uint2 *>(out + (size_t)i * W) = make_uint2(w0, w1);
-            }
-        }
+        iterate_strip<BMAX>(si, tf, tgw + (size_t)g * 32, src_sel, d4e, lane);
     }
 }
 
@@ -373,6 +397,7 @@ static int grid_for(const void *fn, size_t smem, int &cache) {
     return cache;
 }
 
+// Decode: the table setup kernel, then one launch per iteration.
 template <int BMAX>
 static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, void *tables, int iters,
                              cudaStream_t st) {

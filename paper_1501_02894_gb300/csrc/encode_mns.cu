@@ -21,11 +21,14 @@
 //     a block (lock-step, no divergence between blocks);
 //   * a level is skipped as soon as no block of the strip needs it;
 //   * leaves are ranked in the canonical order by a 64-bit warp mask and
-//     written with one 16-byte store each; the strip's offset in the stream
-//     comes from a decoupled look-back over the strips of the image (bounded
-//     spin), so the stream is packed in the same launch.
-// The grid is persistent: each warp takes strips from an atomic ticket in
-// stream order, which also guarantees progress of the look-back.
+//     written with one 16-byte store each, into the strip's slot of the
+//     workspace; pack_kernel (pack.cu) compacts the slots into the stream.
+// The grid is persistent and strips are assigned statically; each warp's
+// next window is fetched by TMA (cp.async.bulk.tensor + mbarrier) while the
+// current strip is encoded.  A second variant (used by the allocation-free
+// entry point) takes strips from an atomic ticket in stream order and packs
+// the stream in place with a decoupled look-back over the strips (bounded
+// spin), so its only scratch is one status word per strip.
 #include "fic_internal.cuh"
 
 namespace fic {
@@ -42,6 +45,7 @@ struct Geom {
 };
 
 constexpr int kWarps = 8;
+constexpr int kSlotRecords = 64;  // records a 1024-pixel strip can hold (4x4 leaves)
 constexpr uint32_t kAgg = 1u << 30, kIncl = 2u << 30, kValMask = (1u << 30) - 1;
 
 // Result of the phase-1 fit of one block.
@@ -236,31 +240,80 @@ struct Code {
     bool pass;
 };
 
-template <int BMAX>
+// SLOTS = true: strips are assigned statically (grid stride) and every strip
+//   writes its records to a fixed slot of the workspace; pack_kernel then
+//   compacts the canonical stream.  No ordering between warps.
+// SLOTS = false: strips come from an atomic ticket in stream order and the
+//   stream is packed in place by a decoupled look-back (needs only one status
+//   word per strip of scratch).
+template <int BMAX, bool SLOTS>
 __global__ void __launch_bounds__(kWarps * 32, 3)
     mns_encode_kernel(const EncDesc *__restrict__ descs, int count, int total_strips,
-                      uint32_t *__restrict__ status, uint32_t *__restrict__ ticket) {
+                      uint32_t *__restrict__ status, uint32_t *__restrict__ ticket, int total_chunks) {
     using G = Geom<BMAX>;
     constexpr int PC = G::PC, NP = G::NP;
     constexpr int UPR = BMAX == 32 ? 4 : (BMAX == 16 ? 8 : 16);
-    extern __shared__ __align__(16) uint32_t smem[];
+    using BX = WinBox<BMAX>;
+    constexpr int RAWB = BX::W * BX::H;  // bytes of the staged window (a multiple of 128)
+    extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_base[kImgTable];
+    __shared__ __align__(8) uint64_t s_bar[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *d4e = smem + warp * G::WORDS;
+    // TMA destinations need 128-byte alignment in the shared window
+    uint8_t *const smem_a = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
+    uint8_t *raw = smem_a + warp * (RAWB + G::WORDS * 4);
+    uint32_t *d4e = reinterpret_cast<uint32_t *>(raw + RAWB);
+    uint64_t *bar = &s_bar[warp];
     const int pr = lane / PC, pc = lane % PC;
     const unsigned FULL = 0xffffffffu;
     if (count <= kImgTable)
         for (int i = threadIdx.x; i < count; i += blockDim.x) s_base[i] = descs[i].strip_base;
+    if (SLOTS) {
+        // clear the pack kernel's look-back words (it runs after this kernel)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total_chunks; i += gridDim.x * blockDim.x)
+            status[i] = 0u;
+    }
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
     __syncthreads();
 
-    int g_next = 0;
-    if (lane == 0) g_next = (int)atomicAdd(ticket, 1u);
-    g_next = __shfl_sync(FULL, g_next, 0);
+    // Window of strip gi: one TMA box load into `raw`, signalled on `bar`.
+    // Issued by lane 0 only; a strip's window is fetched while the previous
+    // strip is being encoded.
+    auto issue_window = [&](int gi) {
+        const int im = find_image_s(s_base, descs, count, gi);
+        const EncDesc &E = descs[im];
+        const int si = gi - E.strip_base;
+        const int rw_ = si / E.spr, sc_ = si - rw_ * E.spr;
+        const int sy = rw_ * BMAX, sx = sc_ * G::SW;
+        const int nv = min(G::TOPS, E.tw - sc_ * G::TOPS);
+        const int x0 = clampi(sx - BMAX / 2, 0, E.W - 2 * BMAX) & ~15;
+        const int y0 = clampi(sy - BMAX / 2, 0, E.H - 2 * BMAX);
+        (void)nv;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, (uint32_t)(E.boxw * BX::H));
+        tma_load_2d(raw, E.map, x0, y0, bar);
+    };
+
+    uint32_t phase = 0;
+    const int gstep = gridDim.x * kWarps;
+    int g = 0, g_next = 0;
+    if (SLOTS) {
+        g = blockIdx.x * kWarps + warp;
+        g_next = g + gstep;
+        if (lane == 0 && g < total_strips) issue_window(g);
+    } else {
+        if (lane == 0) {
+            g = (int)atomicAdd(ticket, 1u);
+            if (g < total_strips) issue_window(g);
+            g_next = (int)atomicAdd(ticket, 1u);
+        }
+        g = __shfl_sync(FULL, g, 0);
+    }
     for (;;) {
-        const int g = g_next;
         if (g >= total_strips) break;
-        // fetch the following ticket now; its latency hides behind this strip
-        if (lane == 0) g_next = (int)atomicAdd(ticket, 1u);
         const int img = find_image_s(s_base, descs, count, g);
         const EncDesc &D = descs[img];
         const int W = D.W, H = D.H, tw = D.tw;
@@ -276,22 +329,39 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
         const uint32_t magic = (uint32_t)((0x100000000ULL + 2 * ko1 - 1) / (2 * ko1));
         const float qscale = (float)ko1 / 255.f;
         const bool ph2 = (D.mode == FIC_MNS) && D.phase2;
-
-        // ---- the lane's range pixels (4 rows x 8), issued first
-        uint2 rw[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            rw[i] = valid ? __ldg(reinterpret_cast<const uint2 *>(D.img + (size_t)(sy0 + 4 * pr + i) * W + sx0 + 8 * pc))
-                          : make_uint2(0u, 0u);
-        // ---- decimated domain window of the strip -> shared memory
+        const int pitch = D.boxw;
         const int rx0 = clampi(sx0 - BMAX / 2, 0, W - 2 * BMAX);
         const int xl = sx0 + (nvalid - 1) * BMAX;
         const int rx1 = clampi(xl - BMAX / 2, 0, W - 2 * BMAX) + 2 * BMAX;
         const int ax0 = rx0 & ~15, ax1 = (rx1 + 15) & ~15;
         const int ry0 = clampi(sy0 - BMAX / 2, 0, H - 2 * BMAX);
         const int c_base = ax0 >> 1, r_base = ry0 >> 1;
+
+        // ---- wait for the window (bounded), then the range pixels and the
+        // decimated pairs, both read from the staged window
+        const bool arrived = mbar_wait(bar, phase, kMbarLimit);
+        phase ^= 1u;
+        if (!__all_sync(FULL, arrived)) {
+            if (lane == 0) {
+                if (SLOTS) D.stats[s] = make_uint2(0u, 0x80000000u);  // no records, error flag
+                else raise_error(D.info, FIC_DEVERR_TIMEOUT);
+            }
+            mbar_wait(bar, phase ^ 1u, kMbarLimit);  // let a late copy land before leaving
+            return;
+        }
+        uint2 rw[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            rw[i] = valid ? *reinterpret_cast<const uint2 *>(raw + (sy0 + 4 * pr + i - ry0) * pitch + sx0 + 8 * pc - ax0)
+                          : make_uint2(0u, 0u);
+        stage_window_smem<BMAX, UPR, NP>(raw, pitch, (ax1 - ax0) >> 4, d4e, lane);
         __syncwarp();
-        stage_window<BMAX, UPR, NP>(D.img, W, ry0, ax0, (ax1 - ax0) >> 4, d4e, lane);
+        // the window buffer is free: fetch the next strip's window now
+        if (lane == 0) {
+            if (g_next < total_strips) issue_window(g_next);
+        }
+        int g_after = g_next + gstep;
+        if (!SLOTS && lane == 0) g_after = (int)atomicAdd(ticket, 1u);
         int sr_h[2] = {0, 0}, srr_h[2] = {0, 0};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -300,7 +370,6 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
             srr_h[0] += (int)__dp4a(rw[i].x, rw[i].x, 0u);
             srr_h[1] += (int)__dp4a(rw[i].y, rw[i].y, 0u);
         }
-        __syncwarp();
 
         // ---- quadtree, level by level
         Leaf leaf[2];
@@ -493,6 +562,27 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
         const uint32_t mhi = __reduce_or_sync(FULL, (uint32_t)(mine >> 32));
         const unsigned long long mask = ((unsigned long long)mhi << 32) | mlo;
         const int cnt = __popcll(mask);
+        if (SLOTS) {
+            // records to the strip's slot; counts, fits and per-top offsets
+            // inside the strip for pack_kernel
+            fic_record *slot = D.slots + (size_t)s * kSlotRecords;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (leaf[h].pos < 0) continue;
+                const int idx = __popcll(mask & ((1ull << leaf[h].pos) - 1ull));
+                *reinterpret_cast<uint4 *>(slot + idx) = make_uint4(leaf[h].w0, leaf[h].w1, leaf[h].w2, leaf[h].w3);
+            }
+            const unsigned ftot = __reduce_add_sync(FULL, fits);
+            splitbits = group_or<PC>(splitbits, BMAX / 8, BMAX / 4);
+            if (valid && (8 * pc) % BMAX == 0 && pr == 0) {
+                D.split[top0 + lane_top] = splitbits;
+                D.tile_off[top0 + lane_top] = (uint32_t)__popcll(mask & ((1ull << (lane_top * cpt)) - 1ull));
+            }
+            if (lane == 0) D.stats[s] = make_uint2((uint32_t)cnt, ftot & 0x7fffffffu);
+            g = g_next;
+            g_next = g_after;
+            continue;
+        }
         // decoupled look-back, 32 predecessors per round (one per lane)
         uint32_t prefix = 0;
         int ok = 1;
@@ -527,11 +617,14 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
                 else raise_error(D.info, FIC_DEVERR_TIMEOUT);
             }
         }
-        g_next = __shfl_sync(FULL, g_next, 0);
         const unsigned ftot = __reduce_add_sync(FULL, fits);
         if (lane == 0 && ftot)
             atomicAdd(reinterpret_cast<unsigned long long *>(D.info + FIC_INFO_FITS_LO), (unsigned long long)ftot);
-        if (!ok) continue;
+        if (!ok) {
+            g = __shfl_sync(FULL, g_next, 0);
+            g_next = g_after;
+            continue;
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (leaf[h].pos < 0) continue;
@@ -552,10 +645,12 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
             D.tile_off[D.tw * D.th] = prefix + (uint32_t)cnt;
             D.info[FIC_INFO_RECORDS] = prefix + (uint32_t)cnt;
         }
+        g = __shfl_sync(FULL, g_next, 0);
+        g_next = g_after;
     }
 }
 
-// Zero the look-back state, the ticket and every stream's info block.
+// Zero the look-back (or pack) state, the ticket and every stream's info block.
 __global__ void encode_init_kernel(const EncDesc *__restrict__ descs, int count, uint32_t *status,
                                    int total_strips, uint32_t *ticket) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -566,50 +661,75 @@ __global__ void encode_init_kernel(const EncDesc *__restrict__ descs, int count,
 }
 
 size_t mns_smem_bytes(int bmax) {
-    int words = bmax == 32 ? Geom<32>::WORDS : (bmax == 16 ? Geom<16>::WORDS : Geom<8>::WORDS);
-    return (size_t)kWarps * words * sizeof(uint32_t);
+    const size_t per = bmax == 32 ? WinBox<32>::W * WinBox<32>::H + Geom<32>::WORDS * 4
+                     : bmax == 16 ? WinBox<16>::W * WinBox<16>::H + Geom<16>::WORDS * 4
+                                  : WinBox<8>::W * WinBox<8>::H + Geom<8>::WORDS * 4;
+    return (size_t)kWarps * per + 128;  // + alignment slack
 }
 
 int mns_strip_width(int bmax) { return 1024 / bmax; }
 
-template <int BMAX>
+template <int BMAX, bool SLOTS>
 static cudaError_t launch_t(const EncDesc *descs, int count, int total_strips, uint32_t *status,
-                            uint32_t *ticket, cudaStream_t st) {
+                            uint32_t *ticket, int total_chunks, cudaStream_t st) {
     static int grid_cache = 0;
     const size_t smem = mns_smem_bytes(BMAX);
     if (grid_cache == 0) {
-        cudaError_t e = cudaFuncSetAttribute(mns_encode_kernel<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(mns_encode_kernel<BMAX, SLOTS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mns_encode_kernel<BMAX>, kWarps * 32, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mns_encode_kernel<BMAX, SLOTS>, kWarps * 32, smem);
         grid_cache = sms * (per > 0 ? per : 1);
     }
     const int need = (total_strips + kWarps - 1) / kWarps;
     const int grid = need < grid_cache ? need : grid_cache;
-    mns_encode_kernel<BMAX><<<grid, kWarps * 32, smem, st>>>(descs, count, total_strips, status, ticket);
+    mns_encode_kernel<BMAX, SLOTS><<<grid, kWarps * 32, smem, st>>>(descs, count, total_strips, status, ticket,
+                                                                    total_chunks);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int total_strips,
-                              uint32_t *status, uint32_t *ticket, cudaStream_t st) {
+static cudaError_t launch_init(const EncDesc *d_descs, int count, int nstatus, uint32_t *status, uint32_t *ticket,
+                               cudaStream_t st) {
     const int threads = 256;
-    int blocks = (total_strips + threads - 1) / threads;
+    int blocks = (nstatus + threads - 1) / threads;
     int b2 = (count * FIC_INFO_WORDS + threads - 1) / threads;
     if (b2 > blocks) blocks = b2;
     if (blocks < 1) blocks = 1;
     if (blocks > 1024) blocks = 1024;
-    encode_init_kernel<<<blocks, threads, 0, st>>>(d_descs, count, status, total_strips, ticket);
-    cudaError_t e = cudaGetLastError();
+    encode_init_kernel<<<blocks, threads, 0, st>>>(d_descs, count, status, nstatus, ticket);
+    return cudaGetLastError();
+}
+
+// Ticket + look-back variant: the stream is packed by the encoder itself.
+cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int total_strips,
+                              uint32_t *status, uint32_t *ticket, cudaStream_t st) {
+    cudaError_t e = launch_init(d_descs, count, total_strips, status, ticket, st);
     if (e != cudaSuccess) return e;
     switch (bmax) {
-    case 32: return launch_t<32>(d_descs, count, total_strips, status, ticket, st);
-    case 16: return launch_t<16>(d_descs, count, total_strips, status, ticket, st);
-    case 8: return launch_t<8>(d_descs, count, total_strips, status, ticket, st);
+    case 32: return launch_t<32, false>(d_descs, count, total_strips, status, ticket, 0, st);
+    case 16: return launch_t<16, false>(d_descs, count, total_strips, status, ticket, 0, st);
+    case 8: return launch_t<8, false>(d_descs, count, total_strips, status, ticket, 0, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_pack(const EncDesc *d_descs, int count, int total_chunks, uint32_t *pack_status, cudaStream_t st);
+
+// Slot variant: encode into per-strip slots, then compact with pack_kernel.
+cudaError_t launch_mns_encode_slots(int bmax, const EncDesc *d_descs, int count, int total_strips, int total_chunks,
+                                    uint32_t *pack_status, cudaStream_t st) {
+    cudaError_t e;
+    switch (bmax) {
+    case 32: e = launch_t<32, true>(d_descs, count, total_strips, pack_status, nullptr, total_chunks, st); break;
+    case 16: e = launch_t<16, true>(d_descs, count, total_strips, pack_status, nullptr, total_chunks, st); break;
+    case 8: e = launch_t<8, true>(d_descs, count, total_strips, pack_status, nullptr, total_chunks, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    return launch_pack(d_descs, count, total_chunks, pack_status, st);
 }
 
 }  // namespace fic
@@ -624,12 +744,14 @@ cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int t
 // the encoder's scratch -- the image descriptor, the look-back status words
 // of the stream packer and the ticket counter -- in this file-scope device
 // array instead of a caller workspace.  Every GPU that loads the library
-// holds the array (about 256 KiB) until the process exits.
+// holds the array (about 256 KiB) until the process exits.  The image's
+// tensor map (for the TMA window loads) lives in the same array.
 #include <mutex>
 
 namespace {
 
 struct NoAllocScratch {
+    fic::TmaMap map;
     fic::EncDesc desc;
     uint32_t ticket;
     uint32_t pad[63];
@@ -708,6 +830,14 @@ extern "C" int fic_encode_noalloc(const uint8_t *d_img, int width, int height, c
     d.o_bits = p->o_bits;
     d.local_radius = p->local_radius;
     d.local_step = p->local_step;
+    {
+        const int bw = bmax == 32 ? WinBox<32>::W : (bmax == 16 ? WinBox<16>::W : WinBox<8>::W);
+        d.boxw = bw < width ? bw : width;
+    }
+    d.map = &scr->map;
+    TmaMap map;
+    rc = make_tma_map(&map, d_img, width, height, d.boxw, 2 * bmax);
+    if (rc) return rc;
     out->width = width;
     out->height = height;
     out->params = *p;
@@ -716,6 +846,7 @@ extern "C" int fic_encode_noalloc(const uint8_t *d_img, int width, int height, c
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // The descriptor is staged from host memory; the status words, the ticket
     // and the stream's info block are cleared by the init kernel of the launch.
+    if (cudaMemcpyAsync(&scr->map, &map, sizeof(map), cudaMemcpyHostToDevice, st) != cudaSuccess) return FIC_ECUDA;
     if (cudaMemcpyAsync(&scr->desc, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess) return FIC_ECUDA;
     return launch_mns_encode(bmax, &scr->desc, 1, (int)nstrips, scr->status, &scr->ticket, st) == cudaSuccess
                ? FIC_OK

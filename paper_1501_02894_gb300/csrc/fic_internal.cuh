@@ -6,12 +6,15 @@
 #include <cuda_runtime.h>
 
 #include "../../include/fic.h"
+#include "tma.cuh"
 
 namespace fic {
 
 // Bounded spin: a wait that has not finished after this many polls gives up,
 // records FIC_DEVERR_TIMEOUT and lets the kernel return.
 constexpr unsigned kSpinLimit = 1u << 22;
+// Polls of an mbarrier before a TMA copy is declared lost.
+constexpr unsigned kMbarLimit = 1u << 20;
 
 // One image of an encode launch.
 struct EncDesc {
@@ -30,13 +33,32 @@ struct EncDesc {
     int32_t mode, bmin, L, phase2;
     int32_t s_bits, o_bits;
     int32_t local_radius, local_step;
+    const TmaMap *map;   // 2-D tensor map of the image (box: the strip's domain window)
+    int32_t boxw;        // box width in pixels (= row pitch of the staged window)
+    int32_t bmax;
+    fic_record *slots;   // slot variant: 64 records per strip (workspace)
+    uint2 *stats;        // slot variant: per strip (record count, fits)
+    int32_t chunk_base;  // slot variant: first 32-strip chunk of the image (pack kernel)
+    int32_t nchunks;
 };
+
+// Box of the TMA window load for strips of top-level side BMAX: columns
+// (16-aligned) x rows.  The window of a strip is at most this wide.
+template <int BMAX>
+struct WinBox {
+    static constexpr int W = BMAX == 32 ? 64 : (BMAX == 16 ? 96 : 160);
+    static constexpr int H = 2 * BMAX;
+};
+
+// Build the tensor map of a W x H uint8 image for boxes of boxw x boxh
+// (host side; the driver entry point is looked up once).
+int make_tma_map(TmaMap *out, const void *base, int W, int H, int boxw, int boxh);
 
 // One image of a decode launch.
 struct DecDesc {
     const fic_record *rec;
     const uint32_t *tile_off;
-    uint8_t *buf[2];     // ping-pong iterates; the last iteration writes buf[iters & 1]
+    uint8_t *buf[2];     // ping-pong iterates; the last iteration writes buf[0]
     int32_t W, H;
     int32_t tw, th, spr, strip_base, nstrips;
     int32_t mode, bmin, L, s_bits, o_bits;
@@ -142,6 +164,27 @@ __device__ __forceinline__ void stage_window(const uint8_t *__restrict__ img, in
             o.y = d4_pair(a[t].y, b[t].y);
             o.z = d4_pair(a[t].z, b[t].z);
             o.w = d4_pair(a[t].w, b[t].w);
+            *reinterpret_cast<uint4 *>(d4e + r * NP + 4 * cu) = o;
+        }
+    }
+}
+
+// Same, from a window already copied into shared memory (row pitch `pitch`).
+template <int BMAX, int UPR, int NP>
+__device__ __forceinline__ void stage_window_smem(const uint8_t *raw, int pitch, int upr, uint32_t *d4e, int lane) {
+    constexpr int ITER = BMAX * UPR / 32;
+#pragma unroll
+    for (int t = 0; t < ITER; ++t) {
+        const int u = lane + 32 * t;
+        const int r = u / UPR, cu = u % UPR;
+        if (cu < upr) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(raw + (2 * r) * pitch + 16 * cu);
+            const uint4 b = *reinterpret_cast<const uint4 *>(raw + (2 * r + 1) * pitch + 16 * cu);
+            uint4 o;
+            o.x = d4_pair(a.x, b.x);
+            o.y = d4_pair(a.y, b.y);
+            o.z = d4_pair(a.z, b.z);
+            o.w = d4_pair(a.w, b.w);
             *reinterpret_cast<uint4 *>(d4e + r * NP + 4 * cu) = o;
         }
     }
