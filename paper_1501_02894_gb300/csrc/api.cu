@@ -48,6 +48,8 @@ cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int t
                               uint32_t *ticket, cudaStream_t st);
 cudaError_t launch_mns_encode_slots(int bmax, const EncDesc *d_descs, int count, int total_strips, int total_chunks,
                                     uint32_t *pack_status, cudaStream_t st);
+cudaError_t launch_local_encode(int bmax, const EncDesc *d_descs, int count, int total_strips, int total_chunks,
+                                uint32_t *pack_status, cudaStream_t st);
 cudaError_t launch_decode(int bmax, const DecDesc *d_descs, int count, int total_strips, void *tables, int iters,
                           cudaStream_t st);
 size_t decode_table_bytes_per_strip();
@@ -71,7 +73,11 @@ int levels_of(const fic_params *p) {
 
 int check_params(const fic_params *p) {
     if (!p) return FIC_EBADPARAM;
-    if (p->mode != FIC_NOSEARCH && p->mode != FIC_MNS) return FIC_EBADPARAM;
+    if (p->mode != FIC_NOSEARCH && p->mode != FIC_MNS && p->mode != FIC_LOCAL) return FIC_EBADPARAM;
+    if (p->mode == FIC_LOCAL &&
+        (p->local_radius < 0 || p->local_radius > 16 || (p->local_radius & 1) || p->local_step < 2 ||
+         (p->local_step & 1)))
+        return FIC_EBADPARAM;
     if (!(p->bmax == 8 || p->bmax == 16 || p->bmax == 32)) return FIC_EBADPARAM;
     if (!is_pow2(p->bmin) || p->bmin < 4 || p->bmin > p->bmax) return FIC_EBADPARAM;
     if (levels_of(p) > 4) return FIC_EBADPARAM;
@@ -107,6 +113,7 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? FIC_OK : FIC_ECUDA; }
 // look-back state live in the caller's workspace.
 struct fic_plan {
     int kind;  // 0 encode, 1 decode
+    int family;  // encode: 0 no-search / MNS, 1 local search
     int count;
     int bmax;
     int total_strips;
@@ -203,6 +210,7 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
         int rc = fic_validate(widths[i], heights[i], p);
         if (rc) return rc;
         if (p->bmax != bmax) return FIC_EBADPARAM;
+        if ((p->mode == FIC_LOCAL) != (params[0].mode == FIC_LOCAL)) return FIC_EBADPARAM;  // one kernel per launch
         if (!d_imgs[i] || (reinterpret_cast<uintptr_t>(d_imgs[i]) & 15)) return FIC_EBADPARAM;
         fic_stream *o = &outs[i];
         if (!o->records || !o->tile_offsets || !o->split || !o->info || o->capacity <= 0) return FIC_EBADPARAM;
@@ -255,6 +263,7 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
     if (!pl) return FIC_ENOMEM;
     uint8_t *w = static_cast<uint8_t *>(d_workspace);
     pl->kind = 0;
+    pl->family = params[0].mode == FIC_LOCAL ? 1 : 0;
     pl->count = count;
     pl->bmax = bmax;
     pl->total_strips = strips;
@@ -288,6 +297,9 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
 
 int fic_encode_plan_run(const fic_plan *pl, void *stream) {
     if (!pl || pl->kind != 0) return FIC_EBADPARAM;
+    if (pl->family == 1)
+        return cuda_rc(launch_local_encode(pl->bmax, pl->d_enc, pl->count, pl->total_strips, pl->total_chunks,
+                                           pl->status, static_cast<cudaStream_t>(stream)));
     return cuda_rc(launch_mns_encode_slots(pl->bmax, pl->d_enc, pl->count, pl->total_strips, pl->total_chunks,
                                            pl->status, static_cast<cudaStream_t>(stream)));
 }

@@ -29,7 +29,7 @@
 // entry point) takes strips from an atomic ticket in stream order and packs
 // the stream in place with a decoupled look-back over the strips (bounded
 // spin), so its only scratch is one status word per strip.
-#include "fic_internal.cuh"
+#include "encode_common.cuh"
 
 namespace fic {
 
@@ -47,198 +47,6 @@ struct Geom {
 constexpr int kWarps = 8;
 constexpr int kSlotRecords = 64;  // records a 1024-pixel strip can hold (4x4 leaves)
 constexpr uint32_t kAgg = 1u << 30, kIncl = 2u << 30, kValMask = (1u << 30) - 1;
-
-// Result of the phase-1 fit of one block.
-struct Fit {
-    long long ncrr, ncdr, ncdd;  // n Srr - Sr^2, n Sdr - Sd Sr, n Sdd - Sd^2
-    int sr;
-    int k, q;
-    bool pass;  // collage error below the level threshold
-};
-
-__device__ __forceinline__ int lum(int q, int ko1, uint32_t magic) {
-    // floor((510 q + ko1) / (2 ko1)) by multiply-high; exact for these ranges
-    return (int)__umulhi((uint32_t)(510 * q + ko1), magic);
-}
-
-// Phase-1 fit (Section 3: the best contrast factor for the one domain, the
-// error, the threshold test).  Exact: the contrast code is the grid point
-// nearest to c* = 512 nCdr / nCdd, found from a float estimate and settled by
-// int64 comparisons against the grid midpoints; ties go to the smaller |c|,
-// then to c > 0.  The luminance code is the level nearest the block mean.
-__device__ __forceinline__ void fit_phase1(int sr, int srr, int sd, int sdd, int sdr, int lg2n,
-                                           int s_bits, int ko1, uint32_t magic, float qscale,
-                                           long long thr, Fit &f) {
-    f.sr = sr;
-    f.ncrr = ((long long)srr << lg2n) - (long long)sr * sr;
-    f.ncdr = ((long long)sdr << lg2n) - (long long)sd * sr;
-    f.ncdd = ((long long)sdd << lg2n) - (long long)sd * sd;
-    const int K = 1 << s_bits, step = 256 >> s_bits;
-    int k;
-    if (f.ncdd <= 0) {
-        k = K >> 1;
-    } else {
-        float cs = 512.f * (float)f.ncdr / (float)f.ncdd;
-        float kf = (cs + 128.f) / (float)step - 0.5f;
-        kf = fminf(fmaxf(kf, 0.f), (float)(K - 1));
-        k = __float2int_rn(kf);
-        const long long a = 512LL * f.ncdr;
-#pragma unroll 1
-        for (int it = 0; it < K && k < K - 1; ++it) {
-            long long m = (long long)(step * (k + 1) - 128);
-            long long b = m * f.ncdd;
-            if (a > b || (a == b && m <= 0)) ++k;
-            else break;
-        }
-#pragma unroll 1
-        for (int it = 0; it < K && k > 0; ++it) {
-            long long m = (long long)(step * k - 128);
-            long long b = m * f.ncdd;
-            if (a > b || (a == b && m <= 0)) break;
-            --k;
-        }
-    }
-    int q0 = __float2int_rn((float)sr * qscale * __int_as_float((127 - lg2n) << 23));
-    q0 = clampi(q0, 0, ko1);
-    int bq = q0, bd = 0x7fffffff;
-#pragma unroll
-    for (int dq = -1; dq <= 1; ++dq) {
-        int q = q0 + dq;
-        if (q < 0 || q > ko1) continue;
-        int d = abs(sr - (lum(q, ko1, magic) << lg2n));
-        if (d < bd) {
-            bd = d;
-            bq = q;
-        }
-    }
-    f.k = k;
-    f.q = bq;
-    const long long c = contrast_code(k, s_bits);
-    const long long e = (long long)bd;
-    const long long E = 262144LL * f.ncrr - 1024LL * c * f.ncdr + c * c * f.ncdd + 262144LL * e * e;
-    f.pass = E < thr;
-}
-
-// Collage error of a phase-2 sub-block with a given luminance and the
-// better of the level's two contrasts (Section 3.2); returns pass and bit.
-__device__ __forceinline__ bool fit_phase2_sub(const Fit &f, int lg2n, int O, int c0, int c1,
-                                               long long thr, int &bit) {
-    // E(c1) < E(c0)  <=>  (c1 + c0) nCdd < 1024 nCdr   (c1 > c0)
-    bit = ((long long)(c1 + c0) * f.ncdd < 1024LL * f.ncdr) ? 1 : 0;
-    const long long c = bit ? c1 : c0;
-    const long long e = (long long)f.sr - ((long long)O << lg2n);
-    const long long E = 262144LL * f.ncrr - 1024LL * c * f.ncdr + c * c * f.ncdd + 262144LL * e * e;
-    return E < thr;
-}
-
-__device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y) {
-    uint32_t z = 0;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) z |= (((x >> b) & 1u) << (2 * b)) | (((y >> b) & 1u) << (2 * b + 1));
-    return z;
-}
-
-// Bitmask of the lanes that form the lane's block when a block spans gx patch
-// columns and gy patch rows.
-template <int PC>
-__device__ __forceinline__ uint32_t group_mask(int pc, int pr, int gx, int gy) {
-    int base = (pr - pr % gy) * PC + (pc - pc % gx);
-    uint32_t row = (gx >= 32) ? 0xffffffffu : ((1u << gx) - 1u);
-    uint32_t m = 0;
-    for (int i = 0; i < gy; ++i) m |= row << (base + i * PC);
-    return m;
-}
-
-template <int PC>
-__device__ __forceinline__ int group_sum(int v, int gx, int gy) {
-    for (int m = 1; m < gx; m <<= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-    for (int m = 1; m < gy; m <<= 1) v += __shfl_xor_sync(0xffffffffu, v, m * PC);
-    return v;
-}
-
-template <int PC>
-__device__ __forceinline__ uint32_t group_or(uint32_t v, int gx, int gy) {
-    for (int m = 1; m < gx; m <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, m);
-    for (int m = 1; m < gy; m <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, m * PC);
-    return v;
-}
-
-struct Leaf {
-    uint32_t w0, w1, w2, w3;  // the 16-byte fic_record
-    int pos;                  // canonical position in the strip, -1 = none
-};
-
-__device__ __forceinline__ void make_leaf(Leaf &L, int x, int y, int level, int phase, int k, int q,
-                                          int d0, int d1, int d2, int dx, int dy, int pos) {
-    L.w0 = (uint32_t)x | ((uint32_t)y << 16);
-    L.w1 = (uint32_t)level | ((uint32_t)phase << 8) | ((uint32_t)k << 16) | ((uint32_t)q << 24);
-    L.w2 = ((uint32_t)d0 & 0xffu) | (((uint32_t)d1 & 0xffu) << 8) | (((uint32_t)d2 & 0xffu) << 16);
-    L.w3 = (uint32_t)dx | ((uint32_t)dy << 16);
-    L.pos = pos;
-}
-
-// Moments of the lane's part of a block of side B >= 8: the patch's 4 rows x
-// 8 pixels against the 4 x 8 decimated domain values at (c, rr) (c even).
-template <int NP>
-__device__ __forceinline__ void patch_moments(const uint32_t *d4e, int c, int rr, const uint2 *rw,
-                                              int &sd, int &sdd, int &sdr) {
-    unsigned a_dr = 0, pk = 0, ql = 0, qh = 0;
-    const uint32_t *base = d4e + rr * NP + (c >> 1);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        // 32-bit loads: for 8x8 blocks the window starts at an odd word
-        const uint2 lo = make_uint2(base[i * NP], base[i * NP + 1]);
-        const uint2 hi = make_uint2(base[i * NP + 2], base[i * NP + 3]);
-        a_dr = dp2a_lo(lo.x, rw[i].x, a_dr);
-        a_dr = dp2a_hi(lo.y, rw[i].x, a_dr);
-        a_dr = dp2a_lo(hi.x, rw[i].y, a_dr);
-        a_dr = dp2a_hi(hi.y, rw[i].y, a_dr);
-        pk += lo.x + lo.y + hi.x + hi.y;
-        acc_sq(lo.x, ql, qh);
-        acc_sq(lo.y, ql, qh);
-        acc_sq(hi.x, ql, qh);
-        acc_sq(hi.y, ql, qh);
-    }
-    sd = (int)((pk & 0xffffu) + (pk >> 16));
-    sdd = (int)(ql + (qh << 8));
-    sdr = (int)a_dr;
-}
-
-// Moments of one 4x4 block (one half of the patch): 4 rows x 4 pixels (word
-// `h` of each row) against 4 x 4 decimated values starting at column c of
-// either parity (an odd start is realigned from three even pairs).
-template <int NP>
-__device__ __forceinline__ void half_moments(const uint32_t *d4e, int c, int rr, const uint2 *rw, int h,
-                                             int &sd, int &sdd, int &sdr) {
-    unsigned a_dr = 0, pk = 0, ql = 0, qh = 0;
-    const uint32_t *base = d4e + rr * NP + (c >> 1);
-    const bool odd = c & 1;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const uint32_t e0 = base[i * NP], e1 = base[i * NP + 1];
-        uint32_t p0 = e0, p1 = e1;
-        if (odd) {
-            const uint32_t e2 = base[i * NP + 2];
-            p0 = __funnelshift_r(e0, e1, 16);
-            p1 = __funnelshift_r(e1, e2, 16);
-        }
-        const uint32_t r = h ? rw[i].y : rw[i].x;
-        a_dr = dp2a_lo(p0, r, a_dr);
-        a_dr = dp2a_hi(p1, r, a_dr);
-        pk += p0 + p1;
-        acc_sq(p0, ql, qh);
-        acc_sq(p1, ql, qh);
-    }
-    sd = (int)((pk & 0xffffu) + (pk >> 16));
-    sdd = (int)(ql + (qh << 8));
-    sdr = (int)a_dr;
-}
-
-// Phase-1 summary of a block that the level loop carries forward.
-struct Code {
-    int k, q;
-    bool pass;
-};
 
 // SLOTS = true: strips are assigned statically (grid stride) and every strip
 //   writes its records to a fixed slot of the workspace; pack_kernel then
@@ -786,6 +594,7 @@ extern "C" int fic_encode_noalloc(const uint8_t *d_img, int width, int height, c
     using namespace fic;
     int rc = fic_validate(width, height, p);
     if (rc) return rc;
+    if (p->mode != FIC_NOSEARCH && p->mode != FIC_MNS) return FIC_EBADPARAM;  // centred-domain modes only
     if (!d_img || (reinterpret_cast<uintptr_t>(d_img) & 15) || !out) return FIC_EBADPARAM;
     if (!out->records || !out->tile_offsets || !out->split || !out->info || out->capacity <= 0)
         return FIC_EBADPARAM;

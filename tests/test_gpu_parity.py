@@ -184,3 +184,36 @@ def test_host_rejects_bad_arguments(fic):
         fic.fic_encode(img, fic.params("mns", 32, 4, 8.0))
     with pytest.raises(fic.FicError):
         fic.fic_encode(torch.zeros((64, 64), dtype=torch.uint8, device="cuda"), fic.params("mns", 32, 2, 8.0))
+
+
+# ---------------------------------------------------------------------------
+# Local search (Section 2): candidates around the centred domain
+
+@pytest.mark.parametrize("thr", [8.0, 4.0])
+def test_local_scene_512(fic, orc, thr):
+    _check_image(fic, orc, synth.gaussian_scene(512, 1), "local", 32, 4, thr, iters=6)
+
+
+def test_local_voronoi_512(fic, orc):
+    _check_image(fic, orc, synth.voronoi(512, 102), "local", 32, 4, 8.0, iters=4)
+
+
+@pytest.mark.parametrize("W,H,bmax,bmin,R,S", [
+    (544, 96, 32, 4, 16, 4),
+    (208, 80, 16, 4, 16, 4),
+    (208, 48, 8, 4, 8, 2),
+    (64, 64, 32, 4, 16, 2),
+    (96, 64, 32, 8, 4, 4),
+    (160, 96, 16, 16, 16, 4),
+])
+def test_local_sizes(fic, orc, W, H, bmax, bmin, R, S):
+    img = synth.gaussian_scene(W, 77 + W + H, H=H)
+    _check_image(fic, orc, img, "local", bmax, bmin, 6.0, iters=4, local_radius=R, local_step=S)
+
+
+def test_local_radius_zero_is_nosearch(fic, orc):
+    img = torch.from_numpy(synth.gaussian_scene(256, 13)).cuda()
+    a = fic.fic_encode(img, fic.params("local", 32, 4, 6.0, local_radius=0)).to_host()
+    b = fic.fic_encode(img, fic.params("nosearch", 32, 4, 6.0)).to_host()
+    assert np.array_equal(a["records"].view(np.uint8), b["records"].view(np.uint8))
+    assert np.array_equal(a["split"], b["split"])
