@@ -64,7 +64,8 @@ extern "C" {
 /* Encoder parameters (one set per image). */
 typedef struct fic_params {
     int32_t mode;         /* FIC_NOSEARCH .. FIC_EXHAUSTIVE */
-    int32_t bmax, bmin;   /* range sides, powers of two, 4 <= bmin <= bmax <= 32, L <= 4 */
+    int32_t bmax, bmin;   /* range sides, powers of two, 4 <= bmin <= bmax <= 32, L <= 4;
+                             FIC_EXHAUSTIVE: a flat partition, bmax = bmin = 8 */
     double thr_rms[4];    /* RMS error threshold E_j per level j=1..4 (Section 3);
                              compared as SSE < round(256 T^2)/256 * n */
     int32_t s_bits;       /* contrast code bits, 1..7 (5: 32 cells) */
@@ -72,8 +73,9 @@ typedef struct fic_params {
     int32_t phase2;       /* MNS only: 1 = try phase 2 before splitting */
     int32_t local_radius; /* FIC_LOCAL: search radius in pixels (16) */
     int32_t local_step;   /* FIC_LOCAL: offset step, even (4) */
-    int32_t dom_step;     /* FIC_EXHAUSTIVE: domain grid step, even (4) */
-    int32_t isometries;   /* FIC_EXHAUSTIVE: 1 or 8 */
+    int32_t dom_step;     /* FIC_EXHAUSTIVE: domain grid step in pixels (4) */
+    int32_t isometries;   /* FIC_EXHAUSTIVE: the first 1..8 isometries are tried */
+    int32_t engine;       /* FIC_EXHAUSTIVE: 0 tensor cores (tcgen05), 1 CUDA cores */
 } fic_params;
 
 /* One stored transform = one quadtree leaf (16 bytes).

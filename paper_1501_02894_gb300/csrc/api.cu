@@ -9,9 +9,10 @@
 
 #include <cudaTypedefs.h>
 
-#include "fic_internal.cuh"
+#include "exhaustive.cuh"
 
 namespace fic {
+cudaError_t launch_exhaustive(const ExhDesc &E, int engine, cudaStream_t st);
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against the driver library).
@@ -73,7 +74,11 @@ int levels_of(const fic_params *p) {
 
 int check_params(const fic_params *p) {
     if (!p) return FIC_EBADPARAM;
-    if (p->mode != FIC_NOSEARCH && p->mode != FIC_MNS && p->mode != FIC_LOCAL) return FIC_EBADPARAM;
+    if (p->mode < FIC_NOSEARCH || p->mode > FIC_EXHAUSTIVE) return FIC_EBADPARAM;
+    if (p->mode == FIC_EXHAUSTIVE &&
+        (p->bmax != kExhB || p->bmin != kExhB || p->isometries < 1 || p->isometries > 8 || p->dom_step < 1 ||
+         p->engine < 0 || p->engine > 1))
+        return FIC_EBADPARAM;
     if (p->mode == FIC_LOCAL &&
         (p->local_radius < 0 || p->local_radius > 16 || (p->local_radius & 1) || p->local_step < 2 ||
          (p->local_step & 1)))
@@ -113,7 +118,7 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? FIC_OK : FIC_ECUDA; }
 // look-back state live in the caller's workspace.
 struct fic_plan {
     int kind;  // 0 encode, 1 decode
-    int family;  // encode: 0 no-search / MNS, 1 local search
+    int family;  // encode: 0 no-search / MNS, 1 local search, 2 exhaustive search
     int count;
     int bmax;
     int total_strips;
@@ -125,10 +130,111 @@ struct fic_plan {
     uint32_t *status;
     uint32_t *ticket;
     std::vector<DecDesc> hdec;  // decode: host copy (buffers per image)
+    std::vector<ExhDesc> hexh;  // exhaustive search: one descriptor per image (launched in turn)
+    std::vector<int> engines;
     void *dec_tables;           // decode: per-strip transform tables
     std::vector<uint8_t *> outs;
     std::vector<size_t> out_bytes;
 };
+
+// Exhaustive search: per image, decimated domains (packed and fp16), domain
+// and range statistics, permuted range rows and per-row results.
+struct ExhLayout {
+    size_t dpairs, dfp16, dstat, afp16, rstat, row_g, row_dk, total;
+};
+
+static ExhLayout exh_layout(int W, int H, const fic_params *p, int *nd_out, int *nd_pad_out, int *ndx_out,
+                            int *ndy_out) {
+    const int ndx = (W - 2 * kExhB) / p->dom_step + 1, ndy = (H - 2 * kExhB) / p->dom_step + 1;
+    const int nd = ndx * ndy, nd_pad = ((nd + kExhNTile - 1) / kExhNTile) * kExhNTile;
+    const size_t nr = (size_t)(W / kExhB) * (H / kExhB);
+    ExhLayout L;
+    L.dpairs = 0;
+    L.dfp16 = L.dpairs + align_up((size_t)nd * 128);
+    L.dstat = L.dfp16 + align_up((size_t)nd_pad * 128);
+    L.afp16 = L.dstat + align_up((size_t)nd_pad * 16);
+    L.rstat = L.afp16 + align_up(nr * 8 * 128);
+    L.row_g = L.rstat + align_up(nr * 16);
+    L.row_dk = L.row_g + align_up(nr * 8 * 8);
+    L.total = L.row_dk + align_up(nr * 8 * 8);
+    if (nd_out) *nd_out = nd;
+    if (nd_pad_out) *nd_pad_out = nd_pad;
+    if (ndx_out) *ndx_out = ndx;
+    if (ndy_out) *ndy_out = ndy;
+    return L;
+}
+
+// Plan of a batch of exhaustive searches: each image gets its own workspace
+// slice and kernel sequence (prep, search, finalize).
+static int exh_plan_create(const uint8_t *const *d_imgs, const int *widths, const int *heights, int count,
+                           const fic_params *params, fic_stream *outs, void *d_workspace, size_t ws_bytes,
+                           fic_plan **plan_out) {
+    if ((reinterpret_cast<uintptr_t>(d_workspace) & (kAlign - 1))) return FIC_ENOMEM;
+    fic_plan *pl = new (std::nothrow) fic_plan();
+    if (!pl) return FIC_ENOMEM;
+    uint8_t *w = static_cast<uint8_t *>(d_workspace);
+    size_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        const fic_params *p = &params[i];
+        int rc = fic_validate(widths[i], heights[i], p);
+        if (rc == FIC_OK && p->mode != FIC_EXHAUSTIVE) rc = FIC_EBADPARAM;
+        fic_stream *o = &outs[i];
+        if (rc == FIC_OK && (!d_imgs[i] || !o->records || !o->tile_offsets || !o->split || !o->info ||
+                             (reinterpret_cast<uintptr_t>(o->records) & 15)))
+            rc = FIC_EBADPARAM;
+        const int W = widths[i], H = heights[i];
+        if (rc == FIC_OK && o->capacity < (W / kExhB) * (H / kExhB)) rc = FIC_ECAPACITY;
+        int nd = 0, nd_pad = 0, ndx = 0, ndy = 0;
+        const ExhLayout L = exh_layout(W, H, p, &nd, &nd_pad, &ndx, &ndy);
+        if (rc == FIC_OK && off + L.total > ws_bytes) rc = FIC_ENOMEM;
+        if (rc) {
+            delete pl;
+            return rc;
+        }
+        o->width = W;
+        o->height = H;
+        o->params = *p;
+        o->ntop = (W / kExhB) * (H / kExhB);
+        ExhDesc E;
+        std::memset(&E, 0, sizeof(E));
+        E.img = d_imgs[i];
+        E.W = W;
+        E.H = H;
+        E.nrx = W / kExhB;
+        E.nry = H / kExhB;
+        E.nr = E.nrx * E.nry;
+        E.ndx = ndx;
+        E.ndy = ndy;
+        E.nd = nd;
+        E.nd_pad = nd_pad;
+        E.step = p->dom_step;
+        E.isos = p->isometries;
+        E.s_bits = p->s_bits;
+        E.o_bits = p->o_bits;
+        E.dpairs = reinterpret_cast<uint32_t *>(w + off + L.dpairs);
+        E.dfp16 = reinterpret_cast<__half *>(w + off + L.dfp16);
+        E.dstat = reinterpret_cast<int4 *>(w + off + L.dstat);
+        E.afp16 = reinterpret_cast<__half *>(w + off + L.afp16);
+        E.rstat = reinterpret_cast<int4 *>(w + off + L.rstat);
+        E.row_g = reinterpret_cast<long long *>(w + off + L.row_g);
+        E.row_dk = reinterpret_cast<int2 *>(w + off + L.row_dk);
+        E.rec = o->records;
+        E.tile_off = o->tile_offsets;
+        E.split = o->split;
+        E.info = o->info;
+        off += L.total;
+        pl->hexh.push_back(E);
+        pl->engines.push_back(p->engine);
+    }
+    pl->kind = 0;
+    pl->family = 2;
+    pl->count = count;
+    pl->bmax = kExhB;
+    pl->ws = d_workspace;
+    pl->ws_bytes = ws_bytes;
+    *plan_out = pl;
+    return FIC_OK;
+}
 
 extern "C" {
 
@@ -184,14 +290,18 @@ static EncLayout enc_layout(int count, size_t strips, size_t chunks) {
 
 size_t fic_encode_workspace_bytes(int count, const int *widths, const int *heights, const fic_params *params) {
     if (count <= 0 || !widths || !heights || !params) return 0;
-    size_t strips = 0, chunks = 0;
+    size_t strips = 0, chunks = 0, exh = 0;
     for (int i = 0; i < count; ++i) {
         if (fic_validate(widths[i], heights[i], &params[i])) return 0;
+        if (params[i].mode == FIC_EXHAUSTIVE) {
+            exh += exh_layout(widths[i], heights[i], &params[i], nullptr, nullptr, nullptr, nullptr).total;
+            continue;
+        }
         const size_t n = (size_t)nstrips_of(widths[i], heights[i], params[i].bmax);
         strips += n;
         chunks += (n + 31) / 32;
     }
-    return enc_layout(count, strips, chunks).total;
+    return enc_layout(count, strips, chunks).total + exh;
 }
 
 int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, const int *heights, int count,
@@ -200,6 +310,8 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
     if (!plan_out || count <= 0 || !d_imgs || !widths || !heights || !params || !outs || !d_workspace)
         return FIC_EBADPARAM;
     *plan_out = nullptr;
+    if (params[0].mode == FIC_EXHAUSTIVE)
+        return exh_plan_create(d_imgs, widths, heights, count, params, outs, d_workspace, ws_bytes, plan_out);
     const int bmax = params[0].bmax;
     std::vector<EncDesc> h((size_t)count);
     std::vector<TmaMap> maps((size_t)count);
@@ -210,7 +322,8 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
         int rc = fic_validate(widths[i], heights[i], p);
         if (rc) return rc;
         if (p->bmax != bmax) return FIC_EBADPARAM;
-        if ((p->mode == FIC_LOCAL) != (params[0].mode == FIC_LOCAL)) return FIC_EBADPARAM;  // one kernel per launch
+        if ((p->mode == FIC_LOCAL) != (params[0].mode == FIC_LOCAL) || p->mode == FIC_EXHAUSTIVE)
+            return FIC_EBADPARAM;  // one kernel family per launch
         if (!d_imgs[i] || (reinterpret_cast<uintptr_t>(d_imgs[i]) & 15)) return FIC_EBADPARAM;
         fic_stream *o = &outs[i];
         if (!o->records || !o->tile_offsets || !o->split || !o->info || o->capacity <= 0) return FIC_EBADPARAM;
@@ -297,6 +410,13 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
 
 int fic_encode_plan_run(const fic_plan *pl, void *stream) {
     if (!pl || pl->kind != 0) return FIC_EBADPARAM;
+    if (pl->family == 2) {
+        for (size_t i = 0; i < pl->hexh.size(); ++i) {
+            const cudaError_t e = launch_exhaustive(pl->hexh[i], pl->engines[i], static_cast<cudaStream_t>(stream));
+            if (e != cudaSuccess) return FIC_ECUDA;
+        }
+        return FIC_OK;
+    }
     if (pl->family == 1)
         return cuda_rc(launch_local_encode(pl->bmax, pl->d_enc, pl->count, pl->total_strips, pl->total_chunks,
                                            pl->status, static_cast<cudaStream_t>(stream)));

@@ -51,6 +51,27 @@ __device__ __forceinline__ int best_contrast(long long ncdr, long long ncdd, int
     return k;
 }
 
+// The luminance code whose level is nearest the block mean Sr / n (ties to
+// the smaller code); *dist = |Sr - n L(q)|.  The float estimate is within
+// one code of the answer, which the exact integer check settles.
+__device__ __forceinline__ int best_luminance(int sr, int lg2n, int ko1, uint32_t magic, float qscale, int &dist) {
+    int q0 = __float2int_rn((float)sr * qscale * __int_as_float((127 - lg2n) << 23));
+    q0 = clampi(q0, 0, ko1);
+    int bq = q0, bd = 0x7fffffff;
+#pragma unroll
+    for (int dq = -1; dq <= 1; ++dq) {
+        const int q = q0 + dq;
+        if (q < 0 || q > ko1) continue;
+        const int d = abs(sr - (lum(q, ko1, magic) << lg2n));
+        if (d < bd) {
+            bd = d;
+            bq = q;
+        }
+    }
+    dist = bd;
+    return bq;
+}
+
 // Phase-1 fit (Section 3: the best contrast factor for the one domain, the
 // error, the threshold test).  Exact: the contrast code is the grid point
 // nearest to c* = 512 nCdr / nCdd, found from a float estimate and settled by
@@ -64,19 +85,8 @@ __device__ __forceinline__ void fit_phase1(int sr, int srr, int sd, int sdd, int
     f.ncdr = ((long long)sdr << lg2n) - (long long)sd * sr;
     f.ncdd = ((long long)sdd << lg2n) - (long long)sd * sd;
     const int k = best_contrast(f.ncdr, f.ncdd, s_bits);
-    int q0 = __float2int_rn((float)sr * qscale * __int_as_float((127 - lg2n) << 23));
-    q0 = clampi(q0, 0, ko1);
-    int bq = q0, bd = 0x7fffffff;
-#pragma unroll
-    for (int dq = -1; dq <= 1; ++dq) {
-        int q = q0 + dq;
-        if (q < 0 || q > ko1) continue;
-        int d = abs(sr - (lum(q, ko1, magic) << lg2n));
-        if (d < bd) {
-            bd = d;
-            bq = q;
-        }
-    }
+    int bd;
+    const int bq = best_luminance(sr, lg2n, ko1, magic, qscale, bd);
     f.k = k;
     f.q = bq;
     const long long c = contrast_code(k, s_bits);

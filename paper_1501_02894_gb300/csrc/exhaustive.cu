@@ -1,0 +1,236 @@
+// exhaustive.cu -- exhaustive domain search (paper Section 1): every range
+// block (flat 8x8 partition) against every domain on a grid of step
+// `dom_step`, under every isometry; the pair with the smallest collage error
+// wins, ties to the smaller domain index, then the smaller isometry.
+//
+// Sum r*d4 of all (range, isometry) x domain pairs is a dense contraction
+// over the 64 decimated values of a block, so it is computed either on the
+// tensor cores (exhaustive_tc.cu: tcgen05, fp16 operands, fp32 accumulators,
+// exact because every partial sum is an integer below 2^24) or here on the
+// CUDA cores (dp2a on packed operands).  Both feed the same screening
+// epilogue: a float lower bound of each candidate's best contrast error
+// skips it unless it may beat the row's best, which is then settled in exact
+// int64 arithmetic.  The isometry is applied on the range side: row
+// (range, t) holds the range pixel r(u, v) at the position of the domain
+// element it meets under isometry t.
+#include "exhaustive.cuh"
+
+namespace fic {
+
+// Decimated domains: packed pairs for dp2a, fp16 K-major rows for the tensor
+// cores, and per-domain statistics (Sd, nCdd, 512 / nCdd).
+__global__ void exh_prep_domains(ExhDesc E) {
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < E.nd_pad; d += gridDim.x * blockDim.x) {
+        if (d >= E.nd) {
+            for (int i = 0; i < kExhK; ++i) E.dfp16[(size_t)d * kExhK + i] = __ushort_as_half(0);
+            E.dstat[d] = make_int4(0, 0, 0, 0);
+            continue;
+        }
+        const int dy = (d / E.ndx) * E.step, dx = (d % E.ndx) * E.step;
+        int sd = 0;
+        long long sdd = 0;
+        for (int v = 0; v < kExhB; ++v) {
+            const uint8_t *p = E.img + (size_t)(dy + 2 * v) * E.W + dx;
+            int vals[kExhB];
+            for (int u = 0; u < kExhB; ++u) {
+                vals[u] = (int)p[2 * u] + p[2 * u + 1] + p[E.W + 2 * u] + p[E.W + 2 * u + 1];
+                sd += vals[u];
+                sdd += (long long)vals[u] * vals[u];
+                E.dfp16[(size_t)d * kExhK + v * kExhB + u] = __int2half_rn(vals[u]);
+            }
+            for (int u = 0; u < kExhB; u += 2)
+                E.dpairs[(size_t)d * 32 + (v * kExhB + u) / 2] = (uint32_t)vals[u] | ((uint32_t)vals[u + 1] << 16);
+        }
+        const long long ncdd = 64LL * sdd - (long long)sd * sd;  // <= 4.3e9: fits an unsigned word
+        const float k512 = ncdd > 0 ? 512.f / (float)ncdd : 0.f;
+        E.dstat[d] = make_int4(sd, (int)(uint32_t)ncdd, __float_as_int(k512), 1);
+    }
+}
+
+// Range rows, one per (range, isometry): A[sv * 8 + su] = r(u, v) where
+// (su, sv) is the domain element that isometry t puts at (u, v).
+__global__ void exh_prep_ranges(ExhDesc E) {
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < E.nr * 8; row += gridDim.x * blockDim.x) {
+        const int r = row >> 3, t = row & 7;
+        const int x = (r % E.nrx) * kExhB, y = (r / E.nrx) * kExhB;
+        int sr = 0, srr = 0;
+        for (int v = 0; v < kExhB; ++v) {
+            for (int u = 0; u < kExhB; ++u) {
+                const int px = E.img[(size_t)(y + v) * E.W + x + u];
+                int su, sv;
+                exh_iso_src(t, kExhB, u, v, su, sv);
+                E.afp16[(size_t)row * kExhK + sv * kExhB + su] = __int2half_rn(px);
+                sr += px;
+                srr += px * px;
+            }
+        }
+        if (t == 0) E.rstat[r] = make_int4(sr, srr, 0, 0);
+    }
+}
+
+// Row state of the screening epilogue.
+struct ExhRow {
+    long long g;  // best exact s-part error
+    float gf;     // the same as float, plus its rounding margin
+    int d, k;
+};
+
+__device__ __forceinline__ void exh_row_init(ExhRow &b) {
+    b.g = 0x7fffffffffffffffLL;
+    b.gf = __int_as_float(0x7f800000);  // +inf
+    b.d = -1;
+    b.k = 0;
+}
+
+// Offer candidate domain d with sum r*d4 = sdr to the row (domains are
+// offered in increasing order, so a strict improvement test keeps the
+// smallest domain index among equal errors).
+__device__ __forceinline__ void exh_offer(ExhRow &b, int d, int sdr, int sr, int4 ds, int s_bits) {
+    const int sd = ds.x;
+    const uint32_t ncdd = (uint32_t)ds.y;
+    const int ncdr = 64 * sdr - sd * sr;
+    const float lb = exh_lower_bound((float)ncdr, (float)ncdd, __int_as_float(ds.z), s_bits);
+    if (lb > b.gf) return;
+    const int k = best_contrast((long long)ncdr, (long long)ncdd, s_bits);
+    const long long c = contrast_code(k, s_bits);
+    const long long g = c * c * (long long)ncdd - 1024LL * c * ncdr;
+    if (g < b.g) {
+        b.g = g;
+        const float gf = (float)g;
+        b.gf = gf + fabsf(gf) * 1e-6f + 1.f;
+        b.d = d;
+        b.k = k;
+    }
+}
+
+// CUDA-core search: a warp holds 4 ranges x 8 isometries (one row per lane),
+// domains are staged 64 at a time in shared memory and read by broadcast.
+constexpr int kExhWarps = 4;
+constexpr int kExhStage = 64;
+
+__global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
+    __shared__ __align__(16) uint32_t s_dp[kExhStage][32];
+    __shared__ int4 s_ds[kExhStage];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = (blockIdx.x * kExhWarps + warp) * 4 + (lane >> 3);
+    const int t = lane & 7;
+    const bool live = r < E.nr && t < E.isos;
+    // the row's permuted range pixels as 16 words of 4 bytes
+    uint32_t aw[16];
+    int sr = 0;
+    {
+        const int rr = live ? r : 0;
+        const int x = (rr % E.nrx) * kExhB, y = (rr / E.nrx) * kExhB;
+        uint8_t a[kExhK];
+#pragma unroll
+        for (int v = 0; v < kExhB; ++v) {
+#pragma unroll
+            for (int u = 0; u < kExhB; ++u) {
+                int su, sv;
+                exh_iso_src(t, kExhB, u, v, su, sv);
+                const uint8_t px = E.img[(size_t)(y + v) * E.W + x + u];
+                a[sv * kExhB + su] = px;
+                sr += px;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            aw[i] = (uint32_t)a[4 * i] | ((uint32_t)a[4 * i + 1] << 8) | ((uint32_t)a[4 * i + 2] << 16) |
+                    ((uint32_t)a[4 * i + 3] << 24);
+    }
+    ExhRow best;
+    exh_row_init(best);
+    for (int d0 = 0; d0 < E.nd; d0 += kExhStage) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kExhStage * 32; i += blockDim.x) {
+            const int j = i >> 5, w = i & 31;
+            s_dp[j][w] = (d0 + j < E.nd) ? E.dpairs[(size_t)(d0 + j) * 32 + w] : 0u;
+        }
+        for (int j = threadIdx.x; j < kExhStage; j += blockDim.x)
+            s_ds[j] = (d0 + j < E.nd) ? E.dstat[d0 + j] : make_int4(0, 0, 0, 0);
+        __syncthreads();
+        const int nj = min(kExhStage, E.nd - d0);
+        for (int j = 0; j < nj; ++j) {
+            unsigned acc = 0;
+            const uint4 *q = reinterpret_cast<const uint4 *>(s_dp[j]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint4 p = q[i];
+                acc = dp2a_lo(p.x, aw[2 * i], acc);
+                acc = dp2a_hi(p.y, aw[2 * i], acc);
+                acc = dp2a_lo(p.z, aw[2 * i + 1], acc);
+                acc = dp2a_hi(p.w, aw[2 * i + 1], acc);
+            }
+            if (live) exh_offer(best, d0 + j, (int)acc, sr, s_ds[j], E.s_bits);
+        }
+    }
+    if (live) {
+        E.row_g[(size_t)r * 8 + t] = best.g;
+        E.row_dk[(size_t)r * 8 + t] = make_int2(best.d, best.k);
+    }
+}
+
+// Combine the isometry rows of each range and write its record (the flat
+// partition: one phase-1 leaf per range, in raster order).
+__global__ void exh_finalize(ExhDesc E) {
+    const int ko1 = (1 << E.o_bits) - 1;
+    const uint32_t magic = (uint32_t)((0x100000000ULL + 2 * ko1 - 1) / (2 * ko1));
+    const float qscale = (float)ko1 / 255.f;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < E.nr; r += gridDim.x * blockDim.x) {
+        long long bg = 0x7fffffffffffffffLL;
+        int bd = 0x7fffffff, bt = 0, bk = 0;
+        for (int t = 0; t < E.isos; ++t) {
+            const long long g = E.row_g[(size_t)r * 8 + t];
+            const int2 dk = E.row_dk[(size_t)r * 8 + t];
+            if (g < bg || (g == bg && dk.x < bd)) {
+                bg = g;
+                bd = dk.x;
+                bt = t;
+                bk = dk.y;
+            }
+        }
+        const int sr = E.rstat[r].x;
+        int dist;
+        const int q = best_luminance(sr, 6, ko1, magic, qscale, dist);
+        const int x = (r % E.nrx) * kExhB, y = (r / E.nrx) * kExhB;
+        const int dx = (bd % E.ndx) * E.step, dy = (bd / E.ndx) * E.step;
+        const uint4 w = make_uint4((uint32_t)x | ((uint32_t)y << 16),
+                                   1u | (1u << 8) | ((uint32_t)bk << 16) | ((uint32_t)q << 24),
+                                   (uint32_t)bt << 24, (uint32_t)dx | ((uint32_t)dy << 16));
+        *reinterpret_cast<uint4 *>(E.rec + r) = w;
+        E.tile_off[r] = (uint32_t)r;
+        E.split[r] = 0u;
+        if (r == 0) {
+            const unsigned long long fits = (unsigned long long)E.nr * E.nd * E.isos;
+            E.tile_off[E.nr] = (uint32_t)E.nr;
+            E.info[FIC_INFO_RECORDS] = (uint32_t)E.nr;
+            E.info[FIC_INFO_FITS_LO] = (uint32_t)fits;
+            E.info[FIC_INFO_FITS_HI] = (uint32_t)(fits >> 32);
+        }
+    }
+}
+
+cudaError_t launch_exh_tc(const ExhDesc &E, uint32_t *err, cudaStream_t st);
+
+// engine 0: tensor cores, 1: CUDA cores.  The stream's info block is
+// cleared first; a device timeout of the tensor path leaves its error bit.
+cudaError_t launch_exhaustive(const ExhDesc &E, int engine, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(E.info, 0, FIC_INFO_WORDS * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    exh_prep_domains<<<(E.nd_pad + 255) / 256, 256, 0, st>>>(E);
+    exh_prep_ranges<<<(E.nr * 8 + 255) / 256, 256, 0, st>>>(E);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (engine == 1) {
+        const int ranges_per_cta = kExhWarps * 4;
+        exh_cuda_kernel<<<(E.nr + ranges_per_cta - 1) / ranges_per_cta, kExhWarps * 32, 0, st>>>(E);
+        e = cudaGetLastError();
+    } else {
+        e = launch_exh_tc(E, E.info + FIC_INFO_ERROR, st);
+    }
+    if (e != cudaSuccess) return e;
+    exh_finalize<<<(E.nr + 255) / 256, 256, 0, st>>>(E);
+    return cudaGetLastError();
+}
+
+}  // namespace fic

@@ -1,0 +1,316 @@
+// exhaustive_tc.cu -- the exhaustive search's sum r*d4 on the 5th-generation
+// tensor cores (tcgen05), with the screening epilogue fused.
+//
+// C[row, d] = sum_k A[row, k] B[d, k], A = range rows (range x isometry, 64
+// fp16 values), B = decimated domains (64 fp16 values).  Operands are exact
+// in fp16 (pixels <= 255, 2x2 sums <= 1020) and every partial sum is an
+// integer below 2^24, so the fp32 accumulator holds sum r*d4 exactly.
+//
+// One CTA owns 128 rows (16 ranges x 8 isometries) and streams every domain
+// tile of 128 domains:
+//   warp 0      TMA producer: the A tile once, B tiles through a 4-stage ring
+//               (128-byte swizzle, mbarrier transaction counts);
+//   warp 1      allocates 256 TMEM columns (two 128-column fp32
+//               accumulators) and issues tcgen05.mma (M=128, N=128, K=16,
+//               four per tile) from one lane, committing to mbarriers;
+//   warps 2..9  epilogue: each warp reads one 32-lane quarter of an
+//               accumulator (tcgen05.ld, 32x32b) for half of the columns and
+//               offers every (row, domain) to the row's screening state.
+// The accumulators alternate, so the epilogue of tile n overlaps the MMA of
+// tile n+1.  Every mbarrier wait is bounded; a timeout sets an error flag,
+// all roles leave their loops, and TMEM is freed before the CTA exits.
+#include <cudaTypedefs.h>
+
+#include "exhaustive.cuh"
+
+namespace fic {
+
+constexpr int kTcRows = 128;   // M
+constexpr int kTcCols = 128;   // N per tile
+constexpr int kTcStages = 4;
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcThreads = (2 + kTcEpiWarps) * 32;
+constexpr uint32_t kTileBytes = kTcCols * kExhK * 2;  // 16 KiB (also the A tile)
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// K-major operand in shared memory with the 128-byte swizzle: rows of 128
+// bytes (64 fp16), 8-row groups 1024 bytes apart.  Fields: start address
+// >> 4 (bits 0-13), leading byte offset >> 4 (16-29, unused here: 1), stride
+// byte offset >> 4 (32-45), descriptor version 1 (46-47), swizzle mode 2 =
+// 128-byte (61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: fp32 accumulator (bits 4-5 = 1),
+// fp16 A and B (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t f16_idesc(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Row state of the screening epilogue (as in exhaustive.cu).
+struct TcRow {
+    long long g;
+    float gf;
+    int d, k;
+};
+
+__device__ __forceinline__ void tc_offer(TcRow &b, int d, int sdr, int sr, int4 ds, int s_bits) {
+    const int sd = ds.x;
+    const uint32_t ncdd = (uint32_t)ds.y;
+    const int ncdr = 64 * sdr - sd * sr;
+    const float lb = exh_lower_bound((float)ncdr, (float)ncdd, __int_as_float(ds.z), s_bits);
+    if (lb > b.gf) return;
+    const int k = best_contrast((long long)ncdr, (long long)ncdd, s_bits);
+    const long long c = contrast_code(k, s_bits);
+    const long long g = c * c * (long long)ncdd - 1024LL * c * ncdr;
+    if (g < b.g) {
+        b.g = g;
+        const float gf = (float)g;
+        b.gf = gf + fabsf(gf) * 1e-6f + 1.f;
+        b.d = d;
+        b.k = k;
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 2)
+    exh_tc_kernel(ExhDesc E, const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                  uint32_t *err) {
+    extern __shared__ __align__(1024) uint8_t tsmem[];
+    uint8_t *base = tsmem + ((1024u - (smem_u32(tsmem) & 1023u)) & 1023u);
+    uint8_t *sA = base;
+    uint8_t *sB = base + kTileBytes;
+    __shared__ __align__(8) uint64_t bar_full[kTcStages], bar_empty[kTcStages], bar_acc_full[2], bar_acc_empty[2],
+        bar_a;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+    __shared__ TcRow s_half[kTcRows];  // the second epilogue warp of each lane quarter hands its state over
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = blockIdx.x * kTcRows;
+    const int ntiles = E.nd_pad / kTcCols;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&bar_acc_full[a], 1);
+            mbar_init(&bar_acc_empty[a], kTcEpiWarps * 32);  // every epilogue thread reads every accumulator
+        }
+        mbar_init(&bar_a, 1);
+        s_abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&s_tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&bar_a, kTileBytes);
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];" ::"r"(smem_u32(sA)),
+                "l"(reinterpret_cast<uint64_t>(&mapA)), "r"(0), "r"(row0), "r"(smem_u32(&bar_a))
+                : "memory");
+            int issued = 0;
+            for (int n = 0; n < ntiles; ++n) {
+                const int s = n % kTcStages;
+                const uint32_t par = (uint32_t)((n / kTcStages) & 1) ^ 1u;
+                if (!mbar_wait(&bar_empty[s], par, kMbarLimit) || s_abort) {
+                    s_abort = 1;
+                    break;
+                }
+                issued = n + 1;
+                mbar_arrive_expect_tx(&bar_full[s], kTileBytes);
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                    "%3}], [%4];" ::"r"(smem_u32(sB + s * kTileBytes)),
+                    "l"(reinterpret_cast<uint64_t>(&mapB)), "r"(0), "r"(n * kTcCols), "r"(smem_u32(&bar_full[s]))
+                    : "memory");
+            }
+            // copies still in flight must land before the CTA may leave
+            mbar_wait(&bar_a, 0u, kMbarLimit);
+            for (int n = max(0, issued - kTcStages); n < issued; ++n)
+                mbar_wait(&bar_full[n % kTcStages], (uint32_t)((n / kTcStages) & 1), kMbarLimit);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = f16_idesc(kTcRows, kTcCols);
+            bool ok = mbar_wait(&bar_a, 0u, kMbarLimit);
+            int last = -1;
+            for (int n = 0; ok && n < ntiles; ++n) {
+                const int s = n % kTcStages, acc = n & 1;
+                if (!mbar_wait(&bar_full[s], (uint32_t)((n / kTcStages) & 1), kMbarLimit) ||
+                    !mbar_wait(&bar_acc_empty[acc], (uint32_t)((n >> 1) & 1) ^ 1u, kMbarLimit) || s_abort) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(acc * kTcCols);
+                const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + s * kTileBytes);
+#pragma unroll
+                for (int kk = 0; kk < kExhK / 16; ++kk)
+                    tc_mma(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, kk > 0);
+                tc_commit(&bar_empty[s]);     // the B stage is free once these MMAs are done
+                tc_commit(&bar_acc_full[acc]);
+                last = n;
+            }
+            if (!ok) s_abort = 1;
+            // every MMA issued must be complete before TMEM is freed
+            if (last >= 0) mbar_wait(&bar_acc_full[last & 1], (uint32_t)((last >> 1) & 1), kMbarLimit);
+        }
+    } else {
+        // ---------------- epilogue: warps 2..9; lane quarter q, column half h
+        const int ew = warp - 2;
+        const int q = warp & 3;              // TMEM lanes 32q .. 32q+31 belong to warps with warp % 4 == q
+        const int h = ew >> 2;               // 0: columns 0..63, 1: columns 64..127
+        const int rloc = 32 * q + lane;
+        const int row = row0 + rloc;
+        const int r = row >> 3, t = row & 7;
+        const bool live = r < E.nr && t < E.isos;
+        const int sr = live ? E.rstat[r].x : 0;
+        TcRow best;
+        best.g = 0x7fffffffffffffffLL;
+        best.gf = __int_as_float(0x7f800000);
+        best.d = -1;
+        best.k = 0;
+        for (int n = 0; n < ntiles; ++n) {
+            const int acc = n & 1;
+            if (!mbar_wait(&bar_acc_full[acc], (uint32_t)((n >> 1) & 1), kMbarLimit) || s_abort) {
+                s_abort = 1;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll 1
+            for (int c0 = 0; c0 < kTcCols / 2; c0 += 32) {
+                const int col = h * (kTcCols / 2) + c0;
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kTcCols + col), v);
+                if (live) {
+                    const int dbase = n * kTcCols + col;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int d = dbase + j;
+                        if (d < E.nd) tc_offer(best, d, __float2int_rn(v[j]), sr, __ldg(E.dstat + d), E.s_bits);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&bar_acc_empty[acc]);
+        }
+        // merge the two column halves of each row (the lower domain half wins ties)
+        if (h == 1) s_half[rloc] = best;
+        asm volatile("bar.sync 1, %0;" ::"r"(kTcEpiWarps * 32));
+        if (h == 0 && live) {
+            const TcRow o = s_half[rloc];
+            if (o.g < best.g) best = o;
+            E.row_g[(size_t)r * 8 + t] = best.g;
+            E.row_dk[(size_t)r * 8 + t] = make_int2(best.d, best.k);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    }
+    if (threadIdx.x == 0 && s_abort) atomicOr(err, FIC_DEVERR_TIMEOUT);
+}
+
+// Tensor maps of the two operands (fp16, 128-byte swizzle, 64 x 128 boxes).
+static int make_f16_map(CUtensorMap *m, const void *base, int rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) !=
+                cudaSuccess ||
+            qr != cudaDriverEntryPointSuccess || !fn)
+            return -1;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)kExhK, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kExhK * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kExhK, (cuuint32_t)kTcRows};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS
+               ? 0
+               : -1;
+}
+
+size_t exh_tc_smem_bytes() { return (size_t)(1 + kTcStages) * kTileBytes + 1024; }
+
+cudaError_t launch_exh_tc(const ExhDesc &E, uint32_t *err, cudaStream_t st) {
+    static bool attr = false;
+    const size_t smem = exh_tc_smem_bytes();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(exh_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    CUtensorMap ma, mb;
+    // rows past the end of A read as zeros (TMA out-of-bounds fill)
+    if (make_f16_map(&ma, E.afp16, E.nr * 8) || make_f16_map(&mb, E.dfp16, E.nd_pad)) return cudaErrorInvalidValue;
+    const int ctas = (E.nr * 8 + kTcRows - 1) / kTcRows;
+    exh_tc_kernel<<<ctas, kTcThreads, smem, st>>>(E, ma, mb, err);
+    return cudaGetLastError();
+}
+
+}  // namespace fic

@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
         ("mode", ctypes.c_int32), ("bmax", ctypes.c_int32), ("bmin", ctypes.c_int32),
         ("thr_rms", ctypes.c_double * 4), ("s_bits", ctypes.c_int32), ("o_bits", ctypes.c_int32),
         ("phase2", ctypes.c_int32), ("local_radius", ctypes.c_int32), ("local_step", ctypes.c_int32),
-        ("dom_step", ctypes.c_int32), ("isometries", ctypes.c_int32),
+        ("dom_step", ctypes.c_int32), ("isometries", ctypes.c_int32), ("engine", ctypes.c_int32),
     ]
 
 
@@ -56,7 +56,7 @@ class StreamC(ctypes.Structure):
 
 
 def params(mode="mns", bmax=32, bmin=4, thr=8.0, s_bits=5, o_bits=7, phase2=True,
-           local_radius=16, local_step=4, dom_step=4, isometries=8) -> Params:
+           local_radius=16, local_step=4, dom_step=4, isometries=8, engine=0) -> Params:
     p = Params()
     p.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     p.bmax, p.bmin = int(bmax), int(bmin)
@@ -68,6 +68,7 @@ def params(mode="mns", bmax=32, bmin=4, thr=8.0, s_bits=5, o_bits=7, phase2=True
     p.phase2 = 1 if phase2 else 0
     p.local_radius, p.local_step = int(local_radius), int(local_step)
     p.dom_step, p.isometries = int(dom_step), int(isometries)
+    p.engine = int(engine)
     return p
 
 

@@ -57,4 +57,4 @@ def test_host_only_calls(libfic):
 def test_record_layout_matches_header():
     from paper_1501_02894_gb300 import fic
     assert fic.RECORD_DTYPE.itemsize == 16
-    assert ctypes.sizeof(fic.Params) == 4 * 3 + 4 + 8 * 4 + 4 * 7 + 4  # padding after bmin and at the end
+    assert ctypes.sizeof(fic.Params) == 4 * 3 + 4 + 8 * 4 + 4 * 8  # padding after bmin
