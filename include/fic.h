@@ -235,6 +235,78 @@ FIC_API void fic_plan_destroy(fic_plan *plan);
 FIC_API int fic_encode_noalloc(const uint8_t *d_img, int width, int height, const fic_params *p,
                                fic_stream *out, void *stream);
 
+/* ---- Serving: continuous batching of encode and decode requests ----
+ * The paper has a single encoder; the server runs many of them at once on
+ * one GPU.  It owns one device allocation of `hbm_budget_bytes` (sub-
+ * allocated per job: image, stream buffers, workspace) and a pinned host
+ * staging area.  fic_submit queues a job and returns at once; a worker
+ * thread admits queued jobs in arrival order as soon as their memory fits
+ * in the budget, forms batches of the admitted jobs (encode jobs sharing
+ * bmax and search family go into one persistent launch, decode jobs into
+ * one decode launch), and runs batches on `streams` CUDA streams so that
+ * work of different batches overlaps on the device.  Jobs that arrive while
+ * others run are admitted as memory frees.  A job whose footprint exceeds
+ * the whole budget is rejected at submit with FIC_EBUDGET. */
+#define FIC_JOB_ENCODE 0
+#define FIC_JOB_DECODE 1
+
+typedef struct fic_server fic_server;
+
+typedef struct fic_server_config {
+    int32_t device;           /* CUDA device ordinal */
+    int32_t streams;          /* concurrent CUDA streams, >= 1 */
+    int32_t max_batch;        /* jobs per batched launch, >= 1 */
+    int32_t queue_capacity;   /* queued + running jobs; fic_submit returns FIC_EBUSY beyond */
+    int64_t hbm_budget_bytes; /* device memory of the server (one allocation at creation) */
+    int64_t host_staging_bytes; /* pinned host memory for inputs/outputs (one allocation) */
+} fic_server_config;
+
+/* A job.  Host buffers stay owned by the caller and must stay valid until
+ * the job completes.  encode: image (width x height, uint8, pitch width) in,
+ * out_records (capacity (width/bmin)*(height/bmin)) and optionally out_split
+ * ((width/bmax)*(height/bmax)) out.  decode: records (canonical order,
+ * nrecords, as an encode produced them) in, out_image (width x height) out,
+ * `iters` decoder iterations. */
+typedef struct fic_job {
+    int32_t kind;
+    int32_t width, height;
+    fic_params params;
+    int32_t iters;
+    int32_t nrecords;
+    const uint8_t *image;
+    const fic_record *records;
+    uint8_t *out_image;
+    fic_record *out_records;
+    uint32_t *out_split;
+} fic_job;
+
+typedef struct fic_job_result {
+    int32_t status;     /* FIC_OK or an error code */
+    int32_t nrecords;   /* encode: records written */
+    int64_t fits;       /* encode: range-domain fits */
+    double latency_ms;  /* submit -> completion */
+    double queue_ms;    /* submit -> launch */
+} fic_job_result;
+
+typedef struct fic_server_stats {
+    int64_t submitted, completed, rejected, batches;
+    int64_t peak_device_bytes;
+    double p50_ms, p99_ms, mean_ms, max_ms; /* latency of completed jobs */
+    double mean_batch;                      /* jobs per batch */
+} fic_server_stats;
+
+FIC_API int fic_server_create(const fic_server_config *cfg, fic_server **out);
+/* Queue a job; *ticket identifies it.  Never blocks on the GPU. */
+FIC_API int fic_submit(fic_server *srv, const fic_job *job, int64_t *ticket);
+/* FIC_EBUSY while the job is queued or running; otherwise the job's
+ * status, with *res filled (the ticket is then released). */
+FIC_API int fic_poll(fic_server *srv, int64_t ticket, fic_job_result *res);
+/* Wait up to timeout_ms (< 0: no limit) for the job; FIC_ETIMEOUT if not done. */
+FIC_API int fic_wait(fic_server *srv, int64_t ticket, int32_t timeout_ms, fic_job_result *res);
+FIC_API int fic_server_get_stats(fic_server *srv, fic_server_stats *st);
+/* Finish every accepted job, stop the worker and free the server. */
+FIC_API int fic_server_destroy(fic_server *srv);
+
 /* Human-readable name of a return code. */
 FIC_API const char *fic_strerror(int code);
 

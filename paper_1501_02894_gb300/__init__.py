@@ -7,6 +7,7 @@ build script (``build.py``); the kernels live in ``csrc/``.
 """
 from .fic import (  # noqa: F401
     RECORD_DTYPE,
+    Server,
     DecodePlan,
     EncodePlan,
     FicError,

@@ -304,9 +304,22 @@ size_t fic_encode_workspace_bytes(int count, const int *widths, const int *heigh
     return enc_layout(count, strips, chunks).total + exh;
 }
 
-int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, const int *heights, int count,
-                           const fic_params *params, fic_stream *outs, void *d_workspace, size_t ws_bytes,
-                           void *stream, fic_plan **plan_out) {
+}  // extern "C"
+
+namespace fic {
+
+size_t encode_plan_staging_bytes(int count) {
+    return align_up(sizeof(TmaMap) * (size_t)count) + align_up(sizeof(EncDesc) * (size_t)count);
+}
+
+size_t decode_plan_staging_bytes(int count) { return align_up(sizeof(DecDesc) * (size_t)count); }
+
+// `staging`, when given, is pinned host memory of encode_plan_staging_bytes
+// that must stay untouched until the plan's work on `stream` has run: the
+// descriptor upload is then a true asynchronous copy.
+int encode_plan_create_staged(const uint8_t *const *d_imgs, const int *widths, const int *heights, int count,
+                              const fic_params *params, fic_stream *outs, void *d_workspace, size_t ws_bytes,
+                              void *stream, uint8_t *staging, fic_plan **plan_out) {
     if (!plan_out || count <= 0 || !d_imgs || !widths || !heights || !params || !outs || !d_workspace)
         return FIC_EBADPARAM;
     *plan_out = nullptr;
@@ -395,10 +408,17 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
             h[(size_t)i].stats = stats + h[(size_t)i].strip_base;
         }
     }
-    cudaError_t e = cudaMemcpyAsync(w, maps.data(), sizeof(TmaMap) * (size_t)count, cudaMemcpyHostToDevice,
+    const void *src_maps = maps.data(), *src_descs = h.data();
+    if (staging) {
+        memcpy(staging, maps.data(), sizeof(TmaMap) * (size_t)count);
+        memcpy(staging + align_up(sizeof(TmaMap) * (size_t)count), h.data(), sizeof(EncDesc) * (size_t)count);
+        src_maps = staging;
+        src_descs = staging + align_up(sizeof(TmaMap) * (size_t)count);
+    }
+    cudaError_t e = cudaMemcpyAsync(w, src_maps, sizeof(TmaMap) * (size_t)count, cudaMemcpyHostToDevice,
                                     static_cast<cudaStream_t>(stream));
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(pl->d_enc, h.data(), sizeof(EncDesc) * (size_t)count, cudaMemcpyHostToDevice,
+        e = cudaMemcpyAsync(pl->d_enc, src_descs, sizeof(EncDesc) * (size_t)count, cudaMemcpyHostToDevice,
                             static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         delete pl;
@@ -406,6 +426,17 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
     }
     *plan_out = pl;
     return FIC_OK;
+}
+
+}  // namespace fic
+
+extern "C" {
+
+int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, const int *heights, int count,
+                           const fic_params *params, fic_stream *outs, void *d_workspace, size_t ws_bytes,
+                           void *stream, fic_plan **plan_out) {
+    return encode_plan_create_staged(d_imgs, widths, heights, count, params, outs, d_workspace, ws_bytes, stream,
+                                     nullptr, plan_out);
 }
 
 int fic_encode_plan_run(const fic_plan *pl, void *stream) {
@@ -465,8 +496,12 @@ size_t fic_decode_workspace_bytes(int count, const int *widths, const int *heigh
     return b + align_up(strips * decode_table_bytes_per_strip());
 }
 
-int fic_decode_plan_create(const fic_stream *sts, int count, uint8_t *const *d_outs, void *d_workspace,
-                           size_t ws_bytes, void *stream, fic_plan **plan_out) {
+}  // extern "C"
+
+namespace fic {
+
+int decode_plan_create_staged(const fic_stream *sts, int count, uint8_t *const *d_outs, void *d_workspace,
+                              size_t ws_bytes, void *stream, uint8_t *staging, fic_plan **plan_out) {
     if (!plan_out || count <= 0 || !sts || !d_outs || !d_workspace) return FIC_EBADPARAM;
     *plan_out = nullptr;
     const int bmax = sts[0].params.bmax;
@@ -527,14 +562,28 @@ int fic_decode_plan_create(const fic_stream *sts, int count, uint8_t *const *d_o
     pl->ws_bytes = ws_bytes;
     pl->d_dec = reinterpret_cast<DecDesc *>(w);
     pl->d_enc = nullptr;
-    cudaError_t e = cudaMemcpyAsync(pl->d_dec, pl->hdec.data(), sizeof(DecDesc) * (size_t)count,
-                                    cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
+    const void *src = pl->hdec.data();
+    if (staging) {
+        memcpy(staging, pl->hdec.data(), sizeof(DecDesc) * (size_t)count);
+        src = staging;
+    }
+    cudaError_t e = cudaMemcpyAsync(pl->d_dec, src, sizeof(DecDesc) * (size_t)count, cudaMemcpyHostToDevice,
+                                    static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         delete pl;
         return FIC_ECUDA;
     }
     *plan_out = pl;
     return FIC_OK;
+}
+
+}  // namespace fic
+
+extern "C" {
+
+int fic_decode_plan_create(const fic_stream *sts, int count, uint8_t *const *d_outs, void *d_workspace,
+                           size_t ws_bytes, void *stream, fic_plan **plan_out) {
+    return decode_plan_create_staged(sts, count, d_outs, d_workspace, ws_bytes, stream, nullptr, plan_out);
 }
 
 int fic_decode_plan_run(const fic_plan *pl, int iters, void *stream) {

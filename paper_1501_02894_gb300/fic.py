@@ -72,6 +72,31 @@ def params(mode="mns", bmax=32, bmin=4, thr=8.0, s_bits=5, o_bits=7, phase2=True
     return p
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("queue_capacity", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
+                ("host_staging_bytes", ctypes.c_int64)]
+
+
+class JobC(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("params", Params), ("iters", ctypes.c_int32), ("nrecords", ctypes.c_int32),
+                ("image", ctypes.c_void_p), ("records", ctypes.c_void_p), ("out_image", ctypes.c_void_p),
+                ("out_records", ctypes.c_void_p), ("out_split", ctypes.c_void_p)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("nrecords", ctypes.c_int32), ("fits", ctypes.c_int64),
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("peak_device_bytes", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("mean_batch", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -106,6 +131,12 @@ def lib():
         L.fic_plan_destroy.argtypes = [vp]
         L.fic_plan_destroy.restype = None
         L.fic_encode_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, P(Params), P(StreamC), vp]
+        L.fic_server_create.argtypes = [P(ServerConfig), P(vp)]
+        L.fic_submit.argtypes = [vp, P(JobC), P(ctypes.c_int64)]
+        L.fic_poll.argtypes = [vp, ctypes.c_int64, P(JobResult)]
+        L.fic_wait.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, P(JobResult)]
+        L.fic_server_get_stats.argtypes = [vp, P(ServerStats)]
+        L.fic_server_destroy.argtypes = [vp]
         L.fic_strerror.argtypes = [ctypes.c_int]
         L.fic_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -319,3 +350,88 @@ class DecodePlan:
 
 def validate(width: int, height: int, p: Params) -> int:
     return int(lib().fic_validate(int(width), int(height), ctypes.byref(p)))
+
+
+JOB_ENCODE, JOB_DECODE = 0, 1
+
+
+class Server:
+    """Continuous-batching request server of the library (fic_submit & co).
+
+    Host buffers of a job (numpy arrays) are kept alive here until the job
+    has been polled or waited for."""
+
+    def __init__(self, hbm_budget_bytes=1 << 30, streams=4, max_batch=64, queue_capacity=100000,
+                 host_staging_bytes=1 << 30, device=None):
+        cfg = ServerConfig()
+        cfg.device = torch.cuda.current_device() if device is None else int(device)
+        cfg.streams, cfg.max_batch, cfg.queue_capacity = int(streams), int(max_batch), int(queue_capacity)
+        cfg.hbm_budget_bytes, cfg.host_staging_bytes = int(hbm_budget_bytes), int(host_staging_bytes)
+        self.handle = ctypes.c_void_p()
+        _check(lib().fic_server_create(ctypes.byref(cfg), ctypes.byref(self.handle)), "fic_server_create")
+        self._live = {}
+
+    def submit_encode(self, image: np.ndarray, p: Params) -> int:
+        image = np.ascontiguousarray(image, dtype=np.uint8)
+        H, W = image.shape
+        cap = (W // p.bmin) * (H // p.bmin)
+        out_rec = np.zeros(max(cap, 1), dtype=RECORD_DTYPE)
+        out_split = np.zeros(max((W // p.bmax) * (H // p.bmax), 1), dtype=np.uint32)
+        j = JobC()
+        j.kind, j.width, j.height, j.params = JOB_ENCODE, W, H, p
+        j.image = image.ctypes.data
+        j.out_records = out_rec.ctypes.data
+        j.out_split = out_split.ctypes.data
+        t = ctypes.c_int64()
+        _check(lib().fic_submit(self.handle, ctypes.byref(j), ctypes.byref(t)), "fic_submit")
+        self._live[t.value] = ("encode", image, out_rec, out_split)
+        return t.value
+
+    def submit_decode(self, records: np.ndarray, W: int, H: int, p: Params, iters: int) -> int:
+        records = np.ascontiguousarray(records, dtype=RECORD_DTYPE)
+        out = np.zeros((H, W), dtype=np.uint8)
+        j = JobC()
+        j.kind, j.width, j.height, j.params, j.iters = JOB_DECODE, W, H, p, int(iters)
+        j.nrecords = len(records)
+        j.records = records.ctypes.data
+        j.out_image = out.ctypes.data
+        t = ctypes.c_int64()
+        _check(lib().fic_submit(self.handle, ctypes.byref(j), ctypes.byref(t)), "fic_submit")
+        self._live[t.value] = ("decode", records, out)
+        return t.value
+
+    def _output(self, ticket, res):
+        ent = self._live.pop(ticket)
+        if ent[0] == "encode":
+            return {"records": ent[2][: res.nrecords].copy(), "split": ent[3].copy(), "fits": int(res.fits),
+                    "latency_ms": res.latency_ms, "queue_ms": res.queue_ms}
+        return {"image": ent[2], "latency_ms": res.latency_ms, "queue_ms": res.queue_ms}
+
+    def poll(self, ticket):
+        res = JobResult()
+        rc = lib().fic_poll(self.handle, ticket, ctypes.byref(res))
+        if rc == -8:
+            return None
+        _check(rc, "fic_poll")
+        return self._output(ticket, res)
+
+    def wait(self, ticket, timeout_ms=-1):
+        res = JobResult()
+        _check(lib().fic_wait(self.handle, ticket, int(timeout_ms), ctypes.byref(res)), "fic_wait")
+        return self._output(ticket, res)
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().fic_server_get_stats(self.handle, ctypes.byref(st)), "fic_server_get_stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().fic_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

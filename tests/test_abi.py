@@ -58,3 +58,23 @@ def test_record_layout_matches_header():
     from paper_1501_02894_gb300 import fic
     assert fic.RECORD_DTYPE.itemsize == 16
     assert ctypes.sizeof(fic.Params) == 4 * 3 + 4 + 8 * 4 + 4 * 8  # padding after bmin
+
+
+def test_server_structs_and_host_checks(libfic):
+    import ctypes as C
+    from paper_1501_02894_gb300 import fic
+    assert C.sizeof(fic.ServerConfig) == 4 * 4 + 8 * 2
+    assert C.sizeof(fic.JobC) == 4 * 3 + 4 + C.sizeof(fic.Params) + 4 * 2 + 8 * 5  # padding before params
+    assert C.sizeof(fic.JobResult) == 4 * 2 + 8 * 3
+    assert C.sizeof(fic.ServerStats) == 8 * 5 + 8 * 5
+    L = fic.lib()
+    cfg = fic.ServerConfig(0, 0, 8, 16, 1 << 20, 1 << 20)  # no streams
+    h = C.c_void_p()
+    assert L.fic_server_create(C.byref(cfg), C.byref(h)) == -2 and not h.value
+    cfg = fic.ServerConfig(0, 1, 8, 16, 0, 1 << 20)       # no budget
+    assert L.fic_server_create(C.byref(cfg), C.byref(h)) == -2
+    t = C.c_int64()
+    assert L.fic_submit(None, None, C.byref(t)) == -2
+    assert L.fic_poll(None, 1, None) == -2
+    assert L.fic_wait(None, 1, 0, None) == -2
+    assert L.fic_server_destroy(None) == -2
