@@ -199,8 +199,10 @@ typedef struct fic_plan fic_plan;
 FIC_API int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, const int *heights,
                            int count, const fic_params *params, fic_stream *outs, void *d_workspace,
                            size_t workspace_bytes, void *stream, fic_plan **plan);
-/* Enqueue the encode of every image of the plan: one small initialisation
- * kernel and one persistent encoder kernel. */
+/* Enqueue the encode of every image of the plan.  No-search, MNS and local
+ * search: one persistent encoder kernel over all images and one pack kernel.
+ * Exhaustive search: four kernels per image (domain and range preparation,
+ * the search, the record writer). */
 FIC_API int fic_encode_plan_run(const fic_plan *plan, void *stream);
 
 /* Same arguments as fic_decode_batch, without the iteration count. */
@@ -210,6 +212,43 @@ FIC_API int fic_decode_plan_create(const fic_stream *sts, int count, uint8_t *co
 FIC_API int fic_decode_plan_run(const fic_plan *plan, int iters, void *stream);
 
 FIC_API void fic_plan_destroy(fic_plan *plan);
+
+/* Run a plan once (as fic_*_plan_run; `iters` is ignored for encode plans)
+ * with a CUDA event after every kernel launch, wait for it and return each
+ * kernel's duration in ms[i] (from the previous kernel's end, so the first
+ * includes any queueing on `stream`) and its name in labels[i] (static
+ * strings; labels may be NULL); *n = number of kernels (at most `cap`;
+ * later kernels still run, untimed).  Synchronous; not for graph capture. */
+FIC_API int fic_plan_run_timed(const fic_plan *plan, int iters, void *stream, float *ms, const char **labels,
+                               int cap, int *n);
+
+/* ---- Launch mapping and its autotuner ----
+ * How the batched kernels map onto the GPU; no choice changes any output
+ * (strips write their records to fixed slots and are packed afterwards).
+ * Applies to no-search / MNS encode plans and to decode plans. */
+typedef struct fic_tuning {
+    int32_t enc_warps;       /* encoder warps per CTA (one strip per warp at a time): 8 or 4 */
+    int32_t enc_ctas_per_sm; /* encoder CTAs per SM; 0 = as many as fit */
+    int32_t enc_dynamic;     /* 1: strips taken from an atomic counter; 0: static grid stride */
+    int32_t dec_ctas_per_sm; /* decoder iteration kernel CTAs per SM; 0 = as many as fit */
+} fic_tuning;
+
+FIC_API int fic_plan_get_tuning(const fic_plan *plan, fic_tuning *t);
+/* FIC_EBADPARAM for values outside the ranges above. */
+FIC_API int fic_plan_set_tuning(fic_plan *plan, const fic_tuning *t);
+/* Time every candidate mapping on the plan's own batch and keep the fastest.
+ * Encode plans try warps {8, 4} x CTAs per SM {1, 2, ..., max} x schedule
+ * {static, dynamic}; decode plans try CTAs per SM {1, ..., max} with `iters`
+ * iterations.  Each candidate runs once untimed, then `reps` times between
+ * CUDA events on `stream`; the score is the median.  Synchronous: returns
+ * after the last run with the plan's outputs written (identical for every
+ * candidate).  *best and *best_ms (either may be NULL) receive the choice
+ * and its median time; `trace` (may be NULL) receives up to `trace_cap`
+ * (candidate, ms) rows as 5 floats each: enc_warps, enc_ctas_per_sm,
+ * enc_dynamic, dec_ctas_per_sm, ms, and *ntrace their number.
+ * Other encode families return FIC_EBADPARAM. */
+FIC_API int fic_plan_autotune(fic_plan *plan, int iters, int reps, void *stream, fic_tuning *best,
+                              float *best_ms, float *trace, int trace_cap, int *ntrace);
 
 /* ---- Allocation-free encode ----
  * The paper has no counterpart to this entry point; it serves callers that

@@ -8,6 +8,7 @@ build script (``build.py``); the kernels live in ``csrc/``.
 from .fic import (  # noqa: F401
     RECORD_DTYPE,
     Server,
+    Tuning,
     DecodePlan,
     EncodePlan,
     FicError,

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of libfic.so: argument checks, descriptor tables,
 // workspace layout and kernel launches.  No allocation happens here: every
 // device buffer (streams, outputs, workspace) belongs to the caller.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -13,6 +14,20 @@
 
 namespace fic {
 cudaError_t launch_exhaustive(const ExhDesc &E, int engine, cudaStream_t st);
+
+// Event recorder of fic_plan_run_timed (active on one thread at a time).
+struct StageMarks {
+    std::vector<cudaEvent_t> ev;
+    std::vector<const char *> label;
+    size_t used = 0;
+};
+thread_local StageMarks *t_marks = nullptr;
+
+void stage_mark(cudaStream_t st, const char *label) {
+    StageMarks *m = t_marks;
+    if (!m || m->used >= m->ev.size()) return;
+    if (cudaEventRecord(m->ev[m->used], st) == cudaSuccess) m->label[m->used++] = label;
+}
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against the driver library).
@@ -48,11 +63,11 @@ int box_width(int bmax, int W) {
 cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int total_strips, uint32_t *status,
                               uint32_t *ticket, cudaStream_t st);
 cudaError_t launch_mns_encode_slots(int bmax, const EncDesc *d_descs, int count, int total_strips, int total_chunks,
-                                    uint32_t *pack_status, cudaStream_t st);
+                                    uint32_t *pack_status, uint32_t *ticket, const EncTune &tune, cudaStream_t st);
 cudaError_t launch_local_encode(int bmax, const EncDesc *d_descs, int count, int total_strips, int total_chunks,
                                 uint32_t *pack_status, cudaStream_t st);
 cudaError_t launch_decode(int bmax, const DecDesc *d_descs, int count, int total_strips, void *tables, int iters,
-                          cudaStream_t st);
+                          const DecTune &tune, cudaStream_t st);
 size_t decode_table_bytes_per_strip();
 int mns_strip_width(int bmax);
 }  // namespace fic
@@ -135,6 +150,8 @@ struct fic_plan {
     void *dec_tables;           // decode: per-strip transform tables
     std::vector<uint8_t *> outs;
     std::vector<size_t> out_bytes;
+    EncTune etune;  // launch mapping (fic_plan_set_tuning / fic_plan_autotune)
+    DecTune dtune;
 };
 
 // Exhaustive search: per image, decimated domains (packed and fp16), domain
@@ -397,7 +414,7 @@ int encode_plan_create_staged(const uint8_t *const *d_imgs, const int *widths, c
     pl->ws_bytes = ws_bytes;
     pl->d_enc = reinterpret_cast<EncDesc *>(w + lay.descs);
     pl->status = reinterpret_cast<uint32_t *>(w + lay.pstatus);
-    pl->ticket = nullptr;
+    pl->ticket = pl->status + chunks;  // the strip counter of the dynamic schedule
     pl->total_chunks = chunks;
     pl->d_dec = nullptr;
     {
@@ -417,6 +434,7 @@ int encode_plan_create_staged(const uint8_t *const *d_imgs, const int *widths, c
     }
     cudaError_t e = cudaMemcpyAsync(w, src_maps, sizeof(TmaMap) * (size_t)count, cudaMemcpyHostToDevice,
                                     static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->ticket, 0, sizeof(uint32_t), static_cast<cudaStream_t>(stream));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(pl->d_enc, src_descs, sizeof(EncDesc) * (size_t)count, cudaMemcpyHostToDevice,
                             static_cast<cudaStream_t>(stream));
@@ -452,10 +470,127 @@ int fic_encode_plan_run(const fic_plan *pl, void *stream) {
         return cuda_rc(launch_local_encode(pl->bmax, pl->d_enc, pl->count, pl->total_strips, pl->total_chunks,
                                            pl->status, static_cast<cudaStream_t>(stream)));
     return cuda_rc(launch_mns_encode_slots(pl->bmax, pl->d_enc, pl->count, pl->total_strips, pl->total_chunks,
-                                           pl->status, static_cast<cudaStream_t>(stream)));
+                                           pl->status, pl->ticket, pl->etune, static_cast<cudaStream_t>(stream)));
 }
 
 void fic_plan_destroy(fic_plan *pl) { delete pl; }
+
+int fic_plan_run_timed(const fic_plan *pl, int iters, void *stream, float *ms, const char **labels, int cap,
+                       int *n) {
+    if (!pl || !ms || !n || cap < 1 || cap > 4096 || (pl->kind == 1 && iters < 0)) return FIC_EBADPARAM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    StageMarks m;
+    m.ev.resize((size_t)cap + 1, nullptr);
+    m.label.resize((size_t)cap + 1, nullptr);
+    int rc = FIC_OK;
+    for (auto &e : m.ev)
+        if (cudaEventCreate(&e) != cudaSuccess) rc = FIC_ECUDA;
+    cudaEvent_t start = m.ev.back();
+    m.ev.pop_back();
+    if (rc == FIC_OK && cudaEventRecord(start, st) != cudaSuccess) rc = FIC_ECUDA;
+    if (rc == FIC_OK) {
+        t_marks = &m;
+        rc = pl->kind == 0 ? fic_encode_plan_run(pl, stream) : fic_decode_plan_run(pl, iters, stream);
+        t_marks = nullptr;
+    }
+    if (rc == FIC_OK && m.used > 0 && cudaEventSynchronize(m.ev[m.used - 1]) != cudaSuccess) rc = FIC_ECUDA;
+    for (size_t i = 0; rc == FIC_OK && i < m.used; ++i) {
+        if (cudaEventElapsedTime(&ms[i], i ? m.ev[i - 1] : start, m.ev[i]) != cudaSuccess) rc = FIC_ECUDA;
+        if (labels) labels[i] = m.label[i];
+    }
+    *n = rc == FIC_OK ? (int)m.used : 0;
+    for (auto e : m.ev)
+        if (e) cudaEventDestroy(e);
+    if (start) cudaEventDestroy(start);
+    return rc;
+}
+
+int fic_plan_get_tuning(const fic_plan *pl, fic_tuning *t) {
+    if (!pl || !t) return FIC_EBADPARAM;
+    t->enc_warps = pl->etune.warps;
+    t->enc_ctas_per_sm = pl->etune.ctas_per_sm;
+    t->enc_dynamic = pl->etune.dynamic;
+    t->dec_ctas_per_sm = pl->dtune.ctas_per_sm;
+    return FIC_OK;
+}
+
+int fic_plan_set_tuning(fic_plan *pl, const fic_tuning *t) {
+    if (!pl || !t) return FIC_EBADPARAM;
+    if ((t->enc_warps != 8 && t->enc_warps != 4) || t->enc_ctas_per_sm < 0 || t->enc_ctas_per_sm > 64 ||
+        (t->enc_dynamic != 0 && t->enc_dynamic != 1) || t->dec_ctas_per_sm < 0 || t->dec_ctas_per_sm > 64)
+        return FIC_EBADPARAM;
+    pl->etune.warps = t->enc_warps;
+    pl->etune.ctas_per_sm = t->enc_ctas_per_sm;
+    pl->etune.dynamic = t->enc_dynamic;
+    pl->dtune.ctas_per_sm = t->dec_ctas_per_sm;
+    return FIC_OK;
+}
+
+int fic_plan_autotune(fic_plan *pl, int iters, int reps, void *stream, fic_tuning *best, float *best_ms,
+                      float *trace, int trace_cap, int *ntrace) {
+    if (!pl || reps < 1 || reps > 1000 || (pl->kind == 0 && pl->family != 0) || (pl->kind == 1 && iters < 1))
+        return FIC_EBADPARAM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // candidate list; CTAs per SM beyond what fits is clamped by the
+    // launcher, so every count up to the register limit is tried
+    std::vector<fic_tuning> cands;
+    fic_tuning cur;
+    fic_plan_get_tuning(pl, &cur);
+    if (pl->kind == 0) {
+        for (int w : {8, 4})
+            for (int k = 1; k <= (w == 8 ? 3 : 4); ++k)
+                for (int dyn = 0; dyn <= 1; ++dyn) cands.push_back(fic_tuning{w, k, dyn, cur.dec_ctas_per_sm});
+    } else {
+        for (int k = 1; k <= 8; ++k) cands.push_back(fic_tuning{cur.enc_warps, cur.enc_ctas_per_sm, cur.enc_dynamic, k});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return FIC_ECUDA;
+    }
+    auto run = [&]() { return pl->kind == 0 ? fic_encode_plan_run(pl, stream) : fic_decode_plan_run(pl, iters, stream); };
+    int rc = FIC_OK, nt = 0, bi = -1;
+    float bms = 0.f;
+    std::vector<float> times((size_t)reps);
+    for (size_t c = 0; c < cands.size() && rc == FIC_OK; ++c) {
+        fic_plan_set_tuning(pl, &cands[c]);
+        rc = run();  // untimed
+        for (int r = 0; r < reps && rc == FIC_OK; ++r) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) rc = FIC_ECUDA;
+            if (rc == FIC_OK) rc = run();
+            if (rc == FIC_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = FIC_ECUDA;
+            if (rc == FIC_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = FIC_ECUDA;
+            if (rc == FIC_OK && cudaEventElapsedTime(&times[(size_t)r], e0, e1) != cudaSuccess) rc = FIC_ECUDA;
+        }
+        if (rc != FIC_OK) break;
+        std::sort(times.begin(), times.end());
+        const float med = times[(size_t)reps / 2];
+        if (trace && nt < trace_cap) {
+            float *row = trace + 5 * nt;
+            row[0] = (float)cands[c].enc_warps;
+            row[1] = (float)cands[c].enc_ctas_per_sm;
+            row[2] = (float)cands[c].enc_dynamic;
+            row[3] = (float)cands[c].dec_ctas_per_sm;
+            row[4] = med;
+            ++nt;
+        }
+        if (bi < 0 || med < bms) {
+            bi = (int)c;
+            bms = med;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != FIC_OK) {
+        fic_plan_set_tuning(pl, &cur);
+        return rc;
+    }
+    fic_plan_set_tuning(pl, &cands[(size_t)bi]);
+    if (best) *best = cands[(size_t)bi];
+    if (best_ms) *best_ms = bms;
+    if (ntrace) *ntrace = nt;
+    return FIC_OK;
+}
 
 int fic_encode_batch(const uint8_t *const *d_imgs, const int *widths, const int *heights, int count,
                      const fic_params *params, fic_stream *outs, void *d_workspace, size_t workspace_bytes,
@@ -596,7 +731,8 @@ int fic_decode_plan_run(const fic_plan *pl, int iters, void *stream) {
         }
         return FIC_OK;
     }
-    return cuda_rc(launch_decode(pl->bmax, pl->d_dec, pl->count, pl->total_strips, pl->dec_tables, iters, st));
+    return cuda_rc(launch_decode(pl->bmax, pl->d_dec, pl->count, pl->total_strips, pl->dec_tables, iters, pl->dtune,
+                                 st));
 }
 
 int fic_decode_batch(const fic_stream *sts, int count, int iters, uint8_t *const *d_outs, void *d_workspace,

@@ -386,22 +386,22 @@ size_t decode_smem_bytes(int bmax) {
     return (size_t)kDecWarps * words * sizeof(uint32_t);
 }
 
-static int grid_for(const void *fn, size_t smem, int &cache) {
-    if (cache == 0) {
-        int dev = 0, sms = 0, per = 0;
+// SM count and resident CTAs per SM of a kernel (cached by the caller).
+static void occupancy_of(const void *fn, size_t smem, int &sms, int &per) {
+    if (per == 0) {
+        int dev = 0, p = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kDecWarps * 32, smem);
-        cache = sms * (per > 0 ? per : 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, kDecWarps * 32, smem);
+        per = p > 0 ? p : 1;
     }
-    return cache;
 }
 
 // Decode: the table setup kernel, then one launch per iteration.
 template <int BMAX>
 static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, void *tables, int iters,
-                             cudaStream_t st) {
-    static int grid_setup = 0, grid_iter = 0;
+                             const DecTune &tune, cudaStream_t st) {
+    static int sms_setup = 0, per_setup = 0, sms_iter = 0, per_iter = 0;
     static bool attr = false;
     const size_t smem = decode_smem_bytes(BMAX);
     if (!attr) {
@@ -414,16 +414,21 @@ static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, 
     uint4 *tfw = reinterpret_cast<uint4 *>(sinfo + total_strips);
     uint4 *tgw = tfw + (size_t)total_strips * 32;
     const int need = (total_strips + kDecWarps - 1) / kDecWarps;
-    const int gs = grid_for((const void *)decode_setup_kernel<BMAX>, 0, grid_setup);
+    occupancy_of((const void *)decode_setup_kernel<BMAX>, 0, sms_setup, per_setup);
+    const int gs = sms_setup * per_setup;
     decode_setup_kernel<BMAX><<<need < gs ? need : gs, kDecWarps * 32, 0, st>>>(descs, count, total_strips, sinfo,
                                                                               tfw, tgw);
+    stage_mark(st, "decode_setup_kernel");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int gi = grid_for((const void *)decode_iter_kernel<BMAX>, smem, grid_iter);
+    occupancy_of((const void *)decode_iter_kernel<BMAX>, smem, sms_iter, per_iter);
+    const int k = tune.ctas_per_sm > 0 && tune.ctas_per_sm < per_iter ? tune.ctas_per_sm : per_iter;
+    const int gi = sms_iter * k;
     const int grid = need < gi ? need : gi;
     for (int it = 0; it < iters; ++it) {
         const int src_sel = (iters - it) & 1;  // the last iteration writes buf[0] (the output)
         decode_iter_kernel<BMAX><<<grid, kDecWarps * 32, smem, st>>>(sinfo, tfw, tgw, total_strips, src_sel, it == 0);
+        stage_mark(st, "decode_iter_kernel");
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -431,11 +436,11 @@ static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, 
 }
 
 cudaError_t launch_decode(int bmax, const DecDesc *d_descs, int count, int total_strips, void *tables, int iters,
-                          cudaStream_t st) {
+                          const DecTune &tune, cudaStream_t st) {
     switch (bmax) {
-    case 32: return dlaunch_t<32>(d_descs, count, total_strips, tables, iters, st);
-    case 16: return dlaunch_t<16>(d_descs, count, total_strips, tables, iters, st);
-    case 8: return dlaunch_t<8>(d_descs, count, total_strips, tables, iters, st);
+    case 32: return dlaunch_t<32>(d_descs, count, total_strips, tables, iters, tune, st);
+    case 16: return dlaunch_t<16>(d_descs, count, total_strips, tables, iters, tune, st);
+    case 8: return dlaunch_t<8>(d_descs, count, total_strips, tables, iters, tune, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -318,10 +318,12 @@ static cudaError_t llaunch_t(const EncDesc *descs, int count, int total_strips, 
     const int need = (total_strips + kLWarps - 1) / kLWarps;
     const int grid = need < grid_cache ? need : grid_cache;
     local_encode_kernel<BMAX><<<grid, kLWarps * 32, smem, st>>>(descs, count, total_strips, pack_status, total_chunks);
+    stage_mark(st, "local_encode_kernel");
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const EncDesc *d_descs, int count, int total_chunks, uint32_t *pack_status, cudaStream_t st);
+cudaError_t launch_pack(const EncDesc *d_descs, int count, int total_chunks, uint32_t *pack_status,
+                        uint32_t *ticket, cudaStream_t st);
 
 cudaError_t launch_local_encode(int bmax, const EncDesc *d_descs, int count, int total_strips, int total_chunks,
                                 uint32_t *pack_status, cudaStream_t st) {
@@ -333,7 +335,7 @@ cudaError_t launch_local_encode(int bmax, const EncDesc *d_descs, int count, int
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    return launch_pack(d_descs, count, total_chunks, pack_status, st);
+    return launch_pack(d_descs, count, total_chunks, pack_status, nullptr, st);
 }
 
 }  // namespace fic

@@ -48,16 +48,19 @@ constexpr int kWarps = 8;
 constexpr int kSlotRecords = 64;  // records a 1024-pixel strip can hold (4x4 leaves)
 constexpr uint32_t kAgg = 1u << 30, kIncl = 2u << 30, kValMask = (1u << 30) - 1;
 
-// SLOTS = true: strips are assigned statically (grid stride) and every strip
-//   writes its records to a fixed slot of the workspace; pack_kernel then
-//   compacts the canonical stream.  No ordering between warps.
+// SLOTS = true: every strip writes its records to a fixed slot of the
+//   workspace and pack_kernel then compacts the canonical stream, so warps
+//   need no ordering: strips are assigned statically (grid stride) or, with
+//   `dyn`, taken from an atomic ticket (pack_kernel resets it).
 // SLOTS = false: strips come from an atomic ticket in stream order and the
 //   stream is packed in place by a decoupled look-back (needs only one status
 //   word per strip of scratch).
-template <int BMAX, bool SLOTS>
-__global__ void __launch_bounds__(kWarps * 32, 3)
+// NW warps per CTA: 8 (registers capped at 80 for 3 CTAs = 24 warps per SM)
+// or 4 (up to 128 registers, no spills, 4 CTAs = 16 warps per SM).
+template <int BMAX, bool SLOTS, int NW>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
     mns_encode_kernel(const EncDesc *__restrict__ descs, int count, int total_strips,
-                      uint32_t *__restrict__ status, uint32_t *__restrict__ ticket, int total_chunks) {
+                      uint32_t *__restrict__ status, uint32_t *__restrict__ ticket, int total_chunks, int dyn) {
     using G = Geom<BMAX>;
     constexpr int PC = G::PC, NP = G::NP;
     constexpr int UPR = BMAX == 32 ? 4 : (BMAX == 16 ? 8 : 16);
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
     constexpr int RAWB = BX::W * BX::H;  // bytes of the staged window (a multiple of 128)
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_base[kImgTable];
-    __shared__ __align__(8) uint64_t s_bar[kWarps];
+    __shared__ __align__(8) uint64_t s_bar[NW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // TMA destinations need 128-byte alignment in the shared window
     uint8_t *const smem_a = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
@@ -106,10 +109,11 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
     };
 
     uint32_t phase = 0;
-    const int gstep = gridDim.x * kWarps;
+    const int gstep = gridDim.x * NW;
+    const bool ticketed = !SLOTS || dyn;
     int g = 0, g_next = 0;
-    if (SLOTS) {
-        g = blockIdx.x * kWarps + warp;
+    if (!ticketed) {
+        g = blockIdx.x * NW + warp;
         g_next = g + gstep;
         if (lane == 0 && g < total_strips) issue_window(g);
     } else {
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
             if (g_next < total_strips) issue_window(g_next);
         }
         int g_after = g_next + gstep;
-        if (!SLOTS && lane == 0) g_after = (int)atomicAdd(ticket, 1u);
+        if (ticketed && lane == 0) g_after = (int)atomicAdd(ticket, 1u);
         int sr_h[2] = {0, 0}, srr_h[2] = {0, 0};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -387,7 +391,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
                 D.tile_off[top0 + lane_top] = (uint32_t)__popcll(mask & ((1ull << (lane_top * cpt)) - 1ull));
             }
             if (lane == 0) D.stats[s] = make_uint2((uint32_t)cnt, ftot & 0x7fffffffu);
-            g = g_next;
+            g = ticketed ? __shfl_sync(FULL, g_next, 0) : g_next;
             g_next = g_after;
             continue;
         }
@@ -468,34 +472,46 @@ __global__ void encode_init_kernel(const EncDesc *__restrict__ descs, int count,
     if (i == 0) *ticket = 0u;
 }
 
-size_t mns_smem_bytes(int bmax) {
+size_t mns_smem_bytes(int bmax, int nw) {
     const size_t per = bmax == 32 ? WinBox<32>::W * WinBox<32>::H + Geom<32>::WORDS * 4
                      : bmax == 16 ? WinBox<16>::W * WinBox<16>::H + Geom<16>::WORDS * 4
                                   : WinBox<8>::W * WinBox<8>::H + Geom<8>::WORDS * 4;
-    return (size_t)kWarps * per + 128;  // + alignment slack
+    return (size_t)nw * per + 128;  // + alignment slack
 }
 
 int mns_strip_width(int bmax) { return 1024 / bmax; }
 
-template <int BMAX, bool SLOTS>
-static cudaError_t launch_t(const EncDesc *descs, int count, int total_strips, uint32_t *status,
-                            uint32_t *ticket, int total_chunks, cudaStream_t st) {
-    static int grid_cache = 0;
-    const size_t smem = mns_smem_bytes(BMAX);
-    if (grid_cache == 0) {
-        cudaError_t e = cudaFuncSetAttribute(mns_encode_kernel<BMAX, SLOTS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per = 0;
+// Resident CTAs per SM of one instantiation (its occupancy limit, cached).
+template <int BMAX, bool SLOTS, int NW>
+static int mns_occupancy(int &sms) {
+    static int per_cache = 0, sms_cache = 0;
+    if (per_cache == 0) {
+        const size_t smem = mns_smem_bytes(BMAX, NW);
+        if (cudaFuncSetAttribute(mns_encode_kernel<BMAX, SLOTS, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return 0;
+        int dev = 0, per = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mns_encode_kernel<BMAX, SLOTS>, kWarps * 32, smem);
-        grid_cache = sms * (per > 0 ? per : 1);
+        cudaDeviceGetAttribute(&sms_cache, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mns_encode_kernel<BMAX, SLOTS, NW>, NW * 32, smem);
+        per_cache = per > 0 ? per : 1;
     }
-    const int need = (total_strips + kWarps - 1) / kWarps;
-    const int grid = need < grid_cache ? need : grid_cache;
-    mns_encode_kernel<BMAX, SLOTS><<<grid, kWarps * 32, smem, st>>>(descs, count, total_strips, status, ticket,
-                                                                    total_chunks);
+    sms = sms_cache;
+    return per_cache;
+}
+
+template <int BMAX, bool SLOTS, int NW>
+static cudaError_t launch_t(const EncDesc *descs, int count, int total_strips, uint32_t *status,
+                            uint32_t *ticket, int total_chunks, int ctas_per_sm, int dyn, cudaStream_t st) {
+    int sms = 0;
+    const int per = mns_occupancy<BMAX, SLOTS, NW>(sms);
+    if (per == 0) return cudaErrorInvalidValue;
+    const int k = ctas_per_sm > 0 && ctas_per_sm < per ? ctas_per_sm : per;
+    const int need = (total_strips + NW - 1) / NW;
+    const int grid = need < sms * k ? need : sms * k;
+    mns_encode_kernel<BMAX, SLOTS, NW><<<grid, NW * 32, mns_smem_bytes(BMAX, NW), st>>>(
+        descs, count, total_strips, status, ticket, total_chunks, dyn);
+    stage_mark(st, "mns_encode_kernel");
     return cudaGetLastError();
 }
 
@@ -517,27 +533,37 @@ cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int t
     cudaError_t e = launch_init(d_descs, count, total_strips, status, ticket, st);
     if (e != cudaSuccess) return e;
     switch (bmax) {
-    case 32: return launch_t<32, false>(d_descs, count, total_strips, status, ticket, 0, st);
-    case 16: return launch_t<16, false>(d_descs, count, total_strips, status, ticket, 0, st);
-    case 8: return launch_t<8, false>(d_descs, count, total_strips, status, ticket, 0, st);
+    case 32: return launch_t<32, false, kWarps>(d_descs, count, total_strips, status, ticket, 0, 0, 1, st);
+    case 16: return launch_t<16, false, kWarps>(d_descs, count, total_strips, status, ticket, 0, 0, 1, st);
+    case 8: return launch_t<8, false, kWarps>(d_descs, count, total_strips, status, ticket, 0, 0, 1, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_pack(const EncDesc *d_descs, int count, int total_chunks, uint32_t *pack_status, cudaStream_t st);
+cudaError_t launch_pack(const EncDesc *d_descs, int count, int total_chunks, uint32_t *pack_status,
+                        uint32_t *ticket, cudaStream_t st);
 
 // Slot variant: encode into per-strip slots, then compact with pack_kernel.
+// `tune` picks warps per CTA, CTAs per SM and the strip schedule; every
+// choice writes the same stream.
 cudaError_t launch_mns_encode_slots(int bmax, const EncDesc *d_descs, int count, int total_strips, int total_chunks,
-                                    uint32_t *pack_status, cudaStream_t st) {
+                                    uint32_t *pack_status, uint32_t *ticket, const EncTune &tune, cudaStream_t st) {
     cudaError_t e;
+    const int k = tune.ctas_per_sm, dyn = tune.dynamic ? 1 : 0;
+    uint32_t *tk = dyn ? ticket : nullptr;
+    const bool w4 = tune.warps == 4;
+#define FIC_SLOTS_LAUNCH(B)                                                                                    \
+    e = w4 ? launch_t<B, true, 4>(d_descs, count, total_strips, pack_status, tk, total_chunks, k, dyn, st)       \
+           : launch_t<B, true, kWarps>(d_descs, count, total_strips, pack_status, tk, total_chunks, k, dyn, st)
     switch (bmax) {
-    case 32: e = launch_t<32, true>(d_descs, count, total_strips, pack_status, nullptr, total_chunks, st); break;
-    case 16: e = launch_t<16, true>(d_descs, count, total_strips, pack_status, nullptr, total_chunks, st); break;
-    case 8: e = launch_t<8, true>(d_descs, count, total_strips, pack_status, nullptr, total_chunks, st); break;
+    case 32: FIC_SLOTS_LAUNCH(32); break;
+    case 16: FIC_SLOTS_LAUNCH(16); break;
+    case 8: FIC_SLOTS_LAUNCH(8); break;
     default: return cudaErrorInvalidValue;
     }
+#undef FIC_SLOTS_LAUNCH
     if (e != cudaSuccess) return e;
-    return launch_pack(d_descs, count, total_chunks, pack_status, st);
+    return launch_pack(d_descs, count, total_chunks, pack_status, tk, st);
 }
 
 }  // namespace fic

@@ -218,18 +218,22 @@ cudaError_t launch_exhaustive(const ExhDesc &E, int engine, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(E.info, 0, FIC_INFO_WORDS * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     exh_prep_domains<<<(E.nd_pad + 255) / 256, 256, 0, st>>>(E);
+    stage_mark(st, "exh_prep_domains");
     exh_prep_ranges<<<(E.nr * 8 + 255) / 256, 256, 0, st>>>(E);
+    stage_mark(st, "exh_prep_ranges");
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (engine == 1) {
         const int ranges_per_cta = kExhWarps * 4;
         exh_cuda_kernel<<<(E.nr + ranges_per_cta - 1) / ranges_per_cta, kExhWarps * 32, 0, st>>>(E);
+        stage_mark(st, "exh_cuda_kernel");
         e = cudaGetLastError();
     } else {
         e = launch_exh_tc(E, E.info + FIC_INFO_ERROR, st);
     }
     if (e != cudaSuccess) return e;
     exh_finalize<<<(E.nr + 255) / 256, 256, 0, st>>>(E);
+    stage_mark(st, "exh_finalize");
     return cudaGetLastError();
 }
 

@@ -310,6 +310,7 @@ cudaError_t launch_exh_tc(const ExhDesc &E, uint32_t *err, cudaStream_t st) {
     if (make_f16_map(&ma, E.afp16, E.nr * 8) || make_f16_map(&mb, E.dfp16, E.nd_pad)) return cudaErrorInvalidValue;
     const int ctas = (E.nr * 8 + kTcRows - 1) / kTcRows;
     exh_tc_kernel<<<ctas, kTcThreads, smem, st>>>(E, ma, mb, err);
+    stage_mark(st, "exh_tc_kernel");
     return cudaGetLastError();
 }
 

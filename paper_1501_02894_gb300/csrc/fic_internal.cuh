@@ -54,6 +54,22 @@ struct WinBox {
 // (host side; the driver entry point is looked up once).
 int make_tma_map(TmaMap *out, const void *base, int W, int H, int boxw, int boxh);
 
+// Per-kernel timing of a plan run (fic_plan_run_timed): launchers call this
+// after every kernel launch; it records an event only while a timed run is
+// active on the calling thread.
+void stage_mark(cudaStream_t st, const char *label);
+
+// Launch mapping of the batched encoder and decoder (chosen by the
+// autotuner; every choice produces the same output).
+struct EncTune {
+    int warps = 8;        // warps per CTA: 8 or 4 (one strip per warp at a time)
+    int ctas_per_sm = 0;  // resident CTAs per SM; 0 = the occupancy limit
+    int dynamic = 0;      // 1: strips from an atomic counter, 0: static grid stride
+};
+struct DecTune {
+    int ctas_per_sm = 0;  // resident CTAs per SM of the iteration kernel; 0 = the occupancy limit
+};
+
 // One image of a decode launch.
 struct DecDesc {
     const fic_record *rec;

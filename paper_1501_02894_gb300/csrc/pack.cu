@@ -23,13 +23,17 @@ constexpr int kSlotRecs = 64;
 // are scheduled first, so a look-back only waits on chunks already running;
 // the wait is bounded in any case).
 __global__ void __launch_bounds__(kPackWarps * 32)
-    pack_kernel(const EncDesc *__restrict__ descs, int count, int total_chunks, uint32_t *__restrict__ pstatus) {
+    pack_kernel(const EncDesc *__restrict__ descs, int count, int total_chunks, uint32_t *__restrict__ pstatus,
+                uint32_t *__restrict__ ticket) {
     __shared__ int s_cb[kImgTable];
     __shared__ int s_img, s_ok;
     __shared__ uint32_t s_cnt[32], s_off[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned FULL = 0xffffffffu;
     const int c = blockIdx.x;
+    // the encoder's strip counter (dynamic schedule) is free again: reset it
+    // for the next launch
+    if (ticket && c == 0 && threadIdx.x == 0) *ticket = 0u;
     if (count <= kImgTable)
         for (int i = threadIdx.x; i < count; i += blockDim.x) s_cb[i] = descs[i].chunk_base;
     __syncthreads();
@@ -140,9 +144,11 @@ __global__ void __launch_bounds__(kPackWarps * 32)
     }
 }
 
-cudaError_t launch_pack(const EncDesc *d_descs, int count, int total_chunks, uint32_t *pack_status, cudaStream_t st) {
+cudaError_t launch_pack(const EncDesc *d_descs, int count, int total_chunks, uint32_t *pack_status,
+                        uint32_t *ticket, cudaStream_t st) {
     if (total_chunks <= 0) return cudaSuccess;
-    pack_kernel<<<total_chunks, kPackWarps * 32, 0, st>>>(d_descs, count, total_chunks, pack_status);
+    pack_kernel<<<total_chunks, kPackWarps * 32, 0, st>>>(d_descs, count, total_chunks, pack_status, ticket);
+    stage_mark(st, "pack_kernel");
     return cudaGetLastError();
 }
 

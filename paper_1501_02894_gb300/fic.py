@@ -72,6 +72,14 @@ def params(mode="mns", bmax=32, bmin=4, thr=8.0, s_bits=5, o_bits=7, phase2=True
     return p
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("enc_warps", ctypes.c_int32), ("enc_ctas_per_sm", ctypes.c_int32), ("enc_dynamic", ctypes.c_int32),
+                ("dec_ctas_per_sm", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
@@ -129,6 +137,12 @@ def lib():
         L.fic_decode_plan_create.argtypes = [P(StreamC), ctypes.c_int, P(vp), vp, ctypes.c_size_t, vp, P(vp)]
         L.fic_decode_plan_run.argtypes = [vp, ctypes.c_int, vp]
         L.fic_plan_destroy.argtypes = [vp]
+        L.fic_plan_get_tuning.argtypes = [vp, P(Tuning)]
+        L.fic_plan_run_timed.argtypes = [vp, ctypes.c_int, vp, P(ctypes.c_float), P(ctypes.c_char_p), ctypes.c_int,
+                                         P(ctypes.c_int)]
+        L.fic_plan_set_tuning.argtypes = [vp, P(Tuning)]
+        L.fic_plan_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, P(Tuning), P(ctypes.c_float),
+                                        P(ctypes.c_float), ctypes.c_int, P(ctypes.c_int)]
         L.fic_plan_destroy.restype = None
         L.fic_encode_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, P(Params), P(StreamC), vp]
         L.fic_server_create.argtypes = [P(ServerConfig), P(vp)]
@@ -291,7 +305,43 @@ def fic_decode_batch(sts, iters: int, outs=None, workspace=None, stream=None):
     return outs
 
 
-class EncodePlan:
+class _Tunable:
+    """Launch mapping of a plan (fic_plan_get_tuning / set / autotune)."""
+
+    @property
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().fic_plan_get_tuning(self.handle, ctypes.byref(t)), "fic_plan_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = Tuning()
+        _check(lib().fic_plan_get_tuning(self.handle, ctypes.byref(t)), "fic_plan_get_tuning")
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        _check(lib().fic_plan_set_tuning(self.handle, ctypes.byref(t)), "fic_plan_set_tuning")
+
+    def _run_timed(self, iters, stream, cap=256):
+        ms = (ctypes.c_float * cap)()
+        labels = (ctypes.c_char_p * cap)()
+        n = ctypes.c_int()
+        _check(lib().fic_plan_run_timed(self.handle, int(iters), _stream_handle(stream), ms, labels, cap,
+                                        ctypes.byref(n)), "fic_plan_run_timed")
+        return [(labels[i].decode(), float(ms[i])) for i in range(n.value)]
+
+    def _autotune(self, iters, reps, stream):
+        best, ms, n = Tuning(), ctypes.c_float(), ctypes.c_int()
+        cap = 64
+        trace = (ctypes.c_float * (5 * cap))()
+        _check(lib().fic_plan_autotune(self.handle, int(iters), int(reps), _stream_handle(stream), ctypes.byref(best),
+                                       ctypes.byref(ms), trace, cap, ctypes.byref(n)), "fic_plan_autotune")
+        rows = [tuple(trace[5 * i: 5 * i + 5]) for i in range(n.value)]
+        keys = ("enc_warps", "enc_ctas_per_sm", "enc_dynamic", "dec_ctas_per_sm")
+        return {"best": best.as_dict(), "best_ms": ms.value,
+                "trials": [dict({k: int(r[j]) for j, k in enumerate(keys)}, ms=round(r[4], 5)) for r in rows]}
+
+
+class EncodePlan(_Tunable):
     """Prepared batch encode: `run()` only enqueues kernels (graph-capturable)."""
 
     def __init__(self, imgs, plist, outs=None, workspace=None, stream=None):
@@ -317,6 +367,13 @@ class EncodePlan:
     def run(self, stream=None):
         _check(lib().fic_encode_plan_run(self.handle, _stream_handle(stream)), "fic_encode_plan_run")
 
+    def autotune(self, reps=5, stream=None):
+        return self._autotune(0, reps, stream)
+
+    def run_timed(self, stream=None):
+        """Run once; [(kernel name, ms)] per launch (synchronous)."""
+        return self._run_timed(0, stream)
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value and _lib is not None:
@@ -324,7 +381,7 @@ class EncodePlan:
             self.handle = None
 
 
-class DecodePlan:
+class DecodePlan(_Tunable):
     def __init__(self, sts, outs=None, workspace=None, stream=None):
         n = len(sts)
         dev = sts[0].records.device
@@ -340,6 +397,13 @@ class DecodePlan:
 
     def run(self, iters: int, stream=None):
         _check(lib().fic_decode_plan_run(self.handle, int(iters), _stream_handle(stream)), "fic_decode_plan_run")
+
+    def autotune(self, iters: int, reps=5, stream=None):
+        return self._autotune(iters, reps, stream)
+
+    def run_timed(self, iters: int, stream=None):
+        """Run once; [(kernel name, ms)] per launch (synchronous)."""
+        return self._run_timed(iters, stream)
 
     def __del__(self):
         h = getattr(self, "handle", None)
