@@ -1,15 +1,27 @@
 """Benchmark of the MNS fractal coder on GB300.
 
-One step = the whole hot path over one batch: the MNS quadtree encode
-(moments, phase 1, phase 2, split, stream packing) of the ten 512x512
-synthetic images shaped like the paper's test images (8 scenes + 2 Voronoi
-images) at each RMS threshold of the sweep {4, 8, 12, 16} -- 40 encodes in
-one persistent launch -- followed by the 10-iteration decode of all 40
-streams.  The step is captured in CUDA graphs and replayed; L2 is flushed
-(a 256 MiB write) before every timed step because the inputs (2.6 MB) are
-far smaller than L2.
+Default workload (cfg2): one step = the whole hot path over one batch: the
+MNS quadtree encode (moments, phase 1, phase 2, split, stream packing) of the
+ten 512x512 synthetic images shaped like the paper's test images (8 scenes +
+2 Voronoi images) at each RMS threshold of the sweep {4, 8, 12, 16} -- 40
+encodes in one persistent launch -- followed by the 10-iteration decode of
+all 40 streams.  The step is captured in CUDA graphs and replayed; L2 is
+flushed (a 256 MiB write) before every timed step because the inputs
+(10.5 MB) are far smaller than L2.
+
+Other workloads (`--workload`), one JSON line each:
+  cfg1  one 256x256 image, MNS 16->4, RMS 8, decode 10 iterations
+  cfg3  exhaustive search (8 isometries, domain step 4, 8x8 ranges) of a
+        512x512 and a 1024x1024 image: tensor-core and CUDA-core engines
+  cfg4  512 images of mixed sides {256..2048} in one persistent launch per
+        pass (CUDA graphs, autotuned launch mapping), MNS 32->4, RMS 8,
+        decode 8 iterations; against per-image launches with the same output
+  cfg5  serving: Poisson arrivals (2000/s), 80 % encode / 20 % decode,
+        sides log-uniform in [128, 4096], through the library's request
+        server; p50/p99 latency and Mpixel/s against a per-request loop
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload cfg2|cfg1|cfg3|cfg4|cfg5]
 
 With N > 1 (torchrun) every rank runs the same workload on its own GPU
 (replicas, weak scaling); rank 0 prints one JSON line.  `--impl reference`
@@ -37,25 +49,72 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 THRESHOLDS = [4.0, 8.0, 12.0, 16.0]
-DECODE_ITERS = 10
 METRIC = "MNS encode Mpixel/s & range-domain fits/s (bit-exact); served p50/p99 latency"
-WORKLOAD = "cfg2: 10 x 512x512 (8 scenes seeds 1-8 + 2 Voronoi 101/102) x RMS {4,8,12,16}, MNS 32->4 + decode 10 it"
+L2_BYTES = 129 << 20
 
 
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return d, "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def workload():
-    imgs = [im for _, im in synth.cfg2_images()]
-    batch = [(im, t) for t in THRESHOLDS for im in imgs]
-    return batch
+# --------------------------------------------------------------------------
+# Workloads
 
+class Spec:
+    """A batched workload: items (image, mode, bmax, bmin, thr), decode iterations."""
+
+    def __init__(self, name, desc, items, iters, autotune=False, plain=False):
+        self.name, self.desc, self.items, self.iters = name, desc, items, iters
+        self.autotune, self.plain = autotune, plain
+
+    @property
+    def pixels(self):
+        return sum(im.size for im, *_ in self.items)
+
+
+def _gen(args):
+    kind, n, seed = args
+    return synth.gaussian_scene(n, seed) if kind == "g" else synth.voronoi(n, seed)
+
+
+def gen_images(specs, workers=None):
+    """Generate synthetic images in a process pool (spawned: safe before or
+    after CUDA initialisation)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    if len(specs) < 8:
+        return [_gen(s) for s in specs]
+    workers = workers or min(16, os.cpu_count() or 1)
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen, specs, chunksize=4))
+
+
+def make_spec(name):
+    if name == "cfg1":
+        return Spec(name, "cfg1: 256x256 scene seed 0, MNS 16->8->4, RMS 8 + decode 10 it",
+                    [(synth.cfg1_image(), "mns", 16, 4, 8.0)], 10)
+    if name == "cfg2":
+        imgs = [im for _, im in synth.cfg2_images()]
+        return Spec(name, "cfg2: 10 x 512x512 (8 scenes seeds 1-8 + 2 Voronoi 101/102) x RMS {4,8,12,16}, "
+                          "MNS 32->4 + decode 10 it",
+                    [(im, "mns", 32, 4, t) for t in THRESHOLDS for im in imgs], 10)
+    if name == "cfg4":
+        sides = synth.cfg4_sides()
+        imgs = gen_images([("g", int(s), 1000 + i) for i, s in enumerate(sides)])
+        return Spec(name, "cfg4: 512 scenes, sides {256,512,1024,2048} w .4/.3/.2/.1 (rng 4, seed 1000+i), "
+                          "MNS 32->4, RMS 8 + decode 8 it, one persistent launch per pass",
+                    [(im, "mns", 32, 4, 8.0) for im in imgs], 8, autotune=True, plain=True)
+    raise ValueError(name)
+
+
+# --------------------------------------------------------------------------
+# Measurement helpers
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
@@ -121,85 +180,37 @@ def traffic_from_profile(kernel_key: str):
         with open(path) as f:
             prof = json.load(f)
         ent = prof[kernel_key]
-        src = os.path.join(ROOT, ent["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if h != ent["source_sha256_16"]:
-            return None
+        for src, h0 in ent["sources"].items():
+            h = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+            if h != h0:
+                return None
         return float(ent["bytes_per_launch"])
     except Exception:
         return None
 
 
-# --------------------------------------------------------------------------
-# CPU oracle (the reference arm and the cpu_baseline object)
-
-def time_oracle(batch, budget_s: float, threads: int):
-    """Encode + decode as many (image, threshold) pairs as fit in the budget,
-    spread over `threads` host threads.  Returns (Mpixel/s, pairs done)."""
-    from concurrent.futures import ThreadPoolExecutor
-
-    from oracle import oracle as O
-
-    O.lib()
-
-    def one(item):
-        im, t = item
-        p = O.make_params("mns", 32, 4, t)
-        leaves, _, _ = O.encode(im, p)
-        O.decode(leaves, im.shape[1], im.shape[0], p, DECODE_ITERS)
-        return im.size
-
-    t0 = time.perf_counter()
-    done_px = 0
-    done = 0
-    i = 0
-    with ThreadPoolExecutor(max_workers=threads) as ex:
-        while time.perf_counter() - t0 < budget_s:
-            chunk = [batch[(i + j) % len(batch)] for j in range(threads)]
-            i += threads
-            for px in ex.map(one, chunk):
-                done_px += px
-                done += 1
-    dt = time.perf_counter() - t0
-    return done_px / dt / 1e6, done, dt
+def gpu_uuid(torch, dev):
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return str(dev.index or 0)
 
 
-def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return 0
-    batch = workload()
-    threads = os.cpu_count() or 1
-    vals = []
-    total_px = sum(im.size for im, _ in batch)
-    # each step is a bounded sample so that the whole run stays within minutes
-    step_s = max(0.5, min(args.ref_step_s, 150.0 / max(1, args.steps + args.warmup)))
-    args.ref_step_s = step_s
-    for _ in range(args.warmup):
-        time_oracle(batch, min(0.5, step_s), threads)
-    for _ in range(args.steps):
-        v, n, dt = time_oracle(batch, step_s, threads)
-        vals.append(v)
-    value = statistics.mean(vals)
-    line = {
-        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(total_px / (value * 1e6) * 1e3, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "mode": "mns", "sample": f"{args.ref_step_s:.0f} s of oracle work per step"},
-        "cpu_baseline": {"value": round(value, 3), "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
-                         "sample": f"(image, threshold) pairs of the batch, encode + {DECODE_ITERS}-iteration decode, "
-                                   f"{args.ref_step_s:.0f} s per step on {threads} threads"},
-        "e2e": {"value": round(value, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
-    return 0
+def kernel_table(rows_per_step):
+    """[(name, ms)] lists of several steps -> per-kernel launches/step, mean ms per launch, share."""
+    agg = {}
+    for rows in rows_per_step:
+        for name, ms in rows:
+            a = agg.setdefault(name, [0, 0.0])
+            a[0] += 1
+            a[1] += ms
+    steps = max(1, len(rows_per_step))
+    total = sum(v[1] for v in agg.values()) or 1.0
+    return {k: {"launches_per_step": v[0] // steps, "ms_per_launch": round(v[1] / v[0], 5),
+                "share": round(v[1] / total, 4)} for k, v in sorted(agg.items(), key=lambda kv: -kv[1][1])}
 
 
-# --------------------------------------------------------------------------
-# GPU arm
-
-def run_ours(args):
+def dist_setup():
     import torch
     import torch.distributed as dist
 
@@ -209,75 +220,198 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    return world, rank, torch.device("cuda", local)
 
+
+def max_over_ranks(world, dev, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_finish(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline object)
+
+def time_oracle(items, iters, budget_s: float, threads: int):
+    """Encode + decode as many items as fit in the budget, spread over
+    `threads` host threads.  Returns (Mpixel/s, items done, seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import oracle as O
+
+    O.lib()
+
+    def one(item):
+        im, mode, bmax, bmin, t = item
+        p = O.make_params(mode, bmax, bmin, t)
+        leaves, _, _ = O.encode(im, p)
+        O.decode(leaves, im.shape[1], im.shape[0], p, iters)
+        return im.size
+
+    t0 = time.perf_counter()
+    done_px = done = i = 0
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        while time.perf_counter() - t0 < budget_s:
+            chunk = [items[(i + j) % len(items)] for j in range(threads)]
+            i += threads
+            for px in ex.map(one, chunk):
+                done_px += px
+                done += 1
+    dt = time.perf_counter() - t0
+    return done_px / dt / 1e6, done, dt
+
+
+def time_oracle_exhaustive(img, budget_s: float, threads: int, dom_step=4, isos=8):
+    """Exhaustive search of sampled 8x8 ranges of `img` for `budget_s`
+    seconds.  Returns (fits/s, ranges done, seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import oracle as O
+
+    O.lib()
+    p = O.make_params("exhaustive", 8, 8, 8.0, dom_step=dom_step, isometries=isos)
+    H, W = img.shape
+    nd = ((W - 16) // dom_step + 1) * ((H - 16) // dom_step + 1)
+    rng = np.random.default_rng(7)
+
+    def one(k):
+        xs = rng.integers(0, W // 8, size=4) * 8
+        ys = rng.integers(0, H // 8, size=4) * 8
+        O.search_ranges(img, p, xs, ys, np.full(4, 8))
+        return 4
+
+    t0 = time.perf_counter()
+    done = 0
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        while time.perf_counter() - t0 < budget_s:
+            done += sum(ex.map(one, range(threads)))
+    dt = time.perf_counter() - t0
+    return done * nd * isos / dt, done, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    step_s = max(0.5, min(args.ref_step_s, 150.0 / max(1, args.steps + args.warmup)))
+    if args.workload == "cfg3":
+        img = synth.cfg3_images()[1][1]
+        for _ in range(args.warmup):
+            time_oracle_exhaustive(img, min(0.5, step_s), threads)
+        vals = [time_oracle_exhaustive(img, step_s, threads)[0] for _ in range(args.steps)]
+        value, unit, desc = statistics.mean(vals), "fits/s", "exhaustive search, sampled 8x8 ranges of the 1024x1024 image"
+        ms, metric = None, "exhaustive-search range-domain fits/s (bit-exact)"
+    elif args.workload == "cfg5":
+        print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no CPU counterpart; "
+                                                              "the oracle arm covers cfg1-cfg4"}), flush=True)
+        return 0
+    else:
+        spec = make_spec(args.workload)
+        for _ in range(args.warmup):
+            time_oracle(spec.items, spec.iters, min(0.5, step_s), threads)
+        vals = [time_oracle(spec.items, spec.iters, step_s, threads)[0] for _ in range(args.steps)]
+        value, unit, desc = statistics.mean(vals), "Mpixel/s", spec.desc
+        ms, metric = round(spec.pixels / (value * 1e6) * 1e3, 3), METRIC
+    line = {
+        "impl": "reference", "metric": metric, "value": round(value, 3), "unit": unit,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": desc, "sample": f"{step_s:.0f} s of oracle work per step"},
+        "cpu_baseline": {"value": round(value, 3), "unit": unit, "cores": threads, "kind": "oracle",
+                         "sample": f"items of the workload, {step_s:.0f} s per step on {threads} threads"},
+        "e2e": {"value": round(value, 3), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm: batched encode + decode (cfg1, cfg2, cfg4)
+
+def run_batched(args, spec: Spec):
+    import torch
+
+    world, rank, dev = dist_setup()
     import paper_1501_02894_gb300 as fic
 
     fic.lib()
-    batch = workload()
-    n = len(batch)
-    pixels = sum(im.size for im, _ in batch)
-    plist = [fic.params("mns", 32, 4, t) for _, t in batch]
-    host = [torch.from_numpy(im).pin_memory() for im, _ in batch]
+    items = spec.items
+    n = len(items)
+    pixels = spec.pixels
+    iters = spec.iters
+    plist = [fic.params(m, bmax, bmin, t) for _, m, bmax, bmin, t in items]
+    host = [torch.from_numpy(it[0]).pin_memory() for it in items]
     dimgs = [h.to(dev) for h in host]
     stream = torch.cuda.Stream(dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush_l2 = pixels < 2 * L2_BYTES
+    flush = torch.empty(256 << 20 if flush_l2 else 1, dtype=torch.uint8, device=dev)
 
     with torch.cuda.stream(stream):
         enc = fic.EncodePlan(dimgs, plist, stream=stream)
         enc.run(stream)
         dec = fic.DecodePlan(enc.outs, stream=stream)
-        dec.run(DECODE_ITERS, stream)
+        dec.run(iters, stream)
     stream.synchronize()
-    nrec = []
-    fits = 0
+    tuning = None
+    if spec.autotune:
+        with torch.cuda.stream(stream):
+            te = enc.autotune(reps=3, stream=stream)
+            td = dec.autotune(iters, reps=3, stream=stream)
+        tuning = {"encode": te, "decode": td}
+    nrec, fits = [], 0
     for st in enc.outs:
         r, f = st.info_host(stream)
         nrec.append(r)
         fits += f
     ntops = [st.ntop for st in enc.outs]
 
-    # CUDA graphs: one for the encode launch, one for the decode iterations
     g_enc, g_dec = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
     with torch.cuda.stream(stream):
         with torch.cuda.graph(g_enc, stream=stream):
             enc.run(stream)
         with torch.cuda.graph(g_dec, stream=stream):
-            dec.run(DECODE_ITERS, stream)
+            dec.run(iters, stream)
     stream.synchronize()
-    launches_per_step = 2 + 1 + DECODE_ITERS  # encoder + pack, decode setup + one launch per iteration
+    with torch.cuda.stream(stream):
+        launches_per_step = len(enc.run_timed(stream)) + len(dec.run_timed(iters, stream))
 
-    def step():
-        g_enc.replay()
-        g_dec.replay()
-
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        gpu_id = str(local)
-    sampler = ClockSampler(gpu_id)
+    sampler = ClockSampler(gpu_uuid(torch, dev))
     sampler.start()
     time.sleep(0.2)
-    # warm-up steps, then keep the GPU busy for --heat-s seconds (clock sampling)
+    warm = max(args.warmup, 3)
     with torch.cuda.stream(stream):
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(warm):
             flush.fill_(1)
-            step()
+            g_enc.replay()
+            g_dec.replay()
     stream.synchronize()
     t_heat = time.perf_counter()
     while time.perf_counter() - t_heat < args.heat_s:
         with torch.cuda.stream(stream):
-            for _ in range(20):
+            for _ in range(5 if pixels > 64 << 20 else 20):
                 flush.fill_(1)
-                step()
+                g_enc.replay()
+                g_dec.replay()
         stream.synchronize()
-    # outputs of the graphs must equal those of the direct launch
     ref0 = enc.outs[0].to_host(stream)
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     if world > 1:
-        dist.barrier()
+        torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     t_wall0 = time.perf_counter()
     with torch.cuda.stream(stream):
@@ -295,28 +429,29 @@ def run_ours(args):
     clocks = sampler.stop()
     enc_ms = [a.elapsed_time(b) for a, b, _ in ev]
     dec_ms = [b.elapsed_time(c) for _, b, c in ev]
-    step_ms = [e + d for e, d in zip(enc_ms, dec_ms)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
+    ms_per_step = max_over_ranks(world, dev, sum(e + d for e, d in zip(enc_ms, dec_ms)) / args.steps)
     value = world * pixels / (ms_per_step * 1e-3) / 1e6
-
     chk = enc.outs[0].to_host(stream)
     assert np.array_equal(chk["records"].view(np.uint8), ref0["records"].view(np.uint8)), "graph replay changed output"
 
+    # ---- per-kernel durations: the same step with an event after every kernel
+    krows = []
+    with torch.cuda.stream(stream):
+        for i in range(min(args.steps, 20)):
+            flush.fill_(i & 0xff)
+            krows.append(enc.run_timed(stream) + dec.run_timed(iters, stream))
+    ktab = kernel_table(krows)
+
     # ---- end to end through the public API: pinned host images in, streams and
     # decoded images out, copies inside the timed region
-    out_host = [torch.empty((512, 512), dtype=torch.uint8).pin_memory() for _ in range(n)]
+    out_host = [torch.empty(tuple(it[0].shape), dtype=torch.uint8).pin_memory() for it in items]
     rec_host = [torch.empty(st.records.numel(), dtype=torch.uint8).pin_memory() for st in enc.outs]
     info_host = torch.empty((n, 16), dtype=torch.int32).pin_memory()
     h2d = pixels
     d2h = pixels + sum(16 * r for r in nrec) + 64 * n
     e2e_ev = []
     with torch.cuda.stream(stream):
-        for i in range(max(args.warmup, 3) + args.steps):
+        for i in range(warm + args.steps):
             s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             flush.fill_(i & 0xff)
             s0.record(stream)
@@ -331,40 +466,33 @@ def run_ours(args):
             s1.record(stream)
             e2e_ev.append((s0, s1))
     stream.synchronize()
-    e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev[max(args.warmup, 3):]]
-    e2e_ms_mean = sum(e2e_ms) / len(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_ms_mean], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms_mean = float(t.item())
-    e2e_value = world * pixels / (e2e_ms_mean * 1e-3) / 1e6
+    e2e_ms = max_over_ranks(world, dev, statistics.mean(a.elapsed_time(b) for a, b in e2e_ev[warm:]))
+    e2e_value = world * pixels / (e2e_ms * 1e-3) / 1e6
 
     # ---- roofline of the dominant kernel (HBM bound): algorithmic bytes per launch
-    peak, peak_kind = load_peaks()
-    enc_bytes = sum(im.size for im, _ in batch) + sum(16 * r for r in nrec) + sum(8 * t + 4 for t in ntops)
+    peaks, peak_kind = load_peaks()
+    peak = float(peaks["hbm_gbs"])
+    enc_bytes = pixels + sum(16 * r for r in nrec) + sum(8 * t + 4 for t in ntops)
     dec_bytes_iter = 2 * pixels + sum(16 * r for r in nrec) + sum(4 * (t + 1) for t in ntops)
-    enc_launch_ms = sum(enc_ms) / len(enc_ms)
-    dec_launch_ms = sum(dec_ms) / len(dec_ms) / DECODE_ITERS
-    enc_gbs = enc_bytes / (enc_launch_ms * 1e-3) / 1e9
-    dec_gbs = dec_bytes_iter / (dec_launch_ms * 1e-3) / 1e9
-    if sum(enc_ms) >= sum(dec_ms):
-        dom, ach, key = "mns_encode_kernel", enc_gbs, "mns_encode_kernel_cfg2"
-    else:
-        dom, ach, key = "decode_iter_kernel", dec_gbs, "decode_iter_kernel_cfg2"
+    alg = {"mns_encode_kernel": enc_bytes, "decode_iter_kernel": dec_bytes_iter}
+    dom = max((k for k in ktab if k in alg), key=lambda k: ktab[k]["share"])
+    ach = alg[dom] / (ktab[dom]["ms_per_launch"] * 1e-3) / 1e9
+    key = f"{dom}_{spec.name}"
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "peak_kind": peak_kind, "traffic": traffic_from_profile(key),
-                "kernels": {"mns_encode": {"ms_per_launch": round(enc_launch_ms, 5), "alg_bytes": enc_bytes,
-                                           "GB_s": round(enc_gbs, 1)},
-                            "decode_iter": {"ms_per_launch": round(dec_launch_ms, 5), "alg_bytes": dec_bytes_iter,
-                                            "GB_s": round(dec_gbs, 1)}}}
+                "alg_bytes_per_launch": alg[dom],
+                "kernels": {k: dict(v, GB_s=round(alg[k] / (v["ms_per_launch"] * 1e-3) / 1e9, 1)) if k in alg else v
+                            for k, v in ktab.items()}}
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+        "warmup": warm, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "images": n, "pixels_per_step": pixels, "l2": "flushed (256 MiB write) before every step",
+        "config": {"workload": spec.desc, "images": n, "pixels_per_step": pixels,
+                   "l2": "flushed (256 MiB write) before every step" if flush_l2 else
+                         f"not flushed: inputs ({pixels / 2**20:.0f} MiB) larger than L2",
                    "parallelism": f"replicas x{world}", "graph": "CUDA graphs (encode, decode)"},
-        "encode_mpix_s": round(world * pixels / (sum(enc_ms) / len(enc_ms) * 1e-3) / 1e6, 3),
+        "encode_mpix_s": round(world * pixels / (statistics.mean(enc_ms) * 1e-3) / 1e6, 3),
         "fits_per_s": round(world * fits / (ms_per_step * 1e-3), 1),
         "fits_per_step": fits,
         "records_per_step": int(sum(nrec)),
@@ -375,17 +503,342 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
+    if tuning:
+        line["autotune"] = {"encode_best": tuning["encode"]["best"], "encode_best_ms": round(tuning["encode"]["best_ms"], 4),
+                            "encode_trials": tuning["encode"]["trials"],
+                            "decode_best": tuning["decode"]["best"], "decode_best_ms": round(tuning["decode"]["best_ms"], 4),
+                            "decode_trials": tuning["decode"]["trials"]}
+    if spec.plain:
+        line["plain_per_image"] = plain_per_image(fic, torch, stream, dimgs, plist, iters, enc, dec, pixels, value)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        v, done, dt = time_oracle(batch, args.cpu_s, threads)
+        v, done, dt = time_oracle(items, iters, args.cpu_s, threads)
         line["cpu_baseline"] = {"value": round(v, 3), "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
-                                "sample": f"{done} (image, threshold) pairs of the batch, encode + "
-                                          f"{DECODE_ITERS}-iteration decode, {dt:.1f} s on {threads} threads"}
+                                "sample": f"{done} images of the batch, encode + {iters}-iteration decode, "
+                                          f"{dt:.1f} s on {threads} threads"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
+    dist_finish(world)
+    return 0
+
+
+def plain_per_image(fic, torch, stream, dimgs, plist, iters, enc, dec, pixels, batched_value):
+    """The same encode + decode, one image at a time: (a) the plain API calls
+    fic_encode + fic_decode per image, (b) one prepared plan per image
+    launched in turn.  Outputs are checked equal to the batched launch."""
+    out = {}
+    with torch.cuda.stream(stream):
+        # (b) per-image plans
+        plans = []
+        for d, p in zip(dimgs, plist):
+            e = fic.EncodePlan([d], p, stream=stream)
+            e.run(stream)
+            plans.append((e, fic.DecodePlan(e.outs, stream=stream)))
+        stream.synchronize()
+        ms = []
+        for rep in range(4):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for e, dp in plans:
+                e.run(stream)
+                dp.run(iters, stream)
+            b.record(stream)
+            stream.synchronize()
+            if rep:
+                ms.append(a.elapsed_time(b))
+        v_plans = pixels / (statistics.mean(ms) * 1e-3) / 1e6
+        # (a) plain API calls
+        ms = []
+        for rep in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            outs = []
+            a.record(stream)
+            for d, p in zip(dimgs, plist):
+                st = fic.fic_encode(d, p, stream=stream)
+                outs.append((st, fic.fic_decode(st, iters, stream=stream)))
+            b.record(stream)
+            stream.synchronize()
+            if rep:
+                ms.append(a.elapsed_time(b))
+        v_api = pixels / (statistics.mean(ms) * 1e-3) / 1e6
+    # identical output: every stream and decoded image of a sample of images
+    same = True
+    for i in range(0, len(dimgs), max(1, len(dimgs) // 16)):
+        ga, gb = enc.outs[i].to_host(stream), outs[i][0].to_host(stream)
+        gc = plans[i][0].outs[0].to_host(stream)
+        same &= np.array_equal(ga["records"].view(np.uint8), gb["records"].view(np.uint8))
+        same &= np.array_equal(ga["records"].view(np.uint8), gc["records"].view(np.uint8))
+        same &= bool(torch.equal(dec.outs[i], outs[i][1])) and bool(torch.equal(dec.outs[i], plans[i][1].outs[0]))
+    return {"api_calls_mpix_s": round(v_api, 3), "per_image_plans_mpix_s": round(v_plans, 3),
+            "batched_over_api_calls": round(batched_value / v_api, 3),
+            "batched_over_per_image_plans": round(batched_value / v_plans, 3),
+            "identical_output": bool(same),
+            "note": "same images and parameters, one image per launch, no graphs; output compared on a sample "
+                    "of 1/16 of the images"}
+
+
+# --------------------------------------------------------------------------
+# GPU arm: exhaustive search (cfg3)
+
+def run_exhaustive(args):
+    import torch
+
+    world, rank, dev = dist_setup()
+    import paper_1501_02894_gb300 as fic
+
+    fic.lib()
+    imgs = synth.cfg3_images()
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peaks, peak_kind = load_peaks()
+    res = {}
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    sampler.start()
+    time.sleep(0.2)
+    outs = {}
+    for engine, ename in ((0, "tcgen05"), (1, "cuda_cores")):
+        plans, work = [], []
+        with torch.cuda.stream(stream):
+            for name, im in imgs:
+                p = fic.params("exhaustive", 8, 8, 8.0, dom_step=4, isometries=8, engine=engine)
+                d = torch.from_numpy(im).to(dev)
+                plan = fic.EncodePlan([d], p, stream=stream)
+                plan.run(stream)
+                plans.append((name, im, d, plan))
+            stream.synchronize()
+            for name, im, d, plan in plans:
+                H, W = im.shape
+                nr = (W // 8) * (H // 8)
+                nd = ((W - 16) // 4 + 1) * ((H - 16) // 4 + 1)
+                work.append((name, nr, nd, W * H))
+                _, f = plan.outs[0].info_host(stream)
+                assert f == nr * nd * 8
+            for _ in range(max(args.warmup, 3)):
+                flush.fill_(1)
+                for _, _, _, plan in plans:
+                    plan.run(stream)
+            stream.synchronize()
+            rows = {name: [] for name, *_ in plans}
+            steps = max(1, min(args.steps, 20))
+            for i in range(steps):
+                flush.fill_(i & 0xff)
+                for name, _, _, plan in plans:
+                    rows[name].append(plan.run_timed(stream))
+        outs[ename] = [plan.outs[0].to_host(stream) for *_, plan in plans]
+        per = {}
+        for (name, nr, nd, px) in work:
+            tab = kernel_table(rows[name])
+            total_ms = sum(v["ms_per_launch"] * v["launches_per_step"] for v in tab.values())
+            search = "exh_tc_kernel" if engine == 0 else "exh_cuda_kernel"
+            flops = 2.0 * nr * 8 * nd * 64
+            s_ms = tab[search]["ms_per_launch"]
+            per[name] = {"ranges": nr, "domains": nd, "fits": nr * nd * 8, "ms": round(total_ms, 4),
+                         "fits_per_s": round(nr * nd * 8 / (total_ms * 1e-3), 1),
+                         "mpix_s": round(px / (total_ms * 1e-3) / 1e6, 3),
+                         "search_kernel": search, "search_ms": s_ms,
+                         "search_tflops": round(flops / (s_ms * 1e-3) / 1e12, 2), "kernels": tab}
+        res[ename] = per
+    clocks = sampler.stop()
+    same = all(np.array_equal(a["records"].view(np.uint8), b["records"].view(np.uint8))
+               for a, b in zip(outs["tcgen05"], outs["cuda_cores"]))
+    tot_fits = sum(v["fits"] for v in res["tcgen05"].values())
+    tot_ms = sum(v["ms"] for v in res["tcgen05"].values())
+    value = world * tot_fits / (tot_ms * 1e-3)
+    big = res["tcgen05"]["scene9_1024"]
+    peak = float(peaks["bf16_tflops"])
+    roofline = {"bound": "tensor", "kernel": "exh_tc_kernel (1024x1024)", "achieved": big["search_tflops"],
+                "peak": peak, "unit": "TFLOP/s", "frac": round(big["search_tflops"] / peak, 4),
+                "peak_kind": f"{peak_kind} bf16 burst x 1 (fp16 operands, same nominal rate)",
+                "traffic": None,
+                "flops_per_launch": 2.0 * big["ranges"] * 8 * big["domains"] * 64,
+                "note": "algorithmic FLOPs = 2 x (ranges x 8 isometries) x domains x 64 decimated values"}
+    line = {
+        "metric": "exhaustive-search range-domain fits/s (bit-exact)", "value": round(value, 1), "unit": "fits/s",
+        "n_gpus": world, "steps": max(1, min(args.steps, 20)), "warmup": max(args.warmup, 3),
+        "ms_per_step": round(tot_ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16 operands, f32 accumulate (exact integers), int64 decisions", "data": "synthetic",
+        "config": {"workload": "cfg3: 512x512 seed 1 + 1024x1024 seed 9, 8x8 ranges, domain step 4, 8 isometries",
+                   "l2": "flushed (256 MiB write) before every step", "parallelism": f"replicas x{world}"},
+        "engines": res, "engines_identical_output": bool(same),
+        "cuda_core_over_tensor_time": round(sum(v["ms"] for v in res["cuda_cores"].values()) / tot_ms, 3),
+        "roofline": roofline, "gpu_launches": 4 * len(imgs) * max(1, min(args.steps, 20)), "clocks": clocks,
+        "e2e": None,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        v, done, dt = time_oracle_exhaustive(imgs[1][1], args.cpu_s, threads)
+        line["cpu_baseline"] = {"value": round(v, 1), "unit": "fits/s", "cores": threads, "kind": "oracle",
+                                "sample": f"{done} random 8x8 ranges of the 1024x1024 image, full search, "
+                                          f"{dt:.1f} s on {threads} threads"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist_finish(world)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm: serving (cfg5)
+
+def run_serving(args):
+    t_setup = time.perf_counter()
+    t_arr, is_enc, side, seeds = synth.cfg5_requests(rate=args.rate, seconds=args.serve_s)
+    nreq = len(t_arr)
+    # image pool: one image per distinct side, from the seed of the first
+    # request of that side (generating every request's own image is
+    # hours of host work at this rate)
+    sides = sorted(set(int(s) for s in side))
+    first = {}
+    for i, s in enumerate(side):
+        first.setdefault(int(s), i)
+    pool_imgs = gen_images([("g", s, int(seeds[first[s]])) for s in sides])
+    pool = dict(zip(sides, pool_imgs))
+
+    import torch
+
+    world, rank, dev = dist_setup()
+    import paper_1501_02894_gb300 as fic
+
+    fic.lib()
+    P = fic.params("mns", 32, 4, 8.0)
+    iters = 8
+    # decode inputs: the stream of each pool image, encoded once at setup
+    streams, offsets = {}, {}
+    for s, im in pool.items():
+        st = fic.fic_encode(torch.from_numpy(im).to(dev), P)
+        h = st.to_host()
+        streams[s] = h["records"].copy()
+        offsets[s] = h["tile_offsets"].astype(np.int32)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+
+    class Buffers:
+        def __init__(self):
+            self.free = {}
+
+        def get(self, key, make):
+            lst = self.free.setdefault(key, [])
+            return lst.pop() if lst else make()
+
+        def put(self, key, buf):
+            self.free[key].append(buf)
+
+    def serve_with_server():
+        srv = fic.Server(hbm_budget_bytes=int(args.hbm_budget_gb * (1 << 30)), streams=4, max_batch=64,
+                         queue_capacity=1 << 20, host_staging_bytes=4 << 30)
+        bufs = Buffers()
+        live = {}  # ticket -> (i, key, bufs, submit lag)
+        lat = np.zeros(nreq)
+        px_done = 0
+        order = []
+        t0 = time.perf_counter() + 0.05
+
+        def reap(block=False):
+            nonlocal px_done
+            while order:
+                tk = order[0]
+                r = srv.wait(tk, -1) if block else srv.poll(tk)
+                if r is None:
+                    return
+                order.pop(0)
+                i, key, b, lag = live.pop(tk)
+                lat[i] = lag + r["latency_ms"]
+                px_done += int(side[i]) ** 2
+                for k2, v in zip(key, b):
+                    bufs.put(k2, v)
+
+        for i in range(nreq):
+            s = int(side[i])
+            now = time.perf_counter() - t0
+            if now < t_arr[i]:
+                reap()
+                while time.perf_counter() - t0 < t_arr[i]:
+                    pass
+            lag = max(0.0, (time.perf_counter() - t0) - t_arr[i]) * 1e3
+            if is_enc[i]:
+                cap, ntop = (s // 4) ** 2, (s // 32) ** 2
+                rb = bufs.get(("r", s), lambda: np.zeros(cap, dtype=fic.RECORD_DTYPE))
+                sb = bufs.get(("s", s), lambda: np.zeros(ntop, dtype=np.uint32))
+                tk = srv.submit_encode(pool[s], P, out_records=rb, out_split=sb)
+                live[tk] = (i, (("r", s), ("s", s)), (rb, sb), lag)
+            else:
+                ob = bufs.get(("o", s), lambda: np.zeros((s, s), dtype=np.uint8))
+                tk = srv.submit_decode(streams[s], s, s, P, iters, out=ob)
+                live[tk] = (i, (("o", s),), (ob,), lag)
+            order.append(tk)
+        reap(block=True)
+        t_end = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return lat, px_done, t_end, st
+
+    def serve_plain():
+        """One request at a time in arrival order: copy in, fic_encode or
+        fic_decode, copy out, synchronise."""
+        lat = np.zeros(nreq)
+        px_done = 0
+        stream = torch.cuda.current_stream()
+        pinned = {s: torch.from_numpy(im).pin_memory() for s, im in pool.items()}
+        t0 = time.perf_counter() + 0.05
+        deadline = args.serve_s * 2 + 30
+        served = 0
+        for i in range(nreq):
+            s = int(side[i])
+            while time.perf_counter() - t0 < t_arr[i]:
+                pass
+            if is_enc[i]:
+                d = pinned[s].to(dev, non_blocking=True)
+                stv = fic.fic_encode(d, P)
+                stv.to_host()
+            else:
+                rec = torch.from_numpy(streams[s].view(np.uint8)).to(dev)
+                stv = fic.Stream(s, s, P, dev)
+                stv.records[: rec.numel()].copy_(rec)
+                stv.tile_offsets.copy_(torch.from_numpy(offsets[s]))
+                fic.fic_decode(stv, iters).cpu()
+            stream.synchronize()
+            lat[i] = (time.perf_counter() - t0 - t_arr[i]) * 1e3
+            px_done += s * s
+            served += 1
+            if time.perf_counter() - t0 > deadline:
+                break
+        t_end = time.perf_counter() - t0
+        return lat[:served], px_done, t_end, served
+
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    sampler.start()
+    lat_s, px_s, t_s, stats = serve_with_server()
+    clocks = sampler.stop()
+    lat_p, px_p, t_p, served_p = serve_plain()
+
+    def pct(a, q):
+        return round(float(np.percentile(a, q)), 3) if len(a) else None
+
+    offered = float(np.sum(side.astype(np.float64) ** 2)) / args.serve_s / 1e6
+    value = px_s / t_s / 1e6
+    line = {
+        "metric": "served MNS encode/decode Mpixel/s with p50/p99 latency (bit-exact)", "value": round(value, 3),
+        "unit": "Mpixel/s", "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": round(t_s * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"cfg5: Poisson {args.rate:.0f} req/s for {args.serve_s:.0f} s, 80% encode / 20% "
+                               f"decode (8 it), sides log-uniform [128,4096] step 32, MNS 32->4 RMS 8; one pool image "
+                               f"per side", "requests": nreq, "distinct_sides": len(sides),
+                   "hbm_budget_gb": args.hbm_budget_gb, "server": "4 streams, batches of <= 64 jobs"},
+        "offered_mpix_s": round(offered, 3),
+        "latency_ms": {"p50": pct(lat_s, 50), "p99": pct(lat_s, 99), "mean": round(float(np.mean(lat_s)), 3),
+                       "max": round(float(np.max(lat_s)), 3), "from": "arrival to result in the caller's buffer"},
+        "server_stats": stats,
+        "plain_per_request": {"mpix_s": round(px_p / t_p / 1e6, 3), "served": int(served_p),
+                              "latency_ms": {"p50": pct(lat_p, 50), "p99": pct(lat_p, 99),
+                                             "mean": round(float(np.mean(lat_p)), 3) if len(lat_p) else None},
+                              "how": "one request at a time in arrival order: H2D, fic_encode / fic_decode, D2H, "
+                                     "synchronise"},
+        "setup_s": round(setup_s, 1), "clocks": clocks, "roofline": None, "gpu_launches": None,
+        "e2e": {"value": round(value, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "note": "the served rate is end to end: host buffers in and out"},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist_finish(world)
     return 0
 
 
@@ -395,14 +848,22 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"])
     ap.add_argument("--cpu-s", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=10.0, help="oracle seconds per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--heat-s", type=float, default=2.0, help="busy seconds before the timed steps (clock sampling)")
+    ap.add_argument("--rate", type=float, default=2000.0, help="cfg5: arrivals per second")
+    ap.add_argument("--serve-s", type=float, default=60.0, help="cfg5: seconds of arrivals")
+    ap.add_argument("--hbm-budget-gb", type=float, default=40.0, help="cfg5: server device memory")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    return run_ours(args)
+    if args.workload == "cfg3":
+        return run_exhaustive(args)
+    if args.workload == "cfg5":
+        return run_serving(args)
+    return run_batched(args, make_spec(args.workload))
 
 
 if __name__ == "__main__":

@@ -435,12 +435,19 @@ class Server:
         _check(lib().fic_server_create(ctypes.byref(cfg), ctypes.byref(self.handle)), "fic_server_create")
         self._live = {}
 
-    def submit_encode(self, image: np.ndarray, p: Params) -> int:
+    def submit_encode(self, image: np.ndarray, p: Params, out_records=None, out_split=None) -> int:
+        """Queue an encode; out_records / out_split (optional, reused by the
+        caller) must hold (W/bmin)*(H/bmin) records and (W/bmax)*(H/bmax) words."""
         image = np.ascontiguousarray(image, dtype=np.uint8)
         H, W = image.shape
         cap = (W // p.bmin) * (H // p.bmin)
-        out_rec = np.zeros(max(cap, 1), dtype=RECORD_DTYPE)
-        out_split = np.zeros(max((W // p.bmax) * (H // p.bmax), 1), dtype=np.uint32)
+        ntop = (W // p.bmax) * (H // p.bmax)
+        out_rec = out_records if out_records is not None else np.zeros(max(cap, 1), dtype=RECORD_DTYPE)
+        out_split = out_split if out_split is not None else np.zeros(max(ntop, 1), dtype=np.uint32)
+        if out_rec.dtype != RECORD_DTYPE or out_rec.size < cap or not out_rec.flags.c_contiguous:
+            raise ValueError("out_records too small or not a contiguous record array")
+        if out_split.dtype != np.uint32 or out_split.size < ntop or not out_split.flags.c_contiguous:
+            raise ValueError("out_split too small or not contiguous uint32")
         j = JobC()
         j.kind, j.width, j.height, j.params = JOB_ENCODE, W, H, p
         j.image = image.ctypes.data
@@ -451,9 +458,11 @@ class Server:
         self._live[t.value] = ("encode", image, out_rec, out_split)
         return t.value
 
-    def submit_decode(self, records: np.ndarray, W: int, H: int, p: Params, iters: int) -> int:
+    def submit_decode(self, records: np.ndarray, W: int, H: int, p: Params, iters: int, out=None) -> int:
         records = np.ascontiguousarray(records, dtype=RECORD_DTYPE)
-        out = np.zeros((H, W), dtype=np.uint8)
+        out = out if out is not None else np.zeros((H, W), dtype=np.uint8)
+        if out.dtype != np.uint8 or out.shape != (H, W) or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous (H, W) uint8 array")
         j = JobC()
         j.kind, j.width, j.height, j.params, j.iters = JOB_DECODE, W, H, p, int(iters)
         j.nrecords = len(records)
@@ -467,7 +476,8 @@ class Server:
     def _output(self, ticket, res):
         ent = self._live.pop(ticket)
         if ent[0] == "encode":
-            return {"records": ent[2][: res.nrecords].copy(), "split": ent[3].copy(), "fits": int(res.fits),
+            # views of the output buffers (the caller's own, when it passed them)
+            return {"records": ent[2][: res.nrecords], "split": ent[3], "fits": int(res.fits),
                     "latency_ms": res.latency_ms, "queue_ms": res.queue_ms}
         return {"image": ent[2], "latency_ms": res.latency_ms, "queue_ms": res.queue_ms}
 
