@@ -224,6 +224,7 @@ def dist_setup():
 
 
 def max_over_ranks(world, dev, v):
+    """The slowest rank's value (replicas: the job ends with the last rank)."""
     if world == 1:
         return v
     import torch
@@ -232,6 +233,13 @@ def max_over_ranks(world, dev, v):
     t = torch.tensor([v], device=dev, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(world, dev, ms_per_step_local, units_per_rank_step):
+    """Whole-job throughput of `world` replicas: every rank processes the same
+    units per step; the job's step time is the slowest rank's."""
+    ms = max_over_ranks(world, dev, ms_per_step_local)
+    return ms, world * units_per_rank_step / (ms * 1e-3)
 
 
 def dist_finish(world):
@@ -429,8 +437,8 @@ def run_batched(args, spec: Spec):
     clocks = sampler.stop()
     enc_ms = [a.elapsed_time(b) for a, b, _ in ev]
     dec_ms = [b.elapsed_time(c) for _, b, c in ev]
-    ms_per_step = max_over_ranks(world, dev, sum(e + d for e, d in zip(enc_ms, dec_ms)) / args.steps)
-    value = world * pixels / (ms_per_step * 1e-3) / 1e6
+    ms_per_step, px_s = replica_throughput(world, dev, sum(e + d for e, d in zip(enc_ms, dec_ms)) / args.steps, pixels)
+    value = px_s / 1e6
     chk = enc.outs[0].to_host(stream)
     assert np.array_equal(chk["records"].view(np.uint8), ref0["records"].view(np.uint8)), "graph replay changed output"
 
@@ -466,8 +474,9 @@ def run_batched(args, spec: Spec):
             s1.record(stream)
             e2e_ev.append((s0, s1))
     stream.synchronize()
-    e2e_ms = max_over_ranks(world, dev, statistics.mean(a.elapsed_time(b) for a, b in e2e_ev[warm:]))
-    e2e_value = world * pixels / (e2e_ms * 1e-3) / 1e6
+    e2e_ms, e2e_px_s = replica_throughput(world, dev, statistics.mean(a.elapsed_time(b) for a, b in e2e_ev[warm:]),
+                                          pixels)
+    e2e_value = e2e_px_s / 1e6
 
     # ---- roofline of the dominant kernel (HBM bound): algorithmic bytes per launch
     peaks, peak_kind = load_peaks()

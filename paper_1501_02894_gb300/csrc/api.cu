@@ -157,7 +157,7 @@ struct fic_plan {
 // Exhaustive search: per image, decimated domains (packed and fp16), domain
 // and range statistics, permuted range rows and per-row results.
 struct ExhLayout {
-    size_t dpairs, dfp16, dstat, afp16, rstat, row_g, row_dk, total;
+    size_t dpairs, dfp16, dstat, dscr, afp16, rstat, row_g, row_dk, total;
 };
 
 static ExhLayout exh_layout(int W, int H, const fic_params *p, int *nd_out, int *nd_pad_out, int *ndx_out,
@@ -169,7 +169,8 @@ static ExhLayout exh_layout(int W, int H, const fic_params *p, int *nd_out, int 
     L.dpairs = 0;
     L.dfp16 = L.dpairs + align_up((size_t)nd * 128);
     L.dstat = L.dfp16 + align_up((size_t)nd_pad * 128);
-    L.afp16 = L.dstat + align_up((size_t)nd_pad * 16);
+    L.dscr = L.dstat + align_up((size_t)nd_pad * 16);
+    L.afp16 = L.dscr + align_up((size_t)nd_pad * 8);
     L.rstat = L.afp16 + align_up(nr * 8 * 128);
     L.row_g = L.rstat + align_up(nr * 16);
     L.row_dk = L.row_g + align_up(nr * 8 * 8);
@@ -231,6 +232,7 @@ static int exh_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
         E.dpairs = reinterpret_cast<uint32_t *>(w + off + L.dpairs);
         E.dfp16 = reinterpret_cast<__half *>(w + off + L.dfp16);
         E.dstat = reinterpret_cast<int4 *>(w + off + L.dstat);
+        E.dscr = reinterpret_cast<float2 *>(w + off + L.dscr);
         E.afp16 = reinterpret_cast<__half *>(w + off + L.afp16);
         E.rstat = reinterpret_cast<int4 *>(w + off + L.rstat);
         E.row_g = reinterpret_cast<long long *>(w + off + L.row_g);

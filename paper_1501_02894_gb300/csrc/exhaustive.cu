@@ -24,6 +24,7 @@ __global__ void exh_prep_domains(ExhDesc E) {
         if (d >= E.nd) {
             for (int i = 0; i < kExhK; ++i) E.dfp16[(size_t)d * kExhK + i] = __ushort_as_half(0);
             E.dstat[d] = make_int4(0, 0, 0, 0);
+            E.dscr[d] = make_float2(0.f, __int_as_float(0x7fc00000));  // NaN: never passes the screen
             continue;
         }
         const int dy = (d / E.ndx) * E.step, dx = (d % E.ndx) * E.step;
@@ -44,6 +45,7 @@ __global__ void exh_prep_domains(ExhDesc E) {
         const long long ncdd = 64LL * sdd - (long long)sd * sd;  // <= 4.3e9: fits an unsigned word
         const float k512 = ncdd > 0 ? 512.f / (float)ncdd : 0.f;
         E.dstat[d] = make_int4(sd, (int)(uint32_t)ncdd, __float_as_int(k512), 1);
+        E.dscr[d] = make_float2(-(float)sd, ncdd > 0 ? 262144.f / (float)ncdd : 0.f);
     }
 }
 
@@ -71,33 +73,29 @@ __global__ void exh_prep_ranges(ExhDesc E) {
 // Row state of the screening epilogue.
 struct ExhRow {
     long long g;  // best exact s-part error
-    float gf;     // the same as float, plus its rounding margin
+    float thr;    // screening threshold of g (exh_threshold)
     int d, k;
 };
 
 __device__ __forceinline__ void exh_row_init(ExhRow &b) {
     b.g = 0x7fffffffffffffffLL;
-    b.gf = __int_as_float(0x7f800000);  // +inf
+    b.thr = __int_as_float(0xff800000);  // -inf: everything passes
     b.d = -1;
     b.k = 0;
 }
 
-// Offer candidate domain d with sum r*d4 = sdr to the row (domains are
-// offered in increasing order, so a strict improvement test keeps the
-// smallest domain index among equal errors).
-__device__ __forceinline__ void exh_offer(ExhRow &b, int d, int sdr, int sr, int4 ds, int s_bits) {
-    const int sd = ds.x;
+// Exact evaluation of candidate domain d (sum r*d4 = sdr) for the row.
+// Domains are offered in increasing order, so a strict improvement test
+// keeps the smallest domain index among equal errors.
+__device__ __forceinline__ void exh_exact(ExhRow &b, int d, int sdr, int sr, int4 ds, int s_bits) {
+    const int ncdr = 64 * sdr - ds.x * sr;
     const uint32_t ncdd = (uint32_t)ds.y;
-    const int ncdr = 64 * sdr - sd * sr;
-    const float lb = exh_lower_bound((float)ncdr, (float)ncdd, __int_as_float(ds.z), s_bits);
-    if (lb > b.gf) return;
     const int k = best_contrast((long long)ncdr, (long long)ncdd, s_bits);
     const long long c = contrast_code(k, s_bits);
     const long long g = c * c * (long long)ncdd - 1024LL * c * ncdr;
     if (g < b.g) {
         b.g = g;
-        const float gf = (float)g;
-        b.gf = gf + fabsf(gf) * 1e-6f + 1.f;
+        b.thr = exh_threshold(g);
         b.d = d;
         b.k = k;
     }
@@ -111,6 +109,7 @@ constexpr int kExhStage = 64;
 __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
     __shared__ __align__(16) uint32_t s_dp[kExhStage][32];
     __shared__ int4 s_ds[kExhStage];
+    __shared__ float2 s_cs[kExhStage];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = (blockIdx.x * kExhWarps + warp) * 4 + (lane >> 3);
     const int t = lane & 7;
@@ -146,8 +145,10 @@ __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
             const int j = i >> 5, w = i & 31;
             s_dp[j][w] = (d0 + j < E.nd) ? E.dpairs[(size_t)(d0 + j) * 32 + w] : 0u;
         }
-        for (int j = threadIdx.x; j < kExhStage; j += blockDim.x)
+        for (int j = threadIdx.x; j < kExhStage; j += blockDim.x) {
             s_ds[j] = (d0 + j < E.nd) ? E.dstat[d0 + j] : make_int4(0, 0, 0, 0);
+            s_cs[j] = (d0 + j < E.nd) ? E.dscr[d0 + j] : make_float2(0.f, 0.f);
+        }
         __syncthreads();
         const int nj = min(kExhStage, E.nd - d0);
         for (int j = 0; j < nj; ++j) {
@@ -161,7 +162,8 @@ __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
                 acc = dp2a_lo(p.z, aw[2 * i + 1], acc);
                 acc = dp2a_hi(p.w, aw[2 * i + 1], acc);
             }
-            if (live) exh_offer(best, d0 + j, (int)acc, sr, s_ds[j], E.s_bits);
+            if (live && exh_screen((float)acc, (float)sr, s_cs[j]) >= best.thr)
+                exh_exact(best, d0 + j, (int)acc, sr, s_ds[j], E.s_bits);
         }
     }
     if (live) {

@@ -24,6 +24,7 @@ struct ExhDesc {
     uint32_t *dpairs;         // [nd][32]   packed (d4, d4) pairs for dp2a
     __half *dfp16;            // [nd_pad][64] decimated domains, K-major, fp16
     int4 *dstat;              // [nd_pad]   Sd, nCdd (u32), 512/nCdd (float bits), valid
+    float2 *dscr;             // [nd_pad]   screening constants: -Sd, 512^2/nCdd (NaN: padding)
     __half *afp16;            // [nr * 8][64] range rows permuted per isometry, fp16
     int4 *rstat;              // [nr]       Sr, Srr
     long long *row_g;         // [nr * 8]   best s-part error of the (range, isometry) row
@@ -52,34 +53,21 @@ __host__ __device__ inline void exh_iso_src(int t, int B, int u, int v, int &su,
     }
 }
 
-// Screening of one candidate against the row's best so far.  g* (the
-// minimum over the contrast grid of c^2 nCdd - 1024 c nCdr) is at least
-// nCdd (dmin^2 - c*^2) with c* = 512 nCdr / nCdd the unconstrained optimum
-// and dmin the distance from c* to the nearest grid code.  The bound is
-// evaluated in float with a margin; a candidate is evaluated exactly (int64)
-// only when the bound does not exclude it.
-struct ExhCand {
-    float cs;    // c* (clamped to the grid's range)
-    float lb;    // lower bound of g*, minus the float margin
-};
-
-__device__ __forceinline__ float exh_lower_bound(float ncdr_f, float ncdd_f, float k512_over_ncdd, int s_bits) {
-    // c* = 512 nCdr / nCdd ; g_cont = -c*^2 nCdd
-    const int K = 1 << s_bits;
-    const float step = (float)(256 >> s_bits);
-    const float cmax = (float)((K - 1) * (128 >> s_bits));  // = 128 - step/2
-    float cs = ncdr_f * k512_over_ncdd;
-    const float csc = fminf(fmaxf(cs, -cmax), cmax);
-    // nearest grid point to csc: c_k = step*k - 128 + step/2
-    const float t = (csc + 128.f - 0.5f * step) / step;
-    const float cnear = fmaf(rintf(t), step, 0.5f * step - 128.f);
-    // a float slip near a grid midpoint may pick the second-nearest code:
-    // shrink the distance by more than the possible error
-    const float d = fmaxf(fabsf(cs - cnear) - 1e-3f, 0.f);
-    // g(c) = nCdd (c - c*)^2 - nCdd c*^2
-    const float g = ncdd_f * (d * d - cs * cs);
-    const float mag = ncdd_f * (d * d + cs * cs);
-    return g - (1e-5f * mag + 64.f);
+// Screening of one candidate against the row's best so far.  Over real c,
+// c^2 nCdd - 1024 c nCdr is smallest at c* = 512 nCdr / nCdd, where it is
+// -L with L = 512^2 nCdr^2 / nCdd; the grid's best code can only do worse,
+// so a candidate with -L >= the row's best exact error g cannot win (ties
+// keep the earlier domain).  The screen computes an upper bound of L in
+// float: nCdr = 64 Sdr - Sd Sr is formed with at most 64 of absolute
+// rounding error (|nCdr| < 2^31, Sdr exact below 2^24), widened by 130, and
+// the product's relative error (< 1e-6) is covered by the row threshold
+// thr(g) = -g (1 - 1e-5) - 1: a candidate is evaluated exactly (int64) only
+// when its bound reaches thr.  Padding domains carry NaN and never pass.
+__device__ __forceinline__ float exh_screen(float sdr_f, float sr_f, float2 cs) {
+    const float u = fabsf(fmaf(sdr_f, 64.f, cs.x * sr_f)) + 130.f;
+    return u * u * cs.y;
 }
+
+__device__ __forceinline__ float exh_threshold(long long g) { return (float)(-g) * (1.f - 1e-5f) - 1.f; }
 
 }  // namespace fic

@@ -95,26 +95,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // Row state of the screening epilogue (as in exhaustive.cu).
 struct TcRow {
     long long g;
-    float gf;
+    float thr;
     int d, k;
 };
 
-__device__ __forceinline__ void tc_offer(TcRow &b, int d, int sdr, int sr, int4 ds, int s_bits) {
-    const int sd = ds.x;
+// The exact evaluation is rare (after a few tiles most candidates fail the
+// screen), so it is kept out of line: 32 inlined copies per column batch
+// would only crowd the instruction cache.
+__device__ __noinline__ TcRow tc_exact(TcRow b, int d, float acc, int sr, int4 ds, int s_bits) {
+    const int ncdr = 64 * __float2int_rn(acc) - ds.x * sr;
     const uint32_t ncdd = (uint32_t)ds.y;
-    const int ncdr = 64 * sdr - sd * sr;
-    const float lb = exh_lower_bound((float)ncdr, (float)ncdd, __int_as_float(ds.z), s_bits);
-    if (lb > b.gf) return;
     const int k = best_contrast((long long)ncdr, (long long)ncdd, s_bits);
     const long long c = contrast_code(k, s_bits);
     const long long g = c * c * (long long)ncdd - 1024LL * c * ncdr;
     if (g < b.g) {
         b.g = g;
-        const float gf = (float)g;
-        b.gf = gf + fabsf(gf) * 1e-6f + 1.f;
+        b.thr = exh_threshold(g);
         b.d = d;
         b.k = k;
     }
+    return b;
 }
 
 __global__ void __launch_bounds__(kTcThreads, 2)
@@ -224,9 +224,10 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         const int r = row >> 3, t = row & 7;
         const bool live = r < E.nr && t < E.isos;
         const int sr = live ? E.rstat[r].x : 0;
+        const float srf = (float)sr;
         TcRow best;
         best.g = 0x7fffffffffffffffLL;
-        best.gf = __int_as_float(0x7f800000);
+        best.thr = live ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);  // dead rows never pass
         best.d = -1;
         best.k = 0;
         for (int n = 0; n < ntiles; ++n) {
@@ -241,13 +242,15 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 const int col = h * (kTcCols / 2) + c0;
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kTcCols + col), v);
-                if (live) {
-                    const int dbase = n * kTcCols + col;
+                const int dbase = n * kTcCols + col;
+                const float4 *cs4 = reinterpret_cast<const float4 *>(E.dscr + dbase);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int d = dbase + j;
-                        if (d < E.nd) tc_offer(best, d, __float2int_rn(v[j]), sr, __ldg(E.dstat + d), E.s_bits);
-                    }
+                for (int j = 0; j < 32; j += 2) {
+                    const float4 c2 = __ldg(cs4 + j / 2);
+                    if (exh_screen(v[j], srf, make_float2(c2.x, c2.y)) >= best.thr)
+                        best = tc_exact(best, dbase + j, v[j], sr, __ldg(E.dstat + dbase + j), E.s_bits);
+                    if (exh_screen(v[j + 1], srf, make_float2(c2.z, c2.w)) >= best.thr)
+                        best = tc_exact(best, dbase + j + 1, v[j + 1], sr, __ldg(E.dstat + dbase + j + 1), E.s_bits);
                 }
             }
             tc_fence_before();
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         asm volatile("bar.sync 1, %0;" ::"r"(kTcEpiWarps * 32));
         if (h == 0 && live) {
             const TcRow o = s_half[rloc];
-            if (o.g < best.g) best = o;
+            if (o.g < best.g || (o.g == best.g && (unsigned)o.d < (unsigned)best.d)) best = o;
             E.row_g[(size_t)r * 8 + t] = best.g;
             E.row_dk[(size_t)r * 8 + t] = make_int2(best.d, best.k);
         }
