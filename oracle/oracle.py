@@ -212,6 +212,11 @@ def phase2_contrast(level: int, bit: int) -> int:
     return int(lib().orc_phase2_contrast(level, bit))
 
 
+def phase2_mbits(level: int) -> int:
+    """Bits of a phase-2 mean difference at `level`, sign included (Section 3.3)."""
+    return int(lib().orc_phase2_mbits(level))
+
+
 def centred(x: int, B: int, W: int) -> int:
     return int(lib().orc_centred(x, B, W))
 
