@@ -31,7 +31,7 @@ void stage_mark(cudaStream_t st, const char *label) {
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against the driver library).
-int make_tma_map(TmaMap *out, const void *base, int W, int H, int boxw, int boxh) {
+int make_tma_map(TmaMap *out, const void *base, int W, int H, int boxw, int boxh, int elem_bytes) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -44,10 +44,11 @@ int make_tma_map(TmaMap *out, const void *base, int W, int H, int boxw, int boxh
     }
     CUtensorMap m;
     const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
-    const cuuint64_t strides[1] = {(cuuint64_t)W};
+    const cuuint64_t strides[1] = {(cuuint64_t)W * (cuuint64_t)elem_bytes};
     const cuuint32_t box[2] = {(cuuint32_t)boxw, (cuuint32_t)boxh};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, estr,
+    const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    CUresult r = encode(&m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return FIC_ECUDA;
@@ -67,7 +68,8 @@ cudaError_t launch_mns_encode_slots(int bmax, const EncDesc *d_descs, int count,
 cudaError_t launch_local_encode(int bmax, const EncDesc *d_descs, int count, int total_strips, int total_chunks,
                                 uint32_t *pack_status, cudaStream_t st);
 cudaError_t launch_decode(int bmax, const DecDesc *d_descs, int count, int total_strips, void *tables, int iters,
-                          const DecTune &tune, cudaStream_t st);
+                          bool d4, const DecTune &tune, cudaStream_t st);
+int decode_d4_box(int bmax);
 size_t decode_table_bytes_per_strip();
 int mns_strip_width(int bmax);
 }  // namespace fic
@@ -152,6 +154,7 @@ struct fic_plan {
     std::vector<size_t> out_bytes;
     EncTune etune;  // launch mapping (fic_plan_set_tuning / fic_plan_autotune)
     DecTune dtune;
+    bool d4 = false;  // decode: iterate on 2x2-sum images (every stream centred)
 };
 
 // Exhaustive search: per image, decimated domains (packed and fp16), domain
@@ -331,7 +334,9 @@ size_t encode_plan_staging_bytes(int count) {
     return align_up(sizeof(TmaMap) * (size_t)count) + align_up(sizeof(EncDesc) * (size_t)count);
 }
 
-size_t decode_plan_staging_bytes(int count) { return align_up(sizeof(DecDesc) * (size_t)count); }
+size_t decode_plan_staging_bytes(int count) {
+    return align_up(sizeof(DecDesc) * (size_t)count) + align_up(2 * sizeof(TmaMap) * (size_t)count);
+}
 
 // `staging`, when given, is pinned host memory of encode_plan_staging_bytes
 // that must stay untouched until the plan's work on `stream` has run: the
@@ -613,7 +618,11 @@ int fic_encode(const uint8_t *d_img, int width, int height, const fic_params *p,
 
 // Decoder workspace layout (each part 256-byte aligned): image descriptors,
 // one scratch iterate per image, per-strip transform tables.
-static size_t dec_head_bytes(int count) { return align_up(sizeof(DecDesc) * (size_t)count); }
+// Decoder workspace head: descriptors, then two tensor maps per image (the
+// 2x2-sum ping-pong images of centred streams).
+static size_t dec_head_bytes(int count) {
+    return align_up(sizeof(DecDesc) * (size_t)count) + align_up(2 * sizeof(TmaMap) * (size_t)count);
+}
 
 size_t fic_decode_workspace_bytes(int count, const int *widths, const int *heights) {
     if (count <= 0 || !widths || !heights) return 0;
@@ -655,6 +664,14 @@ int decode_plan_create_staged(const fic_stream *sts, int count, uint8_t *const *
     pl->hdec.resize((size_t)count);
     uint8_t *w = static_cast<uint8_t *>(d_workspace);
     uint8_t *scratch = w + dec_head_bytes(count);
+    TmaMap *d_maps = reinterpret_cast<TmaMap *>(w + align_up(sizeof(DecDesc) * (size_t)count));
+    std::vector<TmaMap> maps(2 * (size_t)count);
+    // 2x2-sum iteration when every stream uses centred domains and is wide
+    // enough for the window box
+    bool d4 = true;
+    for (int i = 0; i < count; ++i)
+        d4 = d4 && (sts[i].params.mode == FIC_NOSEARCH || sts[i].params.mode == FIC_MNS) &&
+             sts[i].width / 2 >= decode_d4_box(bmax);
     int strips = 0;
     for (int i = 0; i < count; ++i) {
         const fic_stream *s = &sts[i];
@@ -673,6 +690,21 @@ int decode_plan_create_staged(const fic_stream *sts, int count, uint8_t *const *
         d.tile_off = s->tile_offsets;
         d.buf[0] = d_outs[i];
         d.buf[1] = scratch;
+        if (d4) {
+            const size_t half = (size_t)s->width * (size_t)s->height / 2;  // one (W/2) x (H/2) uint16 image
+            d.d4[0] = reinterpret_cast<uint16_t *>(scratch);
+            d.d4[1] = reinterpret_cast<uint16_t *>(scratch + half);
+            for (int k = 0; k < 2; ++k) {
+                rc = make_tma_map(&maps[2 * (size_t)i + k], d.d4[k], s->width / 2, s->height / 2, decode_d4_box(bmax),
+                                  bmax, 2);
+                if (rc) {
+                    delete pl;
+                    return rc;
+                }
+                d.map[k] = d_maps + 2 * i + k;
+            }
+            d.info = s->info;
+        }
         scratch += align_up((size_t)s->width * (size_t)s->height);
         d.W = s->width;
         d.H = s->height;
@@ -693,19 +725,25 @@ int decode_plan_create_staged(const fic_stream *sts, int count, uint8_t *const *
     pl->kind = 1;
     pl->count = count;
     pl->bmax = bmax;
+    pl->d4 = d4;
     pl->total_strips = strips;
     pl->dec_tables = scratch;  // after the per-image iterate buffers
     pl->ws = d_workspace;
     pl->ws_bytes = ws_bytes;
     pl->d_dec = reinterpret_cast<DecDesc *>(w);
     pl->d_enc = nullptr;
-    const void *src = pl->hdec.data();
+    const void *src = pl->hdec.data(), *src_maps = maps.data();
     if (staging) {
         memcpy(staging, pl->hdec.data(), sizeof(DecDesc) * (size_t)count);
+        memcpy(staging + align_up(sizeof(DecDesc) * (size_t)count), maps.data(), 2 * sizeof(TmaMap) * (size_t)count);
         src = staging;
+        src_maps = staging + align_up(sizeof(DecDesc) * (size_t)count);
     }
     cudaError_t e = cudaMemcpyAsync(pl->d_dec, src, sizeof(DecDesc) * (size_t)count, cudaMemcpyHostToDevice,
                                     static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess && d4)
+        e = cudaMemcpyAsync(d_maps, src_maps, 2 * sizeof(TmaMap) * (size_t)count, cudaMemcpyHostToDevice,
+                            static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         delete pl;
         return FIC_ECUDA;
@@ -733,8 +771,8 @@ int fic_decode_plan_run(const fic_plan *pl, int iters, void *stream) {
         }
         return FIC_OK;
     }
-    return cuda_rc(launch_decode(pl->bmax, pl->d_dec, pl->count, pl->total_strips, pl->dec_tables, iters, pl->dtune,
-                                 st));
+    return cuda_rc(launch_decode(pl->bmax, pl->d_dec, pl->count, pl->total_strips, pl->dec_tables, iters, pl->d4,
+                                 pl->dtune, st));
 }
 
 int fic_decode_batch(const fic_stream *sts, int count, int iters, uint8_t *const *d_outs, void *d_workspace,

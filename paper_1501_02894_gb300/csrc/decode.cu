@@ -92,6 +92,18 @@ struct StripInfo {
     uint32_t misc;   // upr | nvalid << 8 | centred << 16
 };
 
+// Per-strip word of the 2x2-sum iteration (centred streams).
+struct StripD4 {
+    uint16_t *d4[2];       // ping-pong 2x2-sum images, (W/2) x (H/2)
+    uint8_t *out;          // pixels, written by the last iteration
+    const TmaMap *map[2];  // tensor maps of d4[0], d4[1] (box 2*NP x BMAX)
+    uint32_t *info;        // the stream's info block (device error bits)
+    int32_t W;             // pixels
+    uint32_t sxy;          // sx0 | sy0 << 16
+    uint32_t wxy;          // window origin in 2x2-sum units: c_base | r_base << 16
+    uint32_t misc;         // nvalid << 8
+};
+
 // Per-half-patch words: fast word (c | rr << 8 | lg << 16 | cbyte << 24, O)
 // and, for domains outside the window, (dx | dy << 16, u0 | v0 << 8 | iso << 16).
 __device__ __forceinline__ uint32_t fast_word(int c, int rr, int lg, int cc) {
@@ -100,9 +112,9 @@ __device__ __forceinline__ uint32_t fast_word(int c, int rr, int lg, int cc) {
 
 // Transform words of one strip (the lookup of every half-patch's transform
 // in the strip's records), written to the decode tables.
-template <int BMAX>
+template <int BMAX, bool D4>
 __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, int count, const int *s_base, int g,
-                                            uint4 *recs, uint8_t *keys, StripInfo *sinfo, uint4 *tfw, uint4 *tgw,
+                                            uint4 *recs, uint8_t *keys, void *sinfo, uint4 *tfw, uint4 *tgw,
                                             int lane) {
     using G = DGeom<BMAX>;
     constexpr int PC = G::PC;
@@ -197,21 +209,36 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
     tfw[(size_t)g * 32 + lane] = make_uint4(fw[0], (uint32_t)Ow[0], fw[1], (uint32_t)Ow[1]);
     if (!centred) tgw[(size_t)g * 32 + lane] = make_uint4(gw[0], hw[0], gw[1], hw[1]);
     if (lane == 0) {
-        StripInfo si;
-        si.buf[0] = D.buf[0];
-        si.buf[1] = D.buf[1];
-        si.W = W;
-        si.sxy = (uint32_t)sx0 | ((uint32_t)sy0 << 16);
-        si.axy = (uint32_t)ax0 | ((uint32_t)ry0 << 16);
-        si.misc = (uint32_t)((ax1 - ax0) >> 4) | ((uint32_t)nvalid << 8) | ((centred ? 1u : 0u) << 16);
-        sinfo[g] = si;
+        if (D4) {
+            StripD4 si;
+            si.d4[0] = D.d4[0];
+            si.d4[1] = D.d4[1];
+            si.out = D.buf[0];
+            si.map[0] = D.map[0];
+            si.map[1] = D.map[1];
+            si.info = D.info;
+            si.W = W;
+            si.sxy = (uint32_t)sx0 | ((uint32_t)sy0 << 16);
+            si.wxy = (uint32_t)c_base | ((uint32_t)r_base << 16);
+            si.misc = (uint32_t)nvalid << 8;
+            static_cast<StripD4 *>(sinfo)[g] = si;
+        } else {
+            StripInfo si;
+            si.buf[0] = D.buf[0];
+            si.buf[1] = D.buf[1];
+            si.W = W;
+            si.sxy = (uint32_t)sx0 | ((uint32_t)sy0 << 16);
+            si.axy = (uint32_t)ax0 | ((uint32_t)ry0 << 16);
+            si.misc = (uint32_t)((ax1 - ax0) >> 4) | ((uint32_t)nvalid << 8) | ((centred ? 1u : 0u) << 16);
+            static_cast<StripInfo *>(sinfo)[g] = si;
+        }
     }
 }
 
-template <int BMAX>
+template <int BMAX, bool D4>
 __global__ void __launch_bounds__(kDecWarps * 32)
-    decode_setup_kernel(const DecDesc *__restrict__ descs, int count, int total_strips, StripInfo *sinfo,
-                        uint4 *tfw, uint4 *tgw) {
+    decode_setup_kernel(const DecDesc *__restrict__ descs, int count, int total_strips, void *sinfo, uint4 *tfw,
+                        uint4 *tgw) {
     __shared__ int s_base[kImgTable];
     __shared__ uint4 s_recs[kDecWarps][64];
     __shared__ uint8_t s_keys[kDecWarps][64];
@@ -221,7 +248,7 @@ __global__ void __launch_bounds__(kDecWarps * 32)
     __syncthreads();
     const int gwarps = gridDim.x * kDecWarps;
     for (int g = blockIdx.x * kDecWarps + warp; g < total_strips; g += gwarps)
-        setup_strip<BMAX>(descs, count, s_base, g, s_recs[warp], s_keys[warp], sinfo, tfw, tgw, lane);
+        setup_strip<BMAX, D4>(descs, count, s_base, g, s_recs[warp], s_keys[warp], sinfo, tfw, tgw, lane);
 }
 
 // First iteration from x0 = 128: d4 - mean d4 = 0, every pixel is its
@@ -234,7 +261,7 @@ __device__ __forceinline__ void first_strip(const StripInfo &si, uint4 tf, int s
     const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
     const int nvalid = (int)((si.misc >> 8) & 0xffu);
     if ((8 * pc) / BMAX >= nvalid) return;
-    uint8_t *out = const_cast<uint8_t *>(si.buf[src_sel ^ 1]) + (size_t)(sy0 + 4 * pr) * si.W + sx0 + 8 * pc;
+    uint8_t *out = const_cast<uint8_t *>(src_sel ? si.buf[0] : si.buf[1]) + (size_t)(sy0 + 4 * pr) * si.W + sx0 + 8 * pc;
     const int O0 = (int)tf.y, O1 = (int)tf.w;
     const uint32_t w0 = pack_sat_u8(O0, O0, pack_sat_u8(O0, O0, 0u));
     const uint32_t w1 = pack_sat_u8(O1, O1, pack_sat_u8(O1, O1, 0u));
@@ -242,69 +269,27 @@ __device__ __forceinline__ void first_strip(const StripInfo &si, uint4 tf, int s
     for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(out + (size_t)i * si.W) = make_uint2(w0, w1);
 }
 
-// One strip of one iteration after the first; for centred domains the
-// decimated window of the previous iterate is already staged in d4e.
+// Decimated domain values (16 per half-patch, packed pairs) of centred
+// transforms, read from the staged window, and the halves' partial Sd4.
 template <int BMAX>
-__device__ __forceinline__ void iterate_strip(const StripInfo &si, uint4 tf, const uint4 *__restrict__ tgw_row,
-                                              int src_sel, const uint32_t *d4e, int lane) {
-    using G = DGeom<BMAX>;
-    constexpr int PC = G::PC, NP = G::NP;
-    const int pr = lane / PC, pc = lane % PC;
-    const unsigned FULL = 0xffffffffu;
-    const int W = si.W;
-    const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
-    const int nvalid = (int)((si.misc >> 8) & 0xffu);
-    const bool centred = (si.misc >> 16) & 1u;
-    const bool valid = (8 * pc) / BMAX < nvalid;
-    const uint8_t *src = si.buf[src_sel];
-    uint8_t *out = const_cast<uint8_t *>(si.buf[src_sel ^ 1]) + (size_t)(sy0 + 4 * pr) * W + sx0 + 8 * pc;
-    const uint32_t fw[2] = {tf.x, tf.z};
-    const int Ov[2] = {(int)tf.y, (int)tf.w};
-
-    // ---- decimated domain values of the half-patches (16 each) and partial Sd4
-    uint32_t dv[2][4][2];  // [half][row][pair]
-    int part[2] = {0, 0};
-    int lg[2];
+__device__ __forceinline__ void load_centred(const uint32_t (&fw)[2], const uint32_t *d4e, uint32_t (&dv)[2][4][2],
+                                             int (&part)[2]) {
+    constexpr int NP = DGeom<BMAX>::NP;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        lg[h] = (int)((fw[h] >> 16) & 0xffu);
+        const int c = (int)(fw[h] & 0xffu), rr = (int)((fw[h] >> 8) & 0xffu);
+        const uint32_t *base = d4e + rr * NP + (c >> 1);
+        const bool odd = c & 1;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) dv[h][i][0] = dv[h][i][1] = 0u;
-        if (!valid) continue;
-        if (centred) {
-            const int c = (int)(fw[h] & 0xffu), rr = (int)((fw[h] >> 8) & 0xffu);
-            const uint32_t *base = d4e + rr * NP + (c >> 1);
-            const bool odd = c & 1;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint32_t e0 = base[i * NP], e1 = base[i * NP + 1];
-                if (odd) {
-                    const uint32_t e2 = base[i * NP + 2];
-                    dv[h][i][0] = __funnelshift_r(e0, e1, 16);
-                    dv[h][i][1] = __funnelshift_r(e1, e2, 16);
-                } else {
-                    dv[h][i][0] = e0;
-                    dv[h][i][1] = e1;
-                }
-            }
-        } else {
-            const uint4 gg = tgw_row[lane];
-            const uint32_t gd = h ? gg.z : gg.x, ge = h ? gg.w : gg.y;
-            const int dx = (int)(gd & 0xffffu), dy = (int)(gd >> 16);
-            const int u0 = (int)(ge & 0xffu), v0 = (int)((ge >> 8) & 0xffu), iso = (int)((ge >> 16) & 0xffu);
-            const int B = 1 << lg[h];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                uint32_t vals[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    int su, sv;
-                    iso_src(iso, B, u0 + e, v0 + i, su, sv);
-                    const uint8_t *p = src + (size_t)(dy + 2 * sv) * W + dx + 2 * su;
-                    vals[e] = (uint32_t)p[0] + p[1] + p[W] + p[W + 1];
-                }
-                dv[h][i][0] = vals[0] | (vals[1] << 16);
-                dv[h][i][1] = vals[2] | (vals[3] << 16);
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t e0 = base[i * NP], e1 = base[i * NP + 1];
+            if (odd) {
+                const uint32_t e2 = base[i * NP + 2];
+                dv[h][i][0] = __funnelshift_r(e0, e1, 16);
+                dv[h][i][1] = __funnelshift_r(e1, e2, 16);
+            } else {
+                dv[h][i][0] = e0;
+                dv[h][i][1] = e1;
             }
         }
         uint32_t pk = 0;
@@ -312,12 +297,23 @@ __device__ __forceinline__ void iterate_strip(const StripInfo &si, uint4 tf, con
         for (int i = 0; i < 4; ++i) pk += dv[h][i][0] + dv[h][i][1];
         part[h] = (int)((pk & 0xffffu) + (pk >> 16));
     }
-    // ---- Sd4 per transform: halves of one lane first (side >= 8), then the
-    // lane group of the transform; every lane runs the same shuffles
+}
+
+// Output pixels of both half-patches, rows packed 4 per word: Sd4 per
+// transform (halves of one lane first for sides >= 8, then the lane group
+// of the transform; every lane runs the same shuffles), then
+// p = (c d4 + K) >> 9 with K = floor((512 n O - c Sd4 + 256 n) / n).
+template <int BMAX>
+__device__ __forceinline__ void transform_rows(const uint32_t (&fw)[2], const int (&Ov)[2],
+                                               const uint32_t (&dv)[2][4][2], const int (&part)[2],
+                                               uint32_t (&w)[4][2]) {
+    constexpr int PC = DGeom<BMAX>::PC;
+    const unsigned FULL = 0xffffffffu;
+    const int lg0 = (int)((fw[0] >> 16) & 0xffu), lg1 = (int)((fw[1] >> 16) & 0xffu);
     int sd4[2];
     {
-        const bool big = lg[0] >= 3;  // a transform of side >= 8 covers both halves
-        const int B = 1 << lg[0];
+        const bool big = lg0 >= 3;  // a transform of side >= 8 covers both halves
+        const int B = 1 << lg0;
         const int gx = big ? B / 8 : 1, gy = big ? B / 4 : 1;
         int v = part[0] + part[1];
 #pragma unroll
@@ -333,24 +329,82 @@ __device__ __forceinline__ void iterate_strip(const StripInfo &si, uint4 tf, con
         sd4[0] = big ? v : part[0];
         sd4[1] = big ? v : part[1];
     }
+    int K[2], cb0[2], cb1[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int lg2n = 2 * (h ? lg1 : lg0);
+        const int c = (int)(int8_t)(fw[h] >> 24);
+        K[h] = (Ov[h] * (1 << (9 + lg2n)) + (1 << (8 + lg2n)) - c * sd4[h]) >> lg2n;
+        cb0[h] = (int)(fw[h] >> 24);
+        cb1[h] = (int)((fw[h] >> 24) << 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        w[i][0] = row_pixels(dv[0][i][0], dv[0][i][1], cb0[0], cb1[0], K[0]);
+        w[i][1] = row_pixels(dv[1][i][0], dv[1][i][1], cb0[1], cb1[1], K[1]);
+    }
+}
 
-    // ---- output pixels: p = (c d4 + K) >> 9 with K = floor((512 n O - c Sd4 + 256 n) / n)
-    if (valid) {
-        int K[2], cb0[2], cb1[2];
+// One strip of one iteration after the first; for centred domains the
+// decimated window of the previous iterate is already staged in d4e.
+template <int BMAX>
+__device__ __forceinline__ void iterate_strip(const StripInfo &si, uint4 tf, const uint4 *__restrict__ tgw_row,
+                                              int src_sel, const uint32_t *d4e, int lane) {
+    using G = DGeom<BMAX>;
+    constexpr int PC = G::PC;
+    const int pr = lane / PC, pc = lane % PC;
+    const int W = si.W;
+    const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
+    const int nvalid = (int)((si.misc >> 8) & 0xffu);
+    const bool centred = (si.misc >> 16) & 1u;
+    const bool valid = (8 * pc) / BMAX < nvalid;
+    const uint8_t *src = src_sel ? si.buf[1] : si.buf[0];
+    uint8_t *out = const_cast<uint8_t *>(src_sel ? si.buf[0] : si.buf[1]) + (size_t)(sy0 + 4 * pr) * W + sx0 + 8 * pc;
+    const uint32_t fw[2] = {tf.x, tf.z};
+    const int Ov[2] = {(int)tf.y, (int)tf.w};
+
+    uint32_t dv[2][4][2];  // [half][row][pair]
+    int part[2] = {0, 0};
+    if (!valid) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dv[h][i][0] = dv[h][i][1] = 0u;
+    } else if (centred) {
+        load_centred<BMAX>(fw, d4e, dv, part);
+    } else {
+        // domains outside the window (local / exhaustive search, isometries)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int lg2n = 2 * lg[h];
-            const int c = (int)(int8_t)(fw[h] >> 24);
-            K[h] = (Ov[h] * (1 << (9 + lg2n)) + (1 << (8 + lg2n)) - c * sd4[h]) >> lg2n;
-            cb0[h] = (int)(fw[h] >> 24);
-            cb1[h] = (int)((fw[h] >> 24) << 8);
-        }
+            const uint4 gg = tgw_row[lane];
+            const uint32_t gd = h ? gg.z : gg.x, ge = h ? gg.w : gg.y;
+            const int dx = (int)(gd & 0xffffu), dy = (int)(gd >> 16);
+            const int u0 = (int)(ge & 0xffu), v0 = (int)((ge >> 8) & 0xffu), iso = (int)((ge >> 16) & 0xffu);
+            const int B = 1 << ((fw[h] >> 16) & 0xffu);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t w0 = row_pixels(dv[0][i][0], dv[0][i][1], cb0[0], cb1[0], K[0]);
-            const uint32_t w1 = row_pixels(dv[1][i][0], dv[1][i][1], cb0[1], cb1[1], K[1]);
-            *reinterpret_cast<uint2 *>(out + (size_t)i * W) = make_uint2(w0, w1);
+            for (int i = 0; i < 4; ++i) {
+                uint32_t vals[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    int su, sv;
+                    iso_src(iso, B, u0 + e, v0 + i, su, sv);
+                    const uint8_t *p = src + (size_t)(dy + 2 * sv) * W + dx + 2 * su;
+                    vals[e] = (uint32_t)p[0] + p[1] + p[W] + p[W + 1];
+                }
+                dv[h][i][0] = vals[0] | (vals[1] << 16);
+                dv[h][i][1] = vals[2] | (vals[3] << 16);
+            }
+            uint32_t pk = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) pk += dv[h][i][0] + dv[h][i][1];
+            part[h] = (int)((pk & 0xffffu) + (pk >> 16));
         }
+    }
+    uint32_t w[4][2];
+    transform_rows<BMAX>(fw, Ov, dv, part, w);
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(out + (size_t)i * W) = make_uint2(w[i][0], w[i][1]);
     }
 }
 
@@ -372,12 +426,189 @@ __global__ void __launch_bounds__(kDecWarps * 32, 4)
         }
         __syncwarp();
         if ((si.misc >> 16) & 1u)
-            stage_window<BMAX, G::UPR, G::NP>(si.buf[src_sel], si.W, (int)(si.axy >> 16), (int)(si.axy & 0xffffu),
+            stage_window<BMAX, G::UPR, G::NP>(src_sel ? si.buf[1] : si.buf[0], si.W, (int)(si.axy >> 16), (int)(si.axy & 0xffffu),
                                               (int)(si.misc & 0xffu), d4e, lane);
         __syncwarp();
         iterate_strip<BMAX>(si, tf, tgw + (size_t)g * 32, src_sel, d4e, lane);
     }
 }
+
+// ---------------------------------------------------------------------------
+// 2x2-sum iteration for centred streams (no-search / MNS).
+//
+// A centred domain starts at even coordinates (x - B/2 with B >= 4, clamped
+// to the even W - 2B), so every decimated value the decoder reads is a value
+// of the previous iterate's 2x2-sum image on the even grid.  Between the
+// first and the last iteration the decoder therefore keeps that (W/2) x (H/2)
+// uint16 image instead of the pixels: an iteration fetches the strip's window
+// of 2x2 sums by TMA straight into the layout the lanes read (no decimation
+// pass), computes the output pixels exactly as above, and stores the 2x2
+// sums of those clamped pixels -- the values the next iteration would form
+// from them.  Only the last iteration writes pixels.  Each warp prefetches
+// its next strip's window into a second buffer while it computes.
+
+// 2x2 sums of two rows of four pixels each: (p0+p1+q0+q1) | (p2+p3+q2+q3) << 16.
+__device__ __forceinline__ uint32_t sum2x2(uint32_t a, uint32_t b) {
+    const uint32_t ha = (a & 0x00ff00ffu) + ((a >> 8) & 0x00ff00ffu);
+    const uint32_t hb = (b & 0x00ff00ffu) + ((b >> 8) & 0x00ff00ffu);
+    return ha + hb;
+}
+
+// First iteration from x0 = 128: every pixel is its transform's luminance.
+// Fields of a strip's StripD4 the lanes use (loaded field by field: the
+// ping-pong selection must not index the struct's arrays dynamically).
+struct StripD4Use {
+    uint8_t *out;
+    uint16_t *d4o;  // 2x2-sum image written by this iteration
+    uint32_t *info;
+    int W;
+    uint32_t sxy, misc;
+};
+
+__device__ __forceinline__ StripD4Use strip_d4_use(const StripD4 *sp, int dst) {
+    StripD4Use u;
+    u.out = sp->out;
+    u.d4o = dst ? sp->d4[1] : sp->d4[0];
+    u.info = sp->info;
+    u.W = sp->W;
+    u.sxy = sp->sxy;
+    u.misc = sp->misc;
+    return u;
+}
+
+template <int BMAX>
+__device__ __forceinline__ void first_d4(const StripD4Use &si, uint4 tf, bool last, int lane) {
+    constexpr int PC = DGeom<BMAX>::PC;
+    const int pr = lane / PC, pc = lane % PC;
+    const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
+    const int nvalid = (int)((si.misc >> 8) & 0xffu);
+    if ((8 * pc) / BMAX >= nvalid) return;
+    const int O0 = min(max((int)tf.y, 0), 255), O1 = min(max((int)tf.w, 0), 255);
+    if (last) {
+        uint8_t *out = si.out + (size_t)(sy0 + 4 * pr) * si.W + sx0 + 8 * pc;
+        const uint32_t w0 = (uint32_t)O0 * 0x01010101u, w1 = (uint32_t)O1 * 0x01010101u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(out + (size_t)i * si.W) = make_uint2(w0, w1);
+    } else {
+        const int W2 = si.W >> 1;
+        uint16_t *o = si.d4o + (size_t)((sy0 >> 1) + 2 * pr) * W2 + (sx0 >> 1) + 4 * pc;
+        const uint32_t w0 = (uint32_t)(4 * O0) * 0x00010001u, w1 = (uint32_t)(4 * O1) * 0x00010001u;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) *reinterpret_cast<uint2 *>(o + (size_t)j * W2) = make_uint2(w0, w1);
+    }
+}
+
+template <int BMAX>
+__device__ __forceinline__ void iterate_d4(const StripD4Use &si, uint4 tf, const uint32_t *win, bool last, int lane) {
+    constexpr int PC = DGeom<BMAX>::PC;
+    const int pr = lane / PC, pc = lane % PC;
+    const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
+    const int nvalid = (int)((si.misc >> 8) & 0xffu);
+    const bool valid = (8 * pc) / BMAX < nvalid;
+    const uint32_t fw[2] = {tf.x, tf.z};
+    const int Ov[2] = {(int)tf.y, (int)tf.w};
+    uint32_t dv[2][4][2];
+    int part[2] = {0, 0};
+    if (valid) {
+        load_centred<BMAX>(fw, win, dv, part);
+    } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dv[h][i][0] = dv[h][i][1] = 0u;
+    }
+    uint32_t w[4][2];
+    transform_rows<BMAX>(fw, Ov, dv, part, w);
+    if (!valid) return;
+    if (last) {
+        uint8_t *out = si.out + (size_t)(sy0 + 4 * pr) * si.W + sx0 + 8 * pc;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(out + (size_t)i * si.W) = make_uint2(w[i][0], w[i][1]);
+    } else {
+        const int W2 = si.W >> 1;
+        uint16_t *o = si.d4o + (size_t)((sy0 >> 1) + 2 * pr) * W2 + (sx0 >> 1) + 4 * pc;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            *reinterpret_cast<uint2 *>(o + (size_t)j * W2) =
+                make_uint2(sum2x2(w[2 * j][0], w[2 * j + 1][0]), sum2x2(w[2 * j][1], w[2 * j + 1][1]));
+    }
+}
+
+// kind bit 0: first iteration (from 128, reads nothing); bit 1: last
+// iteration (writes pixels).  src: the 2x2-sum image read (0/1); the other
+// one is written.
+template <int BMAX>
+__global__ void __launch_bounds__(kDecWarps * 32, 4)
+    decode_d4_iter_kernel(const StripD4 *__restrict__ sinfo, const uint4 *__restrict__ tfw, int total_strips, int src,
+                          int kind) {
+    using G = DGeom<BMAX>;
+    constexpr uint32_t WB = (uint32_t)G::WORDS * 4u;  // one window: BMAX rows x NP words
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t s_bar[kDecWarps][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned FULL = 0xffffffffu;
+    uint8_t *base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
+    uint32_t *win0 = reinterpret_cast<uint32_t *>(base + (size_t)(2 * warp) * WB);
+    uint32_t *win1 = reinterpret_cast<uint32_t *>(base + (size_t)(2 * warp + 1) * WB);
+    const bool first = kind & 1, last = (kind >> 1) & 1;
+    const int dst = first ? 0 : src ^ 1;
+    if (lane == 0) {
+        mbar_init(&s_bar[warp][0], 1);
+        mbar_init(&s_bar[warp][1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int gstep = gridDim.x * kDecWarps;
+    int g = blockIdx.x * kDecWarps + warp;
+    if (first) {
+        for (; g < total_strips; g += gstep)
+            first_d4<BMAX>(strip_d4_use(sinfo + g, dst), tfw[(size_t)g * 32 + lane], last, lane);
+        return;
+    }
+    auto issue = [&](int gi, int b) {
+        const StripD4 *sn = sinfo + gi;
+        const TmaMap *map = src ? sn->map[1] : sn->map[0];
+        const uint32_t wxy = sn->wxy;
+        uint64_t *bar = &s_bar[warp][b];
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, WB);
+        tma_load_2d(b ? win1 : win0, map, (int)(wxy & 0xffffu), (int)(wxy >> 16), bar);
+    };
+    uint32_t par0 = 0, par1 = 0;
+    int b = 0;
+    if (lane == 0 && g < total_strips) issue(g, 0);
+    for (; g < total_strips; g += gstep) {
+        const int gn = g + gstep;
+        const StripD4Use si = strip_d4_use(sinfo + g, dst);
+        const uint4 tf = tfw[(size_t)g * 32 + lane];
+        if (lane == 0 && gn < total_strips) issue(gn, b ^ 1);
+        const uint32_t par = b ? par1 : par0;
+        const bool arrived = mbar_wait(&s_bar[warp][b], par, kMbarLimit);
+        if (!__all_sync(FULL, arrived)) {
+            // give both buffers' copies a bounded chance to land, then leave
+            if (lane == 0) {
+                raise_error(si.info, FIC_DEVERR_TIMEOUT);
+                mbar_wait(&s_bar[warp][b], par, kMbarLimit);
+                if (gn < total_strips) mbar_wait(&s_bar[warp][b ^ 1], b ? par0 : par1, kMbarLimit);
+            }
+            __syncwarp();
+            return;
+        }
+        if (b) par1 ^= 1u;
+        else par0 ^= 1u;
+        iterate_d4<BMAX>(si, tf, b ? win1 : win0, last, lane);
+        __syncwarp();
+        b ^= 1;
+    }
+}
+
+size_t decode_d4_smem_bytes(int bmax) {
+    const int words = bmax == 32 ? DGeom<32>::WORDS : (bmax == 16 ? DGeom<16>::WORDS : DGeom<8>::WORDS);
+    return (size_t)kDecWarps * 2 * words * sizeof(uint32_t) + 128;
+}
+
+// Box width (in 2x2 sums) of the decoder's window loads.
+int decode_d4_box(int bmax) { return 2 * (bmax == 32 ? DGeom<32>::NP : (bmax == 16 ? DGeom<16>::NP : DGeom<8>::NP)); }
 
 size_t decode_table_bytes_per_strip() { return sizeof(StripInfo) + 2 * 32 * sizeof(uint4); }
 
@@ -399,28 +630,55 @@ static void occupancy_of(const void *fn, size_t smem, int &sms, int &per) {
 
 // Decode: the table setup kernel, then one launch per iteration.
 template <int BMAX>
-static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, void *tables, int iters,
+static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, void *tables, int iters, bool d4,
                              const DecTune &tune, cudaStream_t st) {
-    static int sms_setup = 0, per_setup = 0, sms_iter = 0, per_iter = 0;
+    static int sms_setup = 0, per_setup = 0, sms_iter = 0, per_iter = 0, sms_d4 = 0, per_d4 = 0;
     static bool attr = false;
-    const size_t smem = decode_smem_bytes(BMAX);
+    const size_t smem = decode_smem_bytes(BMAX), smem_d4 = decode_d4_smem_bytes(BMAX);
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(decode_iter_kernel<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(decode_d4_iter_kernel<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_d4);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    StripInfo *sinfo = static_cast<StripInfo *>(tables);
-    uint4 *tfw = reinterpret_cast<uint4 *>(sinfo + total_strips);
+    const size_t info_bytes = d4 ? sizeof(StripD4) : sizeof(StripInfo);
+    uint4 *tfw = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(tables) + info_bytes * (size_t)total_strips);
     uint4 *tgw = tfw + (size_t)total_strips * 32;
     const int need = (total_strips + kDecWarps - 1) / kDecWarps;
-    occupancy_of((const void *)decode_setup_kernel<BMAX>, 0, sms_setup, per_setup);
-    const int gs = sms_setup * per_setup;
-    decode_setup_kernel<BMAX><<<need < gs ? need : gs, kDecWarps * 32, 0, st>>>(descs, count, total_strips, sinfo,
-                                                                              tfw, tgw);
+    if (d4) {
+        occupancy_of((const void *)decode_setup_kernel<BMAX, true>, 0, sms_setup, per_setup);
+        const int gs = sms_setup * per_setup;
+        decode_setup_kernel<BMAX, true><<<need < gs ? need : gs, kDecWarps * 32, 0, st>>>(descs, count, total_strips,
+                                                                                        tables, tfw, tgw);
+    } else {
+        occupancy_of((const void *)decode_setup_kernel<BMAX, false>, 0, sms_setup, per_setup);
+        const int gs = sms_setup * per_setup;
+        decode_setup_kernel<BMAX, false><<<need < gs ? need : gs, kDecWarps * 32, 0, st>>>(descs, count, total_strips,
+                                                                                         tables, tfw, tgw);
+    }
     stage_mark(st, "decode_setup_kernel");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (d4) {
+        const StripD4 *sinfo = static_cast<const StripD4 *>(tables);
+        occupancy_of((const void *)decode_d4_iter_kernel<BMAX>, smem_d4, sms_d4, per_d4);
+        const int k = tune.ctas_per_sm > 0 && tune.ctas_per_sm < per_d4 ? tune.ctas_per_sm : per_d4;
+        const int grid = need < sms_d4 * k ? need : sms_d4 * k;
+        for (int it = 0; it < iters; ++it) {
+            // iteration it >= 1 reads image (it - 1) & 1; the first writes image 0
+            const int kind = (it == 0 ? 1 : 0) | (it == iters - 1 ? 2 : 0);
+            decode_d4_iter_kernel<BMAX><<<grid, kDecWarps * 32, smem_d4, st>>>(sinfo, tfw, total_strips,
+                                                                               (it - 1) & 1, kind);
+            stage_mark(st, "decode_d4_iter_kernel");
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    const StripInfo *sinfo = static_cast<const StripInfo *>(tables);
     occupancy_of((const void *)decode_iter_kernel<BMAX>, smem, sms_iter, per_iter);
     const int k = tune.ctas_per_sm > 0 && tune.ctas_per_sm < per_iter ? tune.ctas_per_sm : per_iter;
     const int gi = sms_iter * k;
@@ -436,11 +694,11 @@ static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, 
 }
 
 cudaError_t launch_decode(int bmax, const DecDesc *d_descs, int count, int total_strips, void *tables, int iters,
-                          const DecTune &tune, cudaStream_t st) {
+                          bool d4, const DecTune &tune, cudaStream_t st) {
     switch (bmax) {
-    case 32: return dlaunch_t<32>(d_descs, count, total_strips, tables, iters, tune, st);
-    case 16: return dlaunch_t<16>(d_descs, count, total_strips, tables, iters, tune, st);
-    case 8: return dlaunch_t<8>(d_descs, count, total_strips, tables, iters, tune, st);
+    case 32: return dlaunch_t<32>(d_descs, count, total_strips, tables, iters, d4, tune, st);
+    case 16: return dlaunch_t<16>(d_descs, count, total_strips, tables, iters, d4, tune, st);
+    case 8: return dlaunch_t<8>(d_descs, count, total_strips, tables, iters, d4, tune, st);
     default: return cudaErrorInvalidValue;
     }
 }

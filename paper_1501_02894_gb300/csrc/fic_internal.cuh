@@ -50,9 +50,10 @@ struct WinBox {
     static constexpr int H = 2 * BMAX;
 };
 
-// Build the tensor map of a W x H uint8 image for boxes of boxw x boxh
-// (host side; the driver entry point is looked up once).
-int make_tma_map(TmaMap *out, const void *base, int W, int H, int boxw, int boxh);
+// Build the tensor map of a W x H image of uint8 (elem_bytes 1) or uint16
+// (elem_bytes 2) elements, rows W elements apart, for boxes of boxw x boxh
+// elements (host side; the driver entry point is looked up once).
+int make_tma_map(TmaMap *out, const void *base, int W, int H, int boxw, int boxh, int elem_bytes = 1);
 
 // Per-kernel timing of a plan run (fic_plan_run_timed): launchers call this
 // after every kernel launch; it records an event only while a timed run is
@@ -78,6 +79,11 @@ struct DecDesc {
     int32_t W, H;
     int32_t tw, th, spr, strip_base, nstrips;
     int32_t mode, bmin, L, s_bits, o_bits;
+    // 2x2-sum iteration (centred streams): ping-pong (W/2) x (H/2) images of
+    // 2x2 sums, their tensor maps, and the stream's info block for errors
+    uint16_t *d4[2];
+    const TmaMap *map[2];
+    uint32_t *info;
 };
 
 // Fixed-point codebooks (Section 3.3): c = 128 s on 2^s_bits cell midpoints
