@@ -483,7 +483,7 @@ def run_batched(args, spec: Spec):
     peak = float(peaks["hbm_gbs"])
     enc_bytes = pixels + sum(16 * r for r in nrec) + sum(8 * t + 4 for t in ntops)
     dec_bytes_iter = 2 * pixels + sum(16 * r for r in nrec) + sum(4 * (t + 1) for t in ntops)
-    alg = {"mns_encode_kernel": enc_bytes, "decode_iter_kernel": dec_bytes_iter}
+    alg = {"mns_encode_kernel": enc_bytes, "decode_iter_kernel": dec_bytes_iter, "decode_d4_iter_kernel": dec_bytes_iter}
     dom = max((k for k in ktab if k in alg), key=lambda k: ktab[k]["share"])
     ach = alg[dom] / (ktab[dom]["ms_per_launch"] * 1e-3) / 1e9
     key = f"{dom}_{spec.name}"
@@ -737,6 +737,7 @@ def run_serving(args):
         bufs = Buffers()
         live = {}  # ticket -> (i, key, bufs, submit lag)
         lat = np.zeros(nreq)
+        qms = np.zeros(nreq)
         px_done = 0
         order = []
         t0 = time.perf_counter() + 0.05
@@ -751,6 +752,7 @@ def run_serving(args):
                 order.pop(0)
                 i, key, b, lag = live.pop(tk)
                 lat[i] = lag + r["latency_ms"]
+                qms[i] = lag + r["queue_ms"]
                 px_done += int(side[i]) ** 2
                 for k2, v in zip(key, b):
                     bufs.put(k2, v)
@@ -778,7 +780,7 @@ def run_serving(args):
         t_end = time.perf_counter() - t0
         st = srv.stats()
         srv.close()
-        return lat, px_done, t_end, st
+        return lat, px_done, t_end, st, qms
 
     def serve_plain():
         """One request at a time in arrival order: copy in, fic_encode or
@@ -815,7 +817,7 @@ def run_serving(args):
 
     sampler = ClockSampler(gpu_uuid(torch, dev))
     sampler.start()
-    lat_s, px_s, t_s, stats = serve_with_server()
+    lat_s, px_s, t_s, stats, q_s = serve_with_server()
     clocks = sampler.stop()
     lat_p, px_p, t_p, served_p = serve_plain()
 
@@ -836,6 +838,11 @@ def run_serving(args):
         "latency_ms": {"p50": pct(lat_s, 50), "p99": pct(lat_s, 99), "mean": round(float(np.mean(lat_s)), 3),
                        "max": round(float(np.max(lat_s)), 3), "from": "arrival to result in the caller's buffer"},
         "server_stats": stats,
+        "by_side": {name: {"requests": int(m.sum()), "p50_ms": pct(lat_s[m], 50), "p99_ms": pct(lat_s[m], 99),
+                           "queue_p50_ms": pct(q_s[m], 50), "plain_p50_ms": pct(lat_p[m[:len(lat_p)]], 50),
+                           "plain_p99_ms": pct(lat_p[m[:len(lat_p)]], 99)}
+                    for name, m in (("side<512", side < 512), ("512<=side<1536", (side >= 512) & (side < 1536)),
+                                    ("side>=1536", side >= 1536))},
         "plain_per_request": {"mpix_s": round(px_p / t_p / 1e6, 3), "served": int(served_p),
                               "latency_ms": {"p50": pct(lat_p, 50), "p99": pct(lat_p, 99),
                                              "mean": round(float(np.mean(lat_p)), 3) if len(lat_p) else None},

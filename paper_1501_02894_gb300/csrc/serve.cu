@@ -10,6 +10,7 @@
 // arrive while batches run are admitted as soon as memory frees, so batches
 // of different arrival times overlap on the device.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -94,6 +95,72 @@ struct Alloc {
     size_t n = 0;
 };
 
+// Host copies between the caller's buffers and pinned staging.  Large ones
+// are split over a few helper threads: one thread's memcpy bandwidth would
+// otherwise bound the server on big images.
+class CopyPool {
+  public:
+    explicit CopyPool(int helpers) {
+        for (int i = 0; i < helpers; ++i) threads_.emplace_back([this] { run(); });
+    }
+    ~CopyPool() {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : threads_) t.join();
+    }
+    void copy(void *dst, const void *src, size_t n) {
+        const size_t parts = std::min(threads_.size() + 1, n / kChunk);
+        if (parts <= 1) {
+            memcpy(dst, src, n);
+            return;
+        }
+        const size_t per = (n / parts + 63) & ~(size_t)63;
+        std::atomic<int> left((int)parts - 1);
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            for (size_t k = 1; k < parts; ++k) {
+                const size_t off = k * per, len = std::min(per, n - std::min(n, off));
+                tasks_.push_back(Task{static_cast<uint8_t *>(dst) + off, static_cast<const uint8_t *>(src) + off, len,
+                                      &left});
+            }
+        }
+        cv_.notify_all();
+        memcpy(dst, src, std::min(per, n));
+        while (left.load(std::memory_order_acquire) > 0) std::this_thread::yield();
+    }
+
+  private:
+    static constexpr size_t kChunk = 1 << 20;
+    struct Task {
+        uint8_t *dst;
+        const uint8_t *src;
+        size_t n;
+        std::atomic<int> *left;
+    };
+    void run() {
+        for (;;) {
+            Task t;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [this] { return stop_ || !tasks_.empty(); });
+                if (stop_ && tasks_.empty()) return;
+                t = tasks_.front();
+                tasks_.pop_front();
+            }
+            if (t.n) memcpy(t.dst, t.src, t.n);
+            t.left->fetch_sub(1, std::memory_order_release);
+        }
+    }
+    std::vector<std::thread> threads_;
+    std::deque<Task> tasks_;
+    std::mutex mu_;
+    std::condition_variable cv_;
+    bool stop_ = false;
+};
+
 struct Job {
     int64_t ticket = 0;
     fic_job job{};
@@ -135,6 +202,7 @@ struct fic_server {
     int64_t next_ticket = 1;
     bool stopping = false;
     std::thread worker;
+    CopyPool copies{3};
 
     // statistics
     int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batched_jobs = 0;
@@ -193,13 +261,13 @@ bool prepare_job(fic_server *S, Job *J) {
     const size_t meta = a256(4 * ((size_t)J->ntop + 1)) + a256(4 * (size_t)J->ntop) + 256;
     if (j.kind == FIC_JOB_ENCODE) {
         ok = ok && dget(J->d_img, img) && dget(J->d_rec, (size_t)J->cap * 16) && dget(J->d_meta, meta);
-        if (ok) memcpy(J->h_stage.p, j.image, img);
+        if (ok) S->copies.copy(J->h_stage.p, j.image, img);
     } else {
         ok = ok && dget(J->d_rec, (size_t)std::max(j.nrecords, 1) * 16) && dget(J->d_meta, meta) &&
              dget(J->d_out, img);
         if (ok) {
             // records and the tile offsets of the canonical order
-            memcpy(J->h_stage.p, j.records, (size_t)j.nrecords * 16);
+            S->copies.copy(J->h_stage.p, j.records, (size_t)j.nrecords * 16);
             uint32_t *offs = reinterpret_cast<uint32_t *>(J->h_stage.p + a256((size_t)std::max(j.nrecords, 1) * 16));
             const int bmax = j.params.bmax, tw = j.width / bmax;
             int r = 0;
@@ -370,11 +438,11 @@ void finish_job(fic_server *S, Job *J, int status, Clock::time_point now) {
         else if (info[FIC_INFO_ERROR] & FIC_DEVERR_CAPACITY) r.status = FIC_ECAPACITY;
         r.nrecords = (int32_t)info[FIC_INFO_RECORDS];
         r.fits = (int64_t)info[FIC_INFO_FITS_LO] | ((int64_t)info[FIC_INFO_FITS_HI] << 32);
-        if (j.out_records) memcpy(j.out_records, h, (size_t)std::min(r.nrecords, J->cap) * 16);
+        if (j.out_records) S->copies.copy(j.out_records, h, (size_t)std::min(r.nrecords, J->cap) * 16);
         if (j.out_split) memcpy(j.out_split, h + a256((size_t)J->cap * 16), 4 * (size_t)J->ntop);
     } else if (status == FIC_OK) {
         const size_t rb = (size_t)std::max(j.nrecords, 1) * 16;
-        if (j.out_image) memcpy(j.out_image, J->h_stage.p + a256(rb) + a256(4 * ((size_t)J->ntop + 1)), img);
+        if (j.out_image) S->copies.copy(j.out_image, J->h_stage.p + a256(rb) + a256(4 * ((size_t)J->ntop + 1)), img);
     }
     r.latency_ms = std::chrono::duration<double, std::milli>(now - J->t_submit).count();
     r.queue_ms = std::chrono::duration<double, std::milli>(J->t_launch - J->t_submit).count();
