@@ -362,16 +362,31 @@ def run_batched(args, spec: Spec):
     pixels = spec.pixels
     iters = spec.iters
     plist = [fic.params(m, bmax, bmin, t) for _, m, bmax, bmin, t in items]
-    host = [torch.from_numpy(it[0]).pin_memory() for it in items]
-    dimgs = [h.to(dev) for h in host]
+    # one pinned host arena and one device arena for the batch's images, one
+    # device arena for all streams' records and info blocks, one for the
+    # decoded images: the end-to-end pass moves each with a single copy
+    offs = np.cumsum([0] + [it[0].size for it in items])
+    host_in = torch.empty(int(offs[-1]), dtype=torch.uint8).pin_memory()
+    for it, o in zip(items, offs):
+        host_in[int(o): int(o) + it[0].size].copy_(torch.from_numpy(it[0].reshape(-1)))
+    dev_in = host_in.to(dev)
+    dimgs = [dev_in[int(o): int(o) + it[0].size].view(it[0].shape) for it, o in zip(items, offs)]
+    caps = [fic.stream_sizes(it[0].shape[1], it[0].shape[0], p)[1] for it, p in zip(items, plist)]
+    roffs = np.cumsum([0] + [16 * c for c in caps])
+    rec_arena = torch.empty(int(roffs[-1]), dtype=torch.uint8, device=dev)
+    info_arena = torch.zeros((n, fic.INFO_WORDS), dtype=torch.int32, device=dev)
+    outs_s = [fic.Stream(it[0].shape[1], it[0].shape[0], p, dev, records=rec_arena[int(a): int(b)], info=info_arena[i])
+              for i, (it, p, a, b) in enumerate(zip(items, plist, roffs[:-1], roffs[1:]))]
+    dec_arena = torch.empty(int(offs[-1]), dtype=torch.uint8, device=dev)
+    dec_outs = [dec_arena[int(o): int(o) + it[0].size].view(it[0].shape) for it, o in zip(items, offs)]
     stream = torch.cuda.Stream(dev)
     flush_l2 = pixels < 2 * L2_BYTES
     flush = torch.empty(256 << 20 if flush_l2 else 1, dtype=torch.uint8, device=dev)
 
     with torch.cuda.stream(stream):
-        enc = fic.EncodePlan(dimgs, plist, stream=stream)
+        enc = fic.EncodePlan(dimgs, plist, outs=outs_s, stream=stream)
         enc.run(stream)
-        dec = fic.DecodePlan(enc.outs, stream=stream)
+        dec = fic.DecodePlan(enc.outs, outs=dec_outs, stream=stream)
         dec.run(iters, stream)
     stream.synchronize()
     tuning = None
@@ -450,30 +465,30 @@ def run_batched(args, spec: Spec):
             krows.append(enc.run_timed(stream) + dec.run_timed(iters, stream))
     ktab = kernel_table(krows)
 
-    # ---- end to end through the public API: pinned host images in, streams and
-    # decoded images out, copies inside the timed region
-    out_host = [torch.empty(tuple(it[0].shape), dtype=torch.uint8).pin_memory() for it in items]
-    rec_host = [torch.empty(st.records.numel(), dtype=torch.uint8).pin_memory() for st in enc.outs]
-    info_host = torch.empty((n, 16), dtype=torch.int32).pin_memory()
-    h2d = pixels
-    d2h = pixels + sum(16 * r for r in nrec) + 64 * n
+    # ---- end to end through the public API: the pinned host images in, every
+    # stream's records and info block and the decoded images out, the copies
+    # inside the timed region (one copy per arena)
+    out_host = torch.empty(int(offs[-1]), dtype=torch.uint8).pin_memory()
+    rec_host = torch.empty(rec_arena.numel(), dtype=torch.uint8).pin_memory()
+    info_host = torch.empty((n, fic.INFO_WORDS), dtype=torch.int32).pin_memory()
+    h2d = host_in.numel()
+    d2h = out_host.numel() + rec_host.numel() + 4 * info_host.numel()
     e2e_ev = []
     with torch.cuda.stream(stream):
         for i in range(warm + args.steps):
             s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             flush.fill_(i & 0xff)
             s0.record(stream)
-            for h, d in zip(host, dimgs):
-                d.copy_(h, non_blocking=True)
+            dev_in.copy_(host_in, non_blocking=True)
             g_enc.replay()
             g_dec.replay()
-            for j, st in enumerate(enc.outs):
-                info_host[j].copy_(st.info, non_blocking=True)
-                rec_host[j][: 16 * nrec[j]].copy_(st.records[: 16 * nrec[j]], non_blocking=True)
-                out_host[j].copy_(dec.outs[j], non_blocking=True)
+            info_host.copy_(info_arena, non_blocking=True)
+            rec_host.copy_(rec_arena, non_blocking=True)
+            out_host.copy_(dec_arena, non_blocking=True)
             s1.record(stream)
             e2e_ev.append((s0, s1))
     stream.synchronize()
+    assert np.array_equal(rec_host[: 16 * nrec[0]].numpy(), ref0["records"].view(np.uint8)), "e2e copy differs"
     e2e_ms, e2e_px_s = replica_throughput(world, dev, statistics.mean(a.elapsed_time(b) for a, b in e2e_ev[warm:]),
                                           pixels)
     e2e_value = e2e_px_s / 1e6

@@ -6,6 +6,7 @@ This package is the Python binding of that library (``fic.py``) and its
 build script (``build.py``); the kernels live in ``csrc/``.
 """
 from .fic import (  # noqa: F401
+    INFO_WORDS,
     RECORD_DTYPE,
     Server,
     Tuning,
@@ -21,5 +22,6 @@ from .fic import (  # noqa: F401
     fic_encode_noalloc,
     lib,
     params,
+    stream_sizes,
     validate,
 )

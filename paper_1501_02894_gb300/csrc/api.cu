@@ -173,11 +173,11 @@ static ExhLayout exh_layout(int W, int H, const fic_params *p, int *nd_out, int 
     L.dfp16 = L.dpairs + align_up((size_t)nd * 128);
     L.dstat = L.dfp16 + align_up((size_t)nd_pad * 128);
     L.dscr = L.dstat + align_up((size_t)nd_pad * 16);
-    L.afp16 = L.dscr + align_up((size_t)nd_pad * 8);
+    L.afp16 = L.dscr + align_up((size_t)nd_pad * 16);
     L.rstat = L.afp16 + align_up(nr * 8 * 128);
     L.row_g = L.rstat + align_up(nr * 16);
-    L.row_dk = L.row_g + align_up(nr * 8 * 8);
-    L.total = L.row_dk + align_up(nr * 8 * 8);
+    L.row_dk = L.row_g + align_up(nr * 8 * 8 * kExhMaxSeg);
+    L.total = L.row_dk + align_up(nr * 8 * 8 * kExhMaxSeg);
     if (nd_out) *nd_out = nd;
     if (nd_pad_out) *nd_pad_out = nd_pad;
     if (ndx_out) *ndx_out = ndx;
@@ -235,7 +235,8 @@ static int exh_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
         E.dpairs = reinterpret_cast<uint32_t *>(w + off + L.dpairs);
         E.dfp16 = reinterpret_cast<__half *>(w + off + L.dfp16);
         E.dstat = reinterpret_cast<int4 *>(w + off + L.dstat);
-        E.dscr = reinterpret_cast<float2 *>(w + off + L.dscr);
+        E.dscr = reinterpret_cast<float4 *>(w + off + L.dscr);
+        E.nseg = 1;
         E.afp16 = reinterpret_cast<__half *>(w + off + L.afp16);
         E.rstat = reinterpret_cast<int4 *>(w + off + L.rstat);
         E.row_g = reinterpret_cast<long long *>(w + off + L.row_g);

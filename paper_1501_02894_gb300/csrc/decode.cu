@@ -103,6 +103,58 @@ struct StripD4 {
     uint32_t wxy;          // window origin in 2x2-sum units: c_base | r_base << 16
     uint32_t misc;         // nvalid << 8
 };
+static_assert(sizeof(StripD4) == 64, "strip word: one 64-byte bulk copy");
+
+// 2x2 sums of two rows of four pixels each: (p0+p1+q0+q1) | (p2+p3+q2+q3) << 16.
+__device__ __forceinline__ uint32_t sum2x2(uint32_t a, uint32_t b) {
+    const uint32_t ha = (a & 0x00ff00ffu) + ((a >> 8) & 0x00ff00ffu);
+    const uint32_t hb = (b & 0x00ff00ffu) + ((b >> 8) & 0x00ff00ffu);
+    return ha + hb;
+}
+
+// First iteration from x0 = 128: every pixel is its transform's luminance.
+// Fields of a strip's StripD4 the lanes use (loaded field by field: the
+// ping-pong selection must not index the struct's arrays dynamically).
+struct StripD4Use {
+    uint8_t *out;
+    uint16_t *d4o;  // 2x2-sum image written by this iteration
+    uint32_t *info;
+    int W;
+    uint32_t sxy, misc;
+};
+
+__device__ __forceinline__ StripD4Use strip_d4_use(const StripD4 *sp, int dst) {
+    StripD4Use u;
+    u.out = sp->out;
+    u.d4o = dst ? sp->d4[1] : sp->d4[0];
+    u.info = sp->info;
+    u.W = sp->W;
+    u.sxy = sp->sxy;
+    u.misc = sp->misc;
+    return u;
+}
+
+template <int BMAX>
+__device__ __forceinline__ void first_d4(const StripD4Use &si, uint4 tf, bool last, int lane) {
+    constexpr int PC = DGeom<BMAX>::PC;
+    const int pr = lane / PC, pc = lane % PC;
+    const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
+    const int nvalid = (int)((si.misc >> 8) & 0xffu);
+    if ((8 * pc) / BMAX >= nvalid) return;
+    const int O0 = min(max((int)tf.y, 0), 255), O1 = min(max((int)tf.w, 0), 255);
+    if (last) {
+        uint8_t *out = si.out + (size_t)(sy0 + 4 * pr) * si.W + sx0 + 8 * pc;
+        const uint32_t w0 = (uint32_t)O0 * 0x01010101u, w1 = (uint32_t)O1 * 0x01010101u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(out + (size_t)i * si.W) = make_uint2(w0, w1);
+    } else {
+        const int W2 = si.W >> 1;
+        uint16_t *o = si.d4o + (size_t)((sy0 >> 1) + 2 * pr) * W2 + (sx0 >> 1) + 4 * pc;
+        const uint32_t w0 = (uint32_t)(4 * O0) * 0x00010001u, w1 = (uint32_t)(4 * O1) * 0x00010001u;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) *reinterpret_cast<uint2 *>(o + (size_t)j * W2) = make_uint2(w0, w1);
+    }
+}
 
 // Per-half-patch words: fast word (c | rr << 8 | lg << 16 | cbyte << 24, O)
 // and, for domains outside the window, (dx | dy << 16, u0 | v0 << 8 | iso << 16).
@@ -115,7 +167,7 @@ __device__ __forceinline__ uint32_t fast_word(int c, int rr, int lg, int cc) {
 template <int BMAX, bool D4>
 __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, int count, const int *s_base, int g,
                                             uint4 *recs, uint8_t *keys, void *sinfo, uint4 *tfw, uint4 *tgw,
-                                            int lane) {
+                                            int first_kind, int lane) {
     using G = DGeom<BMAX>;
     constexpr int PC = G::PC;
     const int pr = lane / PC, pc = lane % PC;
@@ -206,8 +258,20 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
         gw[h] = (uint32_t)t_dx | ((uint32_t)t_dy << 16);
         hw[h] = (uint32_t)u0 | ((uint32_t)v0 << 8) | ((uint32_t)t_iso << 16);
     }
-    tfw[(size_t)g * 32 + lane] = make_uint4(fw[0], (uint32_t)Ow[0], fw[1], (uint32_t)Ow[1]);
+    const uint4 tf = make_uint4(fw[0], (uint32_t)Ow[0], fw[1], (uint32_t)Ow[1]);
+    tfw[(size_t)g * 32 + lane] = tf;
     if (!centred) tgw[(size_t)g * 32 + lane] = make_uint4(gw[0], hw[0], gw[1], hw[1]);
+    if (D4 && first_kind) {
+        // the first iteration from 128 needs only the luminance: written here
+        StripD4Use u;
+        u.out = D.buf[0];
+        u.d4o = D.d4[0];
+        u.info = D.info;
+        u.W = W;
+        u.sxy = (uint32_t)sx0 | ((uint32_t)sy0 << 16);
+        u.misc = (uint32_t)nvalid << 8;
+        first_d4<BMAX>(u, tf, first_kind == 3, lane);
+    }
     if (lane == 0) {
         if (D4) {
             StripD4 si;
@@ -238,7 +302,7 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
 template <int BMAX, bool D4>
 __global__ void __launch_bounds__(kDecWarps * 32)
     decode_setup_kernel(const DecDesc *__restrict__ descs, int count, int total_strips, void *sinfo, uint4 *tfw,
-                        uint4 *tgw) {
+                        uint4 *tgw, int first_kind) {
     __shared__ int s_base[kImgTable];
     __shared__ uint4 s_recs[kDecWarps][64];
     __shared__ uint8_t s_keys[kDecWarps][64];
@@ -248,7 +312,7 @@ __global__ void __launch_bounds__(kDecWarps * 32)
     __syncthreads();
     const int gwarps = gridDim.x * kDecWarps;
     for (int g = blockIdx.x * kDecWarps + warp; g < total_strips; g += gwarps)
-        setup_strip<BMAX, D4>(descs, count, s_base, g, s_recs[warp], s_keys[warp], sinfo, tfw, tgw, lane);
+        setup_strip<BMAX, D4>(descs, count, s_base, g, s_recs[warp], s_keys[warp], sinfo, tfw, tgw, first_kind, lane);
 }
 
 // First iteration from x0 = 128: d4 - mean d4 = 0, every pixel is its
@@ -447,57 +511,6 @@ __global__ void __launch_bounds__(kDecWarps * 32, 4)
 // from them.  Only the last iteration writes pixels.  Each warp prefetches
 // its next strip's window into a second buffer while it computes.
 
-// 2x2 sums of two rows of four pixels each: (p0+p1+q0+q1) | (p2+p3+q2+q3) << 16.
-__device__ __forceinline__ uint32_t sum2x2(uint32_t a, uint32_t b) {
-    const uint32_t ha = (a & 0x00ff00ffu) + ((a >> 8) & 0x00ff00ffu);
-    const uint32_t hb = (b & 0x00ff00ffu) + ((b >> 8) & 0x00ff00ffu);
-    return ha + hb;
-}
-
-// First iteration from x0 = 128: every pixel is its transform's luminance.
-// Fields of a strip's StripD4 the lanes use (loaded field by field: the
-// ping-pong selection must not index the struct's arrays dynamically).
-struct StripD4Use {
-    uint8_t *out;
-    uint16_t *d4o;  // 2x2-sum image written by this iteration
-    uint32_t *info;
-    int W;
-    uint32_t sxy, misc;
-};
-
-__device__ __forceinline__ StripD4Use strip_d4_use(const StripD4 *sp, int dst) {
-    StripD4Use u;
-    u.out = sp->out;
-    u.d4o = dst ? sp->d4[1] : sp->d4[0];
-    u.info = sp->info;
-    u.W = sp->W;
-    u.sxy = sp->sxy;
-    u.misc = sp->misc;
-    return u;
-}
-
-template <int BMAX>
-__device__ __forceinline__ void first_d4(const StripD4Use &si, uint4 tf, bool last, int lane) {
-    constexpr int PC = DGeom<BMAX>::PC;
-    const int pr = lane / PC, pc = lane % PC;
-    const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
-    const int nvalid = (int)((si.misc >> 8) & 0xffu);
-    if ((8 * pc) / BMAX >= nvalid) return;
-    const int O0 = min(max((int)tf.y, 0), 255), O1 = min(max((int)tf.w, 0), 255);
-    if (last) {
-        uint8_t *out = si.out + (size_t)(sy0 + 4 * pr) * si.W + sx0 + 8 * pc;
-        const uint32_t w0 = (uint32_t)O0 * 0x01010101u, w1 = (uint32_t)O1 * 0x01010101u;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(out + (size_t)i * si.W) = make_uint2(w0, w1);
-    } else {
-        const int W2 = si.W >> 1;
-        uint16_t *o = si.d4o + (size_t)((sy0 >> 1) + 2 * pr) * W2 + (sx0 >> 1) + 4 * pc;
-        const uint32_t w0 = (uint32_t)(4 * O0) * 0x00010001u, w1 = (uint32_t)(4 * O1) * 0x00010001u;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) *reinterpret_cast<uint2 *>(o + (size_t)j * W2) = make_uint2(w0, w1);
-    }
-}
-
 template <int BMAX>
 __device__ __forceinline__ void iterate_d4(const StripD4Use &si, uint4 tf, const uint32_t *win, bool last, int lane) {
     constexpr int PC = DGeom<BMAX>::PC;
@@ -651,13 +664,14 @@ static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, 
     if (d4) {
         occupancy_of((const void *)decode_setup_kernel<BMAX, true>, 0, sms_setup, per_setup);
         const int gs = sms_setup * per_setup;
-        decode_setup_kernel<BMAX, true><<<need < gs ? need : gs, kDecWarps * 32, 0, st>>>(descs, count, total_strips,
-                                                                                        tables, tfw, tgw);
+        // the setup kernel also writes the first iterate (pixels when it is the only one)
+        decode_setup_kernel<BMAX, true><<<need < gs ? need : gs, kDecWarps * 32, 0, st>>>(
+            descs, count, total_strips, tables, tfw, tgw, iters == 1 ? 3 : 1);
     } else {
         occupancy_of((const void *)decode_setup_kernel<BMAX, false>, 0, sms_setup, per_setup);
         const int gs = sms_setup * per_setup;
         decode_setup_kernel<BMAX, false><<<need < gs ? need : gs, kDecWarps * 32, 0, st>>>(descs, count, total_strips,
-                                                                                         tables, tfw, tgw);
+                                                                                         tables, tfw, tgw, 0);
     }
     stage_mark(st, "decode_setup_kernel");
     cudaError_t e = cudaGetLastError();
@@ -667,9 +681,9 @@ static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, 
         occupancy_of((const void *)decode_d4_iter_kernel<BMAX>, smem_d4, sms_d4, per_d4);
         const int k = tune.ctas_per_sm > 0 && tune.ctas_per_sm < per_d4 ? tune.ctas_per_sm : per_d4;
         const int grid = need < sms_d4 * k ? need : sms_d4 * k;
-        for (int it = 0; it < iters; ++it) {
-            // iteration it >= 1 reads image (it - 1) & 1; the first writes image 0
-            const int kind = (it == 0 ? 1 : 0) | (it == iters - 1 ? 2 : 0);
+        for (int it = 1; it < iters; ++it) {
+            // iteration it >= 1 reads image (it - 1) & 1; the first (in the setup kernel) wrote image 0
+            const int kind = it == iters - 1 ? 2 : 0;
             decode_d4_iter_kernel<BMAX><<<grid, kDecWarps * 32, smem_d4, st>>>(sinfo, tfw, total_strips,
                                                                                (it - 1) & 1, kind);
             stage_mark(st, "decode_d4_iter_kernel");

@@ -24,7 +24,7 @@ __global__ void exh_prep_domains(ExhDesc E) {
         if (d >= E.nd) {
             for (int i = 0; i < kExhK; ++i) E.dfp16[(size_t)d * kExhK + i] = __ushort_as_half(0);
             E.dstat[d] = make_int4(0, 0, 0, 0);
-            E.dscr[d] = make_float2(0.f, __int_as_float(0x7fc00000));  // NaN: never passes the screen
+            E.dscr[d] = make_float4(0.f, __int_as_float(0x7fc00000), __int_as_float(0x7fc00000), 0.f);  // NaN
             continue;
         }
         const int dy = (d / E.ndx) * E.step, dx = (d % E.ndx) * E.step;
@@ -45,7 +45,8 @@ __global__ void exh_prep_domains(ExhDesc E) {
         const long long ncdd = 64LL * sdd - (long long)sd * sd;  // <= 4.3e9: fits an unsigned word
         const float k512 = ncdd > 0 ? 512.f / (float)ncdd : 0.f;
         E.dstat[d] = make_int4(sd, (int)(uint32_t)ncdd, __float_as_int(k512), 1);
-        E.dscr[d] = make_float2(-(float)sd, ncdd > 0 ? 262144.f / (float)ncdd : 0.f);
+        const float sw = ncdd > 0 ? sqrtf(262144.f / (float)ncdd) : 0.f;
+        E.dscr[d] = make_float4(-(float)sd, sw, 130.f * sw, 0.f);
     }
 }
 
@@ -93,7 +94,7 @@ __device__ __forceinline__ void exh_exact(ExhRow &b, int d, int sdr, int sr, int
     const int k = best_contrast((long long)ncdr, (long long)ncdd, s_bits);
     const long long c = contrast_code(k, s_bits);
     const long long g = c * c * (long long)ncdd - 1024LL * c * ncdr;
-    if (g < b.g) {
+    if (exh_better(g, d, b.g, b.d)) {
         b.g = g;
         b.thr = exh_threshold(g);
         b.d = d;
@@ -109,7 +110,7 @@ constexpr int kExhStage = 64;
 __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
     __shared__ __align__(16) uint32_t s_dp[kExhStage][32];
     __shared__ int4 s_ds[kExhStage];
-    __shared__ float2 s_cs[kExhStage];
+    __shared__ float4 s_cs[kExhStage];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = (blockIdx.x * kExhWarps + warp) * 4 + (lane >> 3);
     const int t = lane & 7;
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
         }
         for (int j = threadIdx.x; j < kExhStage; j += blockDim.x) {
             s_ds[j] = (d0 + j < E.nd) ? E.dstat[d0 + j] : make_int4(0, 0, 0, 0);
-            s_cs[j] = (d0 + j < E.nd) ? E.dscr[d0 + j] : make_float2(0.f, 0.f);
+            s_cs[j] = (d0 + j < E.nd) ? E.dscr[d0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();
         const int nj = min(kExhStage, E.nd - d0);
@@ -172,8 +173,9 @@ __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
     }
 }
 
-// Combine the isometry rows of each range and write its record (the flat
-// partition: one phase-1 leaf per range, in raster order).
+// Combine the isometry rows (and domain segments) of each range and write
+// its record (the flat partition: one phase-1 leaf per range, in raster
+// order).  Ties: smaller domain index, then smaller isometry.
 __global__ void exh_finalize(ExhDesc E) {
     const int ko1 = (1 << E.o_bits) - 1;
     const uint32_t magic = (uint32_t)((0x100000000ULL + 2 * ko1 - 1) / (2 * ko1));
@@ -182,13 +184,16 @@ __global__ void exh_finalize(ExhDesc E) {
         long long bg = 0x7fffffffffffffffLL;
         int bd = 0x7fffffff, bt = 0, bk = 0;
         for (int t = 0; t < E.isos; ++t) {
-            const long long g = E.row_g[(size_t)r * 8 + t];
-            const int2 dk = E.row_dk[(size_t)r * 8 + t];
-            if (g < bg || (g == bg && dk.x < bd)) {
-                bg = g;
-                bd = dk.x;
-                bt = t;
-                bk = dk.y;
+            for (int sg = 0; sg < E.nseg; ++sg) {
+                const size_t i = (size_t)sg * E.nr * 8 + (size_t)r * 8 + t;
+                const long long g = E.row_g[i];
+                const int2 dk = E.row_dk[i];
+                if (dk.x >= 0 && exh_better(g, dk.x, bg, bd)) {
+                    bg = g;
+                    bd = dk.x;
+                    bt = t;
+                    bk = dk.y;
+                }
             }
         }
         const int sr = E.rstat[r].x;
@@ -212,7 +217,7 @@ __global__ void exh_finalize(ExhDesc E) {
     }
 }
 
-cudaError_t launch_exh_tc(const ExhDesc &E, uint32_t *err, cudaStream_t st);
+cudaError_t launch_exh_tc(const ExhDesc &E, uint32_t *err, int *nseg, cudaStream_t st);
 
 // engine 0: tensor cores, 1: CUDA cores.  The stream's info block is
 // cleared first; a device timeout of the tensor path leaves its error bit.
@@ -225,16 +230,18 @@ cudaError_t launch_exhaustive(const ExhDesc &E, int engine, cudaStream_t st) {
     stage_mark(st, "exh_prep_ranges");
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    ExhDesc F = E;
     if (engine == 1) {
         const int ranges_per_cta = kExhWarps * 4;
         exh_cuda_kernel<<<(E.nr + ranges_per_cta - 1) / ranges_per_cta, kExhWarps * 32, 0, st>>>(E);
         stage_mark(st, "exh_cuda_kernel");
         e = cudaGetLastError();
+        F.nseg = 1;
     } else {
-        e = launch_exh_tc(E, E.info + FIC_INFO_ERROR, st);
+        e = launch_exh_tc(E, E.info + FIC_INFO_ERROR, &F.nseg, st);
     }
     if (e != cudaSuccess) return e;
-    exh_finalize<<<(E.nr + 255) / 256, 256, 0, st>>>(E);
+    exh_finalize<<<(E.nr + 255) / 256, 256, 0, st>>>(F);
     stage_mark(st, "exh_finalize");
     return cudaGetLastError();
 }

@@ -11,6 +11,7 @@ namespace fic {
 constexpr int kExhB = 8;    // range side
 constexpr int kExhK = 64;   // decimated values per block
 constexpr int kExhNTile = 128;  // domains per tile (the tensor path's N)
+constexpr int kExhMaxSeg = 8;   // domain segments (CTAs sharing one row tile) at most
 
 // One image of an exhaustive-search launch; all arrays live in the workspace.
 struct ExhDesc {
@@ -21,14 +22,16 @@ struct ExhDesc {
     int32_t nd_pad;           // nd rounded up to kExhNTile
     int32_t step, isos;
     int32_t s_bits, o_bits;
+    int32_t nseg;             // domain segments whose per-row bests exh_finalize merges
     uint32_t *dpairs;         // [nd][32]   packed (d4, d4) pairs for dp2a
     __half *dfp16;            // [nd_pad][64] decimated domains, K-major, fp16
     int4 *dstat;              // [nd_pad]   Sd, nCdd (u32), 512/nCdd (float bits), valid
-    float2 *dscr;             // [nd_pad]   screening constants: -Sd, 512^2/nCdd (NaN: padding)
+    float4 *dscr;             // [nd_pad]   screening constants: -Sd, sqrt(512^2/nCdd), 130 * that, 0
+                              //            (NaN: padding)
     __half *afp16;            // [nr * 8][64] range rows permuted per isometry, fp16
     int4 *rstat;              // [nr]       Sr, Srr
-    long long *row_g;         // [nr * 8]   best s-part error of the (range, isometry) row
-    int2 *row_dk;             // [nr * 8]   its domain index and contrast code
+    long long *row_g;         // [nseg][nr * 8] best s-part error of the (range, isometry) row
+    int2 *row_dk;             // [nseg][nr * 8] its domain index and contrast code
     fic_record *rec;
     uint32_t *tile_off;
     uint32_t *split;
@@ -56,18 +59,26 @@ __host__ __device__ inline void exh_iso_src(int t, int B, int u, int v, int &su,
 // Screening of one candidate against the row's best so far.  Over real c,
 // c^2 nCdd - 1024 c nCdr is smallest at c* = 512 nCdr / nCdd, where it is
 // -L with L = 512^2 nCdr^2 / nCdd; the grid's best code can only do worse,
-// so a candidate with -L >= the row's best exact error g cannot win (ties
-// keep the earlier domain).  The screen computes an upper bound of L in
-// float: nCdr = 64 Sdr - Sd Sr is formed with at most 64 of absolute
-// rounding error (|nCdr| < 2^31, Sdr exact below 2^24), widened by 130, and
-// the product's relative error (< 1e-6) is covered by the row threshold
-// thr(g) = -g (1 - 1e-5) - 1: a candidate is evaluated exactly (int64) only
-// when its bound reaches thr.  Padding domains carry NaN and never pass.
-__device__ __forceinline__ float exh_screen(float sdr_f, float sr_f, float2 cs) {
-    const float u = fabsf(fmaf(sdr_f, 64.f, cs.x * sr_f)) + 130.f;
-    return u * u * cs.y;
+// so a candidate with L < -g (g the row's best exact error) cannot win.  The
+// screen compares square roots: v = (|nCdr~| + 130) sqrt(512^2 / nCdd) with
+// nCdr~ = 64 Sdr - Sd Sr formed in float (at most 64 of absolute rounding
+// error: |nCdr| < 2^31, Sdr exact below 2^24), so sqrt(L) <= v (1 + 3e-7);
+// the row threshold sqrt(-g (1 - 1e-5) - 1) (1 - 1e-6) (or -1 while g >= 0)
+// covers those relative errors, and a candidate is evaluated exactly (int64)
+// only when v reaches it.  Padding domains carry NaN and never pass.
+__device__ __forceinline__ float exh_screen(float sdr_f, float sr_f, float4 cs) {
+    const float a = fmaf(sdr_f, 64.f, cs.x * sr_f);
+    return fmaf(fabsf(a), cs.y, cs.z);
 }
 
-__device__ __forceinline__ float exh_threshold(long long g) { return (float)(-g) * (1.f - 1e-5f) - 1.f; }
+__device__ __forceinline__ float exh_threshold(long long g) {
+    const float t = (float)(-g) * (1.f - 1e-5f) - 1.f;
+    return t > 0.f ? sqrtf(t) * (1.f - 1e-6f) : -1.f;
+}
+
+// (g, d) lexicographic improvement: the smaller domain index wins ties.
+__device__ __forceinline__ bool exh_better(long long g, int d, long long bg, int bd) {
+    return g < bg || (g == bg && (unsigned)d < (unsigned)bd);
+}
 
 }  // namespace fic

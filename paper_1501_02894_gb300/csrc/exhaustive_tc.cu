@@ -108,13 +108,28 @@ __device__ __noinline__ TcRow tc_exact(TcRow b, int d, float acc, int sr, int4 d
     const int k = best_contrast((long long)ncdr, (long long)ncdd, s_bits);
     const long long c = contrast_code(k, s_bits);
     const long long g = c * c * (long long)ncdd - 1024LL * c * ncdr;
-    if (g < b.g) {
+    if (exh_better(g, d, b.g, b.d)) {
         b.g = g;
         b.thr = exh_threshold(g);
         b.d = d;
         b.k = k;
     }
     return b;
+}
+
+// Named barrier of the epilogue warps that also ORs a flag over them, so
+// that leaving the tile loop is a uniform decision.
+__device__ __forceinline__ bool epi_bar_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.cta.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(kTcEpiWarps * 32)
+        : "memory");
+    return r != 0;
 }
 
 __global__ void __launch_bounds__(kTcThreads, 2)
@@ -129,10 +144,14 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     __shared__ TcRow s_half[kTcRows];  // the second epilogue warp of each lane quarter hands its state over
+    __shared__ float4 s_cst[2][kTcCols];  // screening constants of the tiles in the two accumulators
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row0 = blockIdx.x * kTcRows;
-    const int ntiles = E.nd_pad / kTcCols;
+    // this CTA's domain segment: tiles [t0, t0 + cnt)
+    const int ntiles_all = E.nd_pad / kTcCols;
+    const int t0 = (int)(((long long)blockIdx.y * ntiles_all) / gridDim.y);
+    const int ntiles = (int)(((long long)(blockIdx.y + 1) * ntiles_all) / gridDim.y) - t0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTcStages; ++s) {
@@ -179,7 +198,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 asm volatile(
                     "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
                     "%3}], [%4];" ::"r"(smem_u32(sB + s * kTileBytes)),
-                    "l"(reinterpret_cast<uint64_t>(&mapB)), "r"(0), "r"(n * kTcCols), "r"(smem_u32(&bar_full[s]))
+                    "l"(reinterpret_cast<uint64_t>(&mapB)), "r"(0), "r"((t0 + n) * kTcCols), "r"(smem_u32(&bar_full[s]))
                     : "memory");
             }
             // copies still in flight must land before the CTA may leave
@@ -227,14 +246,29 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         const float srf = (float)sr;
         TcRow best;
         best.g = 0x7fffffffffffffffLL;
-        best.thr = live ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);  // dead rows never pass
+        best.thr = live ? -1.f : __int_as_float(0x7f800000);  // everything passes / dead rows never pass
         best.d = -1;
         best.k = 0;
+        // screening constants of each tile: staged in shared memory by the
+        // epilogue threads (tile n+1's load is in flight while tile n is
+        // screened); one named barrier per tile, which also makes leaving
+        // the loop after a timeout a uniform decision
+        const int et = threadIdx.x - 64;
+        float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (et < kTcCols && ntiles > 0) pre = __ldg(E.dscr + (size_t)t0 * kTcCols + et);
+        bool bad = false;
         for (int n = 0; n < ntiles; ++n) {
             const int acc = n & 1;
-            if (!mbar_wait(&bar_acc_full[acc], (uint32_t)((n >> 1) & 1), kMbarLimit) || s_abort) {
+            if (et < kTcCols) s_cst[acc][et] = pre;
+            if (epi_bar_or(bad || s_abort)) {
                 s_abort = 1;
                 break;
+            }
+            if (et < kTcCols && n + 1 < ntiles) pre = __ldg(E.dscr + (size_t)(t0 + n + 1) * kTcCols + et);
+            if (!mbar_wait(&bar_acc_full[acc], (uint32_t)((n >> 1) & 1), kMbarLimit)) {
+                bad = true;
+                mbar_arrive(&bar_acc_empty[acc]);
+                continue;
             }
             tc_fence_after();
 #pragma unroll 1
@@ -242,28 +276,27 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 const int col = h * (kTcCols / 2) + c0;
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kTcCols + col), v);
-                const int dbase = n * kTcCols + col;
-                const float4 *cs4 = reinterpret_cast<const float4 *>(E.dscr + dbase);
+                const int dbase = (t0 + n) * kTcCols + col;
+                const float4 *cs = &s_cst[acc][col];
 #pragma unroll
-                for (int j = 0; j < 32; j += 2) {
-                    const float4 c2 = __ldg(cs4 + j / 2);
-                    if (exh_screen(v[j], srf, make_float2(c2.x, c2.y)) >= best.thr)
+                for (int j = 0; j < 32; ++j) {
+                    if (exh_screen(v[j], srf, cs[j]) >= best.thr)
                         best = tc_exact(best, dbase + j, v[j], sr, __ldg(E.dstat + dbase + j), E.s_bits);
-                    if (exh_screen(v[j + 1], srf, make_float2(c2.z, c2.w)) >= best.thr)
-                        best = tc_exact(best, dbase + j + 1, v[j + 1], sr, __ldg(E.dstat + dbase + j + 1), E.s_bits);
                 }
             }
             tc_fence_before();
             mbar_arrive(&bar_acc_empty[acc]);
         }
+        if (bad) s_abort = 1;
         // merge the two column halves of each row (the lower domain half wins ties)
         if (h == 1) s_half[rloc] = best;
         asm volatile("bar.sync 1, %0;" ::"r"(kTcEpiWarps * 32));
         if (h == 0 && live) {
             const TcRow o = s_half[rloc];
-            if (o.g < best.g || (o.g == best.g && (unsigned)o.d < (unsigned)best.d)) best = o;
-            E.row_g[(size_t)r * 8 + t] = best.g;
-            E.row_dk[(size_t)r * 8 + t] = make_int2(best.d, best.k);
+            if (exh_better(o.g, o.d, best.g, best.d)) best = o;
+            const size_t i = (size_t)blockIdx.y * E.nr * 8 + (size_t)r * 8 + t;
+            E.row_g[i] = best.g;
+            E.row_dk[i] = make_int2(best.d, best.k);
         }
     }
     tc_fence_before();
@@ -300,7 +333,10 @@ static int make_f16_map(CUtensorMap *m, const void *base, int rows) {
 
 size_t exh_tc_smem_bytes() { return (size_t)(1 + kTcStages) * kTileBytes + 1024; }
 
-cudaError_t launch_exh_tc(const ExhDesc &E, uint32_t *err, cudaStream_t st) {
+// The domain axis is split into up to kExhMaxSeg segments (one CTA per row
+// tile and segment) so that small images still give every SM several CTAs;
+// *nseg receives the count for exh_finalize.
+cudaError_t launch_exh_tc(const ExhDesc &E, uint32_t *err, int *nseg, cudaStream_t st) {
     static bool attr = false;
     const size_t smem = exh_tc_smem_bytes();
     if (!attr) {
@@ -312,7 +348,20 @@ cudaError_t launch_exh_tc(const ExhDesc &E, uint32_t *err, cudaStream_t st) {
     // rows past the end of A read as zeros (TMA out-of-bounds fill)
     if (make_f16_map(&ma, E.afp16, E.nr * 8) || make_f16_map(&mb, E.dfp16, E.nd_pad)) return cudaErrorInvalidValue;
     const int ctas = (E.nr * 8 + kTcRows - 1) / kTcRows;
-    exh_tc_kernel<<<ctas, kTcThreads, smem, st>>>(E, ma, mb, err);
+    static int slots = 0;
+    if (slots == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, exh_tc_kernel, kTcThreads, smem);
+        slots = sms * (per > 0 ? per : 1);
+    }
+    const int ntiles = E.nd_pad / kTcCols;
+    int seg = (4 * slots + ctas - 1) / ctas;  // about four waves of CTAs
+    seg = seg < 1 ? 1 : (seg > kExhMaxSeg ? kExhMaxSeg : seg);
+    seg = seg > ntiles ? ntiles : seg;
+    *nseg = seg;
+    exh_tc_kernel<<<dim3(ctas, seg), kTcThreads, smem, st>>>(E, ma, mb, err);
     stage_mark(st, "exh_tc_kernel");
     return cudaGetLastError();
 }

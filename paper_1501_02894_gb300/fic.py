@@ -171,19 +171,33 @@ def _ptr(t: torch.Tensor):
     return ctypes.c_void_p(t.data_ptr())
 
 
-class Stream:
-    """A transform stream whose device buffers are owned by torch tensors."""
+def stream_sizes(width: int, height: int, p: Params):
+    """(top-level blocks, record capacity) of a stream."""
+    ntop, cap = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().fic_stream_sizes(width, height, ctypes.byref(p), ctypes.byref(ntop), ctypes.byref(cap)),
+           "fic_stream_sizes")
+    return ntop.value, cap.value
 
-    def __init__(self, width: int, height: int, p: Params, device="cuda"):
-        ntop, cap = ctypes.c_int32(), ctypes.c_int32()
-        _check(lib().fic_stream_sizes(width, height, ctypes.byref(p), ctypes.byref(ntop), ctypes.byref(cap)),
-               "fic_stream_sizes")
+
+class Stream:
+    """A transform stream whose device buffers are owned by torch tensors.
+
+    `records` / `info` may be given (uint8 views of capacity * 16 bytes,
+    16-byte aligned, and int32 views of 16 words), e.g. slices of one arena
+    so that a batch's streams come back to the host in one copy."""
+
+    def __init__(self, width: int, height: int, p: Params, device="cuda", records=None, info=None):
+        ntop, cap = stream_sizes(width, height, p)
         self.width, self.height, self.params = int(width), int(height), p
-        self.ntop, self.capacity = ntop.value, cap.value
-        self.records = torch.empty(self.capacity * 16, dtype=torch.uint8, device=device)
+        self.ntop, self.capacity = ntop, cap
+        if records is not None and (records.numel() < cap * 16 or records.data_ptr() % 16):
+            raise ValueError("records view too small or not 16-byte aligned")
+        if info is not None and info.numel() < INFO_WORDS:
+            raise ValueError("info view too small")
+        self.records = records if records is not None else torch.empty(cap * 16, dtype=torch.uint8, device=device)
         self.tile_offsets = torch.empty(self.ntop + 1, dtype=torch.int32, device=device)
         self.split = torch.empty(self.ntop, dtype=torch.int32, device=device)
-        self.info = torch.zeros(INFO_WORDS, dtype=torch.int32, device=device)
+        self.info = info if info is not None else torch.zeros(INFO_WORDS, dtype=torch.int32, device=device)
         self.c = StreamC()
         self.c.width, self.c.height, self.c.params = self.width, self.height, p
         self.c.ntop, self.c.capacity = self.ntop, self.capacity
@@ -338,7 +352,7 @@ class _Tunable:
         rows = [tuple(trace[5 * i: 5 * i + 5]) for i in range(n.value)]
         keys = ("enc_warps", "enc_ctas_per_sm", "enc_dynamic", "dec_ctas_per_sm")
         return {"best": best.as_dict(), "best_ms": ms.value,
-                "trials": [dict({k: int(r[j]) for j, k in enumerate(keys)}, ms=round(r[4], 5)) for r in rows]}
+                "trials": [dict({k: int(r[j]) for j, k in enumerate(keys)}, ms=float(r[4])) for r in rows]}
 
 
 class EncodePlan(_Tunable):

@@ -217,3 +217,29 @@ def test_local_radius_zero_is_nosearch(fic, orc):
     b = fic.fic_encode(img, fic.params("nosearch", 32, 4, 6.0)).to_host()
     assert np.array_equal(a["records"].view(np.uint8), b["records"].view(np.uint8))
     assert np.array_equal(a["split"], b["split"])
+
+
+def test_decode_paths_agree(fic, orc):
+    """Centred streams decode on 2x2-sum images; a batch that holds a
+    local-search stream (or a stream too narrow for the window box) takes the
+    pixel path.  Both equal the oracle."""
+    a = synth.gaussian_scene(256, 61)
+    b = synth.gaussian_scene(256, 62)
+    pa, opa = _pair(fic, orc, "mns", 32, 4, 8.0)
+    pb, opb = _pair(fic, orc, "local", 32, 4, 8.0)
+    sa = fic.fic_encode(torch.from_numpy(a).cuda(), pa)
+    sb = fic.fic_encode(torch.from_numpy(b).cuda(), pb)
+    want_a = orc.decode(orc.encode(a, opa)[0], 256, 256, opa, 7)
+    want_b = orc.decode(orc.encode(b, opb)[0], 256, 256, opb, 7)
+    only_centred = fic.fic_decode_batch([sa], 7)[0].cpu().numpy()
+    mixed = [t.cpu().numpy() for t in fic.fic_decode_batch([sa, sb], 7)]
+    assert np.array_equal(only_centred, want_a)
+    assert np.array_equal(mixed[0], want_a) and np.array_equal(mixed[1], want_b)
+    for iters in (1, 2, 3):  # first-and-last, first then last, one middle iteration
+        got = fic.fic_decode_batch([sa], iters)[0].cpu().numpy()
+        assert np.array_equal(got, orc.decode(orc.encode(a, opa)[0], 256, 256, opa, iters))
+    # bmax 16 on a 64-pixel-wide image: narrower than the 2x2-sum window box
+    c = synth.gaussian_scene(64, 63, H=128)
+    pc, opc = _pair(fic, orc, "mns", 16, 4, 6.0)
+    sc = fic.fic_encode(torch.from_numpy(c).cuda(), pc)
+    assert np.array_equal(fic.fic_decode(sc, 5).cpu().numpy(), orc.decode(orc.encode(c, opc)[0], 64, 128, opc, 5))
