@@ -665,6 +665,23 @@ def run_exhaustive(args):
     clocks = sampler.stop()
     same = all(np.array_equal(a["records"].view(np.uint8), b["records"].view(np.uint8))
                for a, b in zip(outs["tcgen05"], outs["cuda_cores"]))
+    # Section 2 (Figs. 2, 3): distribution of x_d - x_r, y_d - y_r of the
+    # exhaustive search, against two uniform random points (p(u) = 1 - |u|)
+    offset_stats = {}
+    for (name, im, d, plan) in plans:
+        H, W = im.shape
+        with torch.cuda.stream(stream):
+            hx, hy = fic.offset_histogram(plan.outs[0], stream)
+        stream.synchronize()
+        st = {}
+        for axis, h, n in (("x", hx, W), ("y", hy, H)):
+            c = h.cpu().numpy().astype(np.float64)
+            u = (np.arange(2 * n) - n) / n
+            tot = c.sum()
+            st[f"mean_abs_d{axis}_over_side"] = round(float((c * np.abs(u)).sum() / tot), 4)
+            st[f"frac_abs_d{axis}_le_side_over_8"] = round(float(c[np.abs(u) <= 0.125].sum() / tot), 4)
+        st["uniform_model"] = {"mean_abs": round(1 / 3, 4), "frac_le_1_8": round(2 * 0.125 - 0.125 ** 2, 4)}
+        offset_stats[name] = st
     tot_fits = sum(v["fits"] for v in res["tcgen05"].values())
     tot_ms = sum(v["ms"] for v in res["tcgen05"].values())
     value = world * tot_fits / (tot_ms * 1e-3)
@@ -683,7 +700,7 @@ def run_exhaustive(args):
         "dtype": "f16 operands, f32 accumulate (exact integers), int64 decisions", "data": "synthetic",
         "config": {"workload": "cfg3: 512x512 seed 1 + 1024x1024 seed 9, 8x8 ranges, domain step 4, 8 isometries",
                    "l2": "flushed (256 MiB write) before every step", "parallelism": f"replicas x{world}"},
-        "engines": res, "engines_identical_output": bool(same),
+        "engines": res, "engines_identical_output": bool(same), "offset_stats": offset_stats,
         "cuda_core_over_tensor_time": round(sum(v["ms"] for v in res["cuda_cores"].values()) / tot_ms, 3),
         "roofline": roofline, "gpu_launches": 4 * len(imgs) * max(1, min(args.steps, 20)), "clocks": clocks,
         "e2e": None,

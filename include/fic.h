@@ -274,6 +274,16 @@ FIC_API int fic_plan_autotune(fic_plan *plan, int iters, int reps, void *stream,
 FIC_API int fic_encode_noalloc(const uint8_t *d_img, int width, int height, const fic_params *p,
                                fic_stream *out, void *stream);
 
+/* ---- Position statistics (Section 2, Figs. 2 and 3) ----
+ * Histograms of x_d - x_r and y_d - y_r over the stream's records: the
+ * offset between each range block and its domain block.  hx has 2*width
+ * bins (bin (x_d - x_r) + width), hy 2*height bins (bin (y_d - y_r) +
+ * height), uint32 device arrays; counts are ADDED (zero them first).  The
+ * record count is read on the device from the stream's info block.  For
+ * no-search / MNS streams the domain is the centred one (phase-2 records:
+ * the block's).  Asynchronous on `stream`; FIC_EBADPARAM for null pointers. */
+FIC_API int fic_offset_histogram(const fic_stream *st, uint32_t *d_hx, uint32_t *d_hy, void *stream);
+
 /* ---- Serving: continuous batching of encode and decode requests ----
  * The paper has a single encoder; the server runs many of them at once on
  * one GPU.  It owns one device allocation of `hbm_budget_bytes` (sub-

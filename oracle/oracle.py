@@ -249,6 +249,15 @@ def check(W, H, p: OrcParams) -> int:
     return int(lib().orc_check(W, H, ctypes.byref(p)))
 
 
+def offset_histogram(leaves: np.ndarray, W: int, H: int):
+    """Counts of x_d - x_r (bin + W, 2W bins) and y_d - y_r (bin + H, 2H
+    bins) over the leaves: the distributions Section 2 (Figs. 2, 3) shows
+    for an exhaustive search."""
+    ox = leaves["dx"].astype(np.int64) - leaves["x"].astype(np.int64) + W
+    oy = leaves["dy"].astype(np.int64) - leaves["y"].astype(np.int64) + H
+    return (np.bincount(ox, minlength=2 * W).astype(np.int64), np.bincount(oy, minlength=2 * H).astype(np.int64))
+
+
 def psnr(a: np.ndarray, b: np.ndarray) -> float:
     """Peak signal-to-noise ratio with peak 255 (Section 4)."""
     d = a.astype(np.float64) - b.astype(np.float64)

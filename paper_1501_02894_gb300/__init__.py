@@ -21,6 +21,7 @@ from .fic import (  # noqa: F401
     fic_encode_batch,
     fic_encode_noalloc,
     lib,
+    offset_histogram,
     params,
     stream_sizes,
     validate,

@@ -578,10 +578,15 @@ __global__ void __launch_bounds__(kDecWarps * 32, 4)
             first_d4<BMAX>(strip_d4_use(sinfo + g, dst), tfw[(size_t)g * 32 + lane], last, lane);
         return;
     }
-    auto issue = [&](int gi, int b) {
+    // lane 0: box coordinates of a strip's window (map of the image read,
+    // origin); those of the strip after next are loaded one strip ahead so
+    // that issuing a copy never waits on a global load
+    auto coords = [&](int gi, const TmaMap *&map, uint32_t &wxy) {
         const StripD4 *sn = sinfo + gi;
-        const TmaMap *map = src ? sn->map[1] : sn->map[0];
-        const uint32_t wxy = sn->wxy;
+        map = src ? sn->map[1] : sn->map[0];
+        wxy = sn->wxy;
+    };
+    auto issue = [&](int b, const TmaMap *map, uint32_t wxy) {
         uint64_t *bar = &s_bar[warp][b];
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar, WB);
@@ -589,12 +594,23 @@ __global__ void __launch_bounds__(kDecWarps * 32, 4)
     };
     uint32_t par0 = 0, par1 = 0;
     int b = 0;
-    if (lane == 0 && g < total_strips) issue(g, 0);
+    const TmaMap *nmap = nullptr;
+    uint32_t nwxy = 0;
+    if (lane == 0 && g < total_strips) {
+        const TmaMap *m0;
+        uint32_t w0;
+        coords(g, m0, w0);
+        issue(0, m0, w0);
+        if (g + gstep < total_strips) coords(g + gstep, nmap, nwxy);
+    }
     for (; g < total_strips; g += gstep) {
         const int gn = g + gstep;
         const StripD4Use si = strip_d4_use(sinfo + g, dst);
         const uint4 tf = tfw[(size_t)g * 32 + lane];
-        if (lane == 0 && gn < total_strips) issue(gn, b ^ 1);
+        if (lane == 0 && gn < total_strips) {
+            issue(b ^ 1, nmap, nwxy);
+            if (gn + gstep < total_strips) coords(gn + gstep, nmap, nwxy);
+        }
         const uint32_t par = b ? par1 : par0;
         const bool arrived = mbar_wait(&s_bar[warp][b], par, kMbarLimit);
         if (!__all_sync(FULL, arrived)) {

@@ -151,6 +151,7 @@ def lib():
         L.fic_wait.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, P(JobResult)]
         L.fic_server_get_stats.argtypes = [vp, P(ServerStats)]
         L.fic_server_destroy.argtypes = [vp]
+        L.fic_offset_histogram.argtypes = [P(StreamC), vp, vp, vp]
         L.fic_strerror.argtypes = [ctypes.c_int]
         L.fic_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -424,6 +425,16 @@ class DecodePlan(_Tunable):
         if h is not None and h.value and _lib is not None:
             _lib.fic_plan_destroy(h)
             self.handle = None
+
+
+def offset_histogram(st: Stream, stream=None):
+    """Histograms (torch int32 on the stream's device) of x_d - x_r (2W bins,
+    bin offset + W) and y_d - y_r (2H bins) over the stream's records."""
+    hx = torch.zeros(2 * st.width, dtype=torch.int32, device=st.records.device)
+    hy = torch.zeros(2 * st.height, dtype=torch.int32, device=st.records.device)
+    _check(lib().fic_offset_histogram(ctypes.byref(st.c), _ptr(hx), _ptr(hy), _stream_handle(stream)),
+           "fic_offset_histogram")
+    return hx, hy
 
 
 def validate(width: int, height: int, p: Params) -> int:
