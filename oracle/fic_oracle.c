@@ -644,3 +644,182 @@ int orc_count_candidates(const uint8_t *img, int W, int H, const orc_params *p, 
     orc_fit f;
     return orc_search(img, W, H, p, x, y, B, &f);
 }
+
+/* ------------------------------------------------------------------ */
+/* Bitstream: the stored parameters of Section 3.3 with the level-id rule
+ * of Technique 2 (Section 3.4).
+ *
+ * Layout (a reading: the paper gives the fields and their widths, not an
+ * order): bits are appended least-significant first into 32-bit words (bit
+ * i of the stream is bit i % 32 of word i / 32).  Leaves follow the
+ * canonical order; per leaf:
+ *   level - 1          ceil(log2 L) bits; with Technique 2 a last-level
+ *                      leaf that is not the first (top-left) of its group
+ *                      of four has none (its level is implied)
+ *   phase              1 bit (0: phase 1, 1: phase 2) at levels < L when
+ *                      MNS phase 2 is on
+ *   phase 1            k (s_bits), q (o_bits), then the domain: local
+ *                      search the offset index ((oy + R)/step * per +
+ *                      (ox + R)/step, per = 2R/step + 1) in ceil(log2 per^2)
+ *                      bits; exhaustive search the domain's raster index on
+ *                      the step grid (ceil(log2 count) bits) and the
+ *                      isometry (ceil(log2 isometries) bits)
+ *   phase 2            q_i (o_bits), the three differences O_k - O_i (M
+ *                      bits each, two's complement, M of Section 3.3), the
+ *                      four contrast choices (4 bits, bit b = sub-block b)
+ * Positions, block sides and centred domains are implied by the order.
+ * tile_bits[t] is the first bit of top-level block t (tile_bits[ntop] = the
+ * total): an index that lets a reader start at any block. */
+
+static void put_bits(uint32_t *w, int64_t *pos, uint32_t v, int nb) {
+    for (int i = 0; i < nb; i++, (*pos)++)
+        if ((v >> i) & 1u) w[*pos >> 5] |= 1u << (*pos & 31);
+}
+
+static uint32_t get_bits(const uint32_t *w, int64_t *pos, int nb) {
+    uint32_t v = 0;
+    for (int i = 0; i < nb; i++, (*pos)++) v |= ((w[*pos >> 5] >> (*pos & 31)) & 1u) << i;
+    return v;
+}
+
+typedef struct {
+    int L, lbits, phase_bit_on, extra_kind;
+    int per, rstep, local_bits;   /* local search */
+    int ndx, dom_bits, iso_bits;  /* exhaustive search */
+} bit_layout;
+
+static void layout_of(int W, int H, const orc_params *p, bit_layout *b) {
+    b->L = nlevels(p);
+    b->lbits = ilog2_ceil(b->L);
+    b->phase_bit_on = p->mode == ORC_MNS && p->phase2;
+    b->extra_kind = p->mode == ORC_LOCAL ? 1 : (p->mode == ORC_EXHAUSTIVE ? 2 : 0);
+    b->rstep = p->local_step > 0 ? p->local_radius / p->local_step : 0;
+    b->per = 2 * b->rstep + 1;
+    b->local_bits = ilog2_ceil((long)b->per * b->per);
+    b->ndx = p->dom_step > 0 ? (W - 2 * p->bmin) / p->dom_step + 1 : 0;
+    b->dom_bits = b->extra_kind == 2 ? ilog2_ceil((long)orc_count_domains(W, H, p->bmin, p->dom_step)) : 0;
+    b->iso_bits = b->extra_kind == 2 ? ilog2_ceil(p->isometries) : 0;
+}
+
+/* Bits of the stream of `leaves` (canonical order).  words[0..nwords) must
+ * be zero; returns ORC_ECAPACITY when they are too few. */
+int orc_serialize(const orc_leaf *leaves, int nleaves, int W, int H, const orc_params *p, int technique2,
+                  uint32_t *words, int64_t nwords, uint64_t *tile_bits, int64_t *nbits) {
+    int rc = orc_check(W, H, p);
+    if (rc) return rc;
+    bit_layout b;
+    layout_of(W, H, p, &b);
+    int tw = W / p->bmax, ntop = tw * (H / p->bmax);
+    int64_t pos = 0;
+    int t_next = 0;
+    for (int i = 0; i < nleaves; i++) {
+        const orc_leaf *lf = &leaves[i];
+        int t = (lf->y / p->bmax) * tw + lf->x / p->bmax;
+        while (t_next <= t) tile_bits[t_next++] = (uint64_t)pos;
+        int B = p->bmax >> (lf->level - 1);
+        /* worst case of one leaf: 8 + 1 + 8 + 3 * 7 + 4 + 32 bits */
+        if ((pos + 80) / 32 + 1 > nwords) return ORC_ECAPACITY;
+        int first = ((lf->x / B) % 2 == 0) && ((lf->y / B) % 2 == 0);
+        if (!(technique2 && b.L > 1 && lf->level == b.L && !first)) put_bits(words, &pos, lf->level - 1u, b.lbits);
+        if (b.phase_bit_on && lf->level < b.L) put_bits(words, &pos, lf->phase == 2 ? 1u : 0u, 1);
+        if (lf->phase == 1) {
+            put_bits(words, &pos, lf->k, p->s_bits);
+            put_bits(words, &pos, lf->q, p->o_bits);
+            if (b.extra_kind == 1) {
+                int ox = lf->dx - orc_centred(lf->x, B, W), oy = lf->dy - orc_centred(lf->y, B, H);
+                int idx = (oy / p->local_step + b.rstep) * b.per + (ox / p->local_step + b.rstep);
+                put_bits(words, &pos, (uint32_t)idx, b.local_bits);
+            } else if (b.extra_kind == 2) {
+                int idx = (lf->dy / p->dom_step) * b.ndx + lf->dx / p->dom_step;
+                put_bits(words, &pos, (uint32_t)idx, b.dom_bits);
+                put_bits(words, &pos, lf->iso, b.iso_bits);
+            }
+        } else {
+            int M = orc_phase2_mbits(lf->level);
+            put_bits(words, &pos, lf->q, p->o_bits);
+            for (int k = 0; k < 3; k++) put_bits(words, &pos, (uint32_t)lf->d[k] & ((1u << M) - 1u), M);
+            put_bits(words, &pos, lf->k, 4);
+        }
+    }
+    while (t_next <= ntop) tile_bits[t_next++] = (uint64_t)pos;
+    *nbits = pos;
+    return ORC_OK;
+}
+
+/* Read a stream back: leaves in canonical order with every record field
+ * (positions from the order, centred domains recomputed), split masks, the
+ * tile index.  ORC_EBADPARAM for a stream that does not tile the image. */
+int orc_parse(const uint32_t *words, int64_t nbits, int W, int H, const orc_params *p, int technique2,
+              orc_leaf *out, int cap, uint32_t *split, uint64_t *tile_bits, int *nleaves) {
+    int rc = orc_check(W, H, p);
+    if (rc) return rc;
+    bit_layout b;
+    layout_of(W, H, p, &b);
+    int tw = W / p->bmax, th = H / p->bmax;
+    int cells = p->bmax / p->bmin;
+    int64_t pos = 0;
+    int n = 0;
+    for (int t = 0; t < tw * th; t++) {
+        tile_bits[t] = (uint64_t)pos;
+        split[t] = 0;
+        int tx = (t % tw) * p->bmax, ty = (t / tw) * p->bmax;
+        int c = 0;
+        while (c < cells * cells) {
+            int cx = 0, cy = 0;
+            for (int k = 0; k < 8; k++) {
+                cx |= ((c >> (2 * k)) & 1) << k;
+                cy |= ((c >> (2 * k + 1)) & 1) << k;
+            }
+            int level;
+            if (technique2 && b.L > 1 && (c & 3) != 0) level = b.L;
+            else level = (int)get_bits(words, &pos, b.lbits) + 1;
+            if (level < 1 || level > b.L) return ORC_EBADPARAM;
+            int B = p->bmax >> (level - 1);
+            int span = (B / p->bmin) * (B / p->bmin);
+            if (c % span != 0 || n >= cap || pos > nbits) return ORC_EBADPARAM;
+            orc_leaf lf;
+            memset(&lf, 0, sizeof(lf));
+            lf.x = (uint16_t)(tx + cx * p->bmin);
+            lf.y = (uint16_t)(ty + cy * p->bmin);
+            lf.level = (uint8_t)level;
+            lf.dx = (uint16_t)orc_centred(lf.x, B, W);
+            lf.dy = (uint16_t)orc_centred(lf.y, B, H);
+            int phase = 1;
+            if (b.phase_bit_on && level < b.L) phase = get_bits(words, &pos, 1) ? 2 : 1;
+            lf.phase = (uint8_t)phase;
+            if (phase == 1) {
+                lf.k = (uint8_t)get_bits(words, &pos, p->s_bits);
+                lf.q = (uint8_t)get_bits(words, &pos, p->o_bits);
+                if (b.extra_kind == 1) {
+                    int idx = (int)get_bits(words, &pos, b.local_bits);
+                    if (idx >= b.per * b.per) return ORC_EBADPARAM;
+                    lf.dx = (uint16_t)(lf.dx + (idx % b.per - b.rstep) * p->local_step);
+                    lf.dy = (uint16_t)(lf.dy + (idx / b.per - b.rstep) * p->local_step);
+                } else if (b.extra_kind == 2) {
+                    int idx = (int)get_bits(words, &pos, b.dom_bits);
+                    lf.dx = (uint16_t)((idx % b.ndx) * p->dom_step);
+                    lf.dy = (uint16_t)((idx / b.ndx) * p->dom_step);
+                    lf.iso = (uint8_t)get_bits(words, &pos, b.iso_bits);
+                }
+            } else {
+                int M = orc_phase2_mbits(level);
+                lf.q = (uint8_t)get_bits(words, &pos, p->o_bits);
+                for (int k = 0; k < 3; k++) {
+                    int v = (int)get_bits(words, &pos, M);
+                    if (v >= (1 << (M - 1))) v -= 1 << M;  /* two's complement */
+                    lf.d[k] = (int8_t)v;
+                }
+                lf.k = (uint8_t)get_bits(words, &pos, 4);
+            }
+            if (pos > nbits) return ORC_EBADPARAM;
+            for (int a = 1; a < level; a++)
+                split[t] |= 1u << (((1u << (2 * (a - 1))) - 1) / 3 + (uint32_t)(c >> (2 * (b.L - a))));
+            out[n++] = lf;
+            c += span;
+        }
+    }
+    tile_bits[tw * th] = (uint64_t)pos;
+    if (pos != nbits) return ORC_EBADPARAM;
+    *nleaves = n;
+    return ORC_OK;
+}

@@ -86,6 +86,13 @@ def lib():
         L.orc_bits.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                P(OrcParams), ctypes.c_int]
         L.orc_bits.restype = ctypes.c_int64
+        vp = ctypes.c_void_p
+        L.orc_serialize.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(OrcParams), ctypes.c_int, vp,
+                                    ctypes.c_int64, vp, P(ctypes.c_int64)]
+        L.orc_serialize.restype = ctypes.c_int
+        L.orc_parse.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, P(OrcParams), ctypes.c_int, vp,
+                                ctypes.c_int, vp, vp, P(ctypes.c_int)]
+        L.orc_parse.restype = ctypes.c_int
         L.orc_fit_pair.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32),
@@ -169,6 +176,39 @@ def bits(leaves: np.ndarray, W: int, H: int, p: OrcParams, technique2: bool = Tr
     leaves = np.ascontiguousarray(leaves, dtype=LEAF_DTYPE)
     return int(lib().orc_bits(leaves.ctypes.data, len(leaves), W, H, ctypes.byref(p),
                               1 if technique2 else 0))
+
+
+def serialize(leaves: np.ndarray, W: int, H: int, p: OrcParams, technique2: bool = True):
+    """The bitstream of Sections 3.3-3.4: (uint32 words, tile bit index of
+    ntop + 1 entries, number of bits)."""
+    leaves = np.ascontiguousarray(leaves, dtype=LEAF_DTYPE)
+    ntop = (W // p.bmax) * (H // p.bmax)
+    words = np.zeros(len(leaves) * 3 + 8, dtype=np.uint32)
+    tile_bits = np.zeros(ntop + 1, dtype=np.uint64)
+    nbits = ctypes.c_int64()
+    rc = lib().orc_serialize(leaves.ctypes.data, len(leaves), W, H, ctypes.byref(p), 1 if technique2 else 0,
+                             words.ctypes.data, words.size, tile_bits.ctypes.data, ctypes.byref(nbits))
+    if rc:
+        raise RuntimeError(f"orc_serialize failed ({rc})")
+    return words[: (nbits.value + 31) // 32].copy(), tile_bits, int(nbits.value)
+
+
+def parse(words: np.ndarray, nbits: int, W: int, H: int, p: OrcParams, technique2: bool = True):
+    """Read a bitstream back: (leaves, split masks, tile bit index)."""
+    words = np.ascontiguousarray(words, dtype=np.uint32)
+    if words.size == 0:
+        words = np.zeros(1, dtype=np.uint32)
+    ntop = (W // p.bmax) * (H // p.bmax)
+    cap = (W // p.bmin) * (H // p.bmin)
+    out = np.zeros(cap, dtype=LEAF_DTYPE)
+    split = np.zeros(ntop, dtype=np.uint32)
+    tile_bits = np.zeros(ntop + 1, dtype=np.uint64)
+    n = ctypes.c_int()
+    rc = lib().orc_parse(words.ctypes.data, int(nbits), W, H, ctypes.byref(p), 1 if technique2 else 0,
+                         out.ctypes.data, cap, split.ctypes.data, tile_bits.ctypes.data, ctypes.byref(n))
+    if rc:
+        raise ValueError(f"orc_parse: malformed stream ({rc})")
+    return out[: n.value].copy(), split, tile_bits
 
 
 def fit_pair(img, x, y, B, dx, dy, iso=0, s_bits=5, o_bits=7):
