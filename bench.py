@@ -527,6 +527,8 @@ def run_batched(args, spec: Spec):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
+    if spec.name in ("cfg1", "cfg2"):
+        line["rate_distortion"], line["bitstream"] = rate_distortion(fic, torch, stream, items, enc, dec, nrec)
     if tuning:
         line["autotune"] = {"encode_best": tuning["encode"]["best"], "encode_best_ms": round(tuning["encode"]["best_ms"], 4),
                             "encode_trials": tuning["encode"]["trials"],
@@ -544,6 +546,41 @@ def run_batched(args, spec: Spec):
         print(json.dumps(line), flush=True)
     dist_finish(world)
     return 0
+
+
+def rate_distortion(fic, torch, stream, items, enc, dec, nrec):
+    """Bits per pixel of each stream's bitstream (Sections 3.3-3.4, with
+    Technique 2) and PSNR of its decode (Section 4), per threshold; plus the
+    device time of writing and reading all the bitstreams."""
+    from oracle import oracle as O  # PSNR definition only
+
+    per = {}
+    with torch.cuda.stream(stream):
+        bits = [fic.serialize(st, True, stream) for st in enc.outs]
+        # timing: every stream written, then every stream read back
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        for st in enc.outs:
+            fic.serialize(st, True, stream)
+        ev[1].record(stream)
+        back = [fic.parse(w, ix, st.width, st.height, st.params, True, stream) for (w, ix), st in zip(bits, enc.outs)]
+        ev[2].record(stream)
+    stream.synchronize()
+    total_bits = 0
+    for (im, mode, bmax, bmin, t), (w, ix), d in zip(items, bits, dec.outs):
+        nb = int(ix[-1].item())
+        total_bits += nb
+        e = per.setdefault(t, {"bpp": [], "psnr": []})
+        e["bpp"].append(nb / im.size)
+        e["psnr"].append(O.psnr(im, d.cpu().numpy()))
+    same = all(np.array_equal(b.to_host(stream)["records"].view(np.uint8), st.to_host(stream)["records"].view(np.uint8))
+               for b, st in zip(back[:4], enc.outs[:4]))
+    rd = [{"rms_threshold": t, "bpp": round(float(np.mean(v["bpp"])), 4), "psnr_db": round(float(np.mean(v["psnr"])), 3)}
+          for t, v in sorted(per.items())]
+    return rd, {"streams": len(items), "records": int(sum(nrec)), "bits": total_bits,
+                "serialize_ms": round(ev[0].elapsed_time(ev[1]), 4), "parse_ms": round(ev[1].elapsed_time(ev[2]), 4),
+                "round_trip_identical": bool(same),
+                "note": "one serialize / parse call per stream (three kernels each); technique 2 on"}
 
 
 def plain_per_image(fic, torch, stream, dimgs, plist, iters, enc, dec, pixels, batched_value):

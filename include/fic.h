@@ -107,6 +107,7 @@ typedef struct fic_record {
 /* Device error bits in FIC_INFO_ERROR. */
 #define FIC_DEVERR_TIMEOUT 1u
 #define FIC_DEVERR_CAPACITY 2u
+#define FIC_DEVERR_FORMAT 4u   /* fic_parse: the bitstream does not tile the image */
 
 /* A transform stream in device memory.  The caller allocates every buffer
  * (sizes from fic_stream_sizes) and keeps ownership.
@@ -137,6 +138,11 @@ FIC_API int fic_version(void);
  * error code the encoder would return.  Requirements: width and height
  * multiples of bmax and of 16, at least 2*bmax, at most 65535. */
 FIC_API int fic_validate(int width, int height, const fic_params *p);
+/* The checks a stream that already exists must pass to be decoded,
+ * serialised or rescaled: the geometry and codebooks of fic_validate without
+ * the encoder's mode-specific limits (an exhaustive-search stream rescaled
+ * by 2 has 16 x 16 ranges). */
+FIC_API int fic_validate_stream(int width, int height, const fic_params *p);
 
 /* Sizes of the buffers of a stream for this image: number of top-level
  * blocks and the largest possible record count (every range at bmin). */
@@ -273,6 +279,53 @@ FIC_API int fic_plan_autotune(fic_plan *plan, int iters, int reps, void *stream,
 #define FIC_NOALLOC_MAX_STRIPS 65536
 FIC_API int fic_encode_noalloc(const uint8_t *d_img, int width, int height, const fic_params *p,
                                fic_stream *out, void *stream);
+
+/* ---- Bitstream of the stored parameters (Sections 3.3 and 3.4) ----
+ * Layout: bits appended least-significant first into uint32 words; leaves
+ * in the stream's canonical order; per leaf: level - 1 in ceil(log2 L)
+ * bits (with technique2 != 0, omitted for a last-level leaf that is not the
+ * top-left of its group of four: Technique 2, Section 3.4); 1 phase bit at
+ * levels < L when MNS phase 2 is on; phase 1: k (s_bits), q (o_bits), and
+ * for local search the offset index ((oy/step + R/step) * per + ox/step +
+ * R/step, per = 2R/step + 1) in ceil(log2 per^2) bits, for exhaustive search
+ * the domain's raster index on the step grid (ceil(log2 #domains) bits) and
+ * the isometry (ceil(log2 isometries) bits); phase 2: q_i (o_bits), the
+ * three differences O_k - O_i (M bits two's complement, M = 5 at level 1,
+ * 6 below, Section 3.3), the four contrast bits.  Positions and centred
+ * domains are implied by the order.  tile_bits[t] (uint64, ntop + 1 entries)
+ * is the first bit of top-level block t and tile_bits[ntop] the total: an
+ * index that lets every block be read independently.  The paper fixes the
+ * fields and widths; their order is this library's.  Device pointers,
+ * asynchronous on `stream`; the workspace holds the scans. */
+FIC_API int64_t fic_bitstream_max_words(int width, int height, const fic_params *p);
+FIC_API size_t fic_bitstream_workspace_bytes(int width, int height, const fic_params *p);
+/* Write the bitstream of `st` (records, tile offsets and record count as an
+ * encode left them) into d_words (at least fic_bitstream_max_words words;
+ * zeroed first) and its index into d_tile_bits. */
+FIC_API int fic_serialize(const fic_stream *st, int technique2, uint32_t *d_words, int64_t nwords,
+                          uint64_t *d_tile_bits, void *d_workspace, size_t workspace_bytes, void *stream);
+/* Read a bitstream back into `out` (width, height and params set by the
+ * caller, buffers from fic_stream_sizes): records, tile offsets, split masks
+ * and the record count (fits 0).  A stream that does not tile the image
+ * sets FIC_DEVERR_FORMAT in out->info (fic_stream_info returns FIC_EBADPARAM
+ * for it). */
+FIC_API int fic_parse(const uint32_t *d_words, int64_t nwords, const uint64_t *d_tile_bits, int technique2,
+                      fic_stream *out, void *d_workspace, size_t workspace_bytes, void *stream);
+
+/* ---- Resolution-independent decoding (Section 1) ----
+ * The stored transforms describe the image at no particular resolution.
+ * fic_rescale_params gives the geometry of a stream rescaled by 2^shift
+ * (shift +1: twice the resolution, -1: half): sides, block sides, local
+ * search radius/step and domain step times 2^shift.  FIC_EBADPARAM when a
+ * rescaled quantity is not an integer or leaves fic_validate_stream's
+ * limits.  fic_stream_rescale writes the rescaled records (positions and
+ * domains times 2^shift, codes unchanged), tile offsets, split masks and
+ * info into `out`, whose width/height/params must be the rescaled ones and
+ * whose buffers come from fic_stream_sizes; decoding `out` renders the
+ * attractor on the rescaled grid.  Asynchronous on `stream`. */
+FIC_API int fic_rescale_params(int width, int height, const fic_params *p, int shift, int *width_out,
+                               int *height_out, fic_params *p_out);
+FIC_API int fic_stream_rescale(const fic_stream *in, int shift, fic_stream *out, void *stream);
 
 /* ---- Position statistics (Section 2, Figs. 2 and 3) ----
  * Histograms of x_d - x_r and y_d - y_r over the stream's records: the

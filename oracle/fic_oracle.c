@@ -44,6 +44,8 @@ typedef struct {
     int32_t local_radius, local_step;
     int32_t dom_step;
     int32_t isometries;
+    int32_t phase2_domain; /* 0: sub-blocks use their own centred domains; 1: the
+                              quadrants of the parent's (alternative reading) */
 } orc_params;
 
 /* One leaf of the quadtree, i.e. one stored transform (16 bytes). */
@@ -299,6 +301,22 @@ int orc_search(const uint8_t *img, int W, int H, const orc_params *p, int x, int
 /* ------------------------------------------------------------------ */
 /* MNS phase 2 (Sections 3.1 - 3.3)                                     */
 
+/* Domain of phase-2 sub-block sb (TL, TR, BL, BR) of block (x, y, B): the
+ * paper does not say which domain a sub-block uses.  Reading 0: its own
+ * centred domain (the no-search rule at the sub-block size).  Reading 1:
+ * the matching quadrant of the parent block's centred domain, i.e. the
+ * parent's 2B x 2B domain cut into four B x B quarters. */
+static void phase2_domain_of(const orc_params *p, int W, int H, int x, int y, int B, int sb, int *dx, int *dy) {
+    int h = B / 2;
+    if (p->phase2_domain) {
+        *dx = orc_centred(x, B, W) + (sb & 1) * B;
+        *dy = orc_centred(y, B, H) + (sb >> 1) * B;
+    } else {
+        *dx = orc_centred(x + (sb & 1) * h, h, W);
+        *dy = orc_centred(y + (sb >> 1) * h, h, H);
+    }
+}
+
 /* Phase 2 of a block that failed phase 1 at level j < L ("Technique 1").
  * O_i is the block's quantised mean (its phase-1 luminance code q_i).  The
  * four sub-blocks (TL, TR, BL, BR) have means O_k; their differences to O_i
@@ -321,7 +339,8 @@ int orc_phase2(const uint8_t *img, int W, int H, const orc_params *p, int level,
     orc_moments ms[4];
     for (int sb = 0; sb < 4; sb++) {
         int sx = x + (sb & 1) * h, sy = y + (sb >> 1) * h;
-        int dx = orc_centred(sx, h, W), dy = orc_centred(sy, h, H);
+        int dx, dy;
+        phase2_domain_of(p, W, H, x, y, B, sb, &dx, &dy);
         orc_moments_of(img, W, sx, sy, h, dx, dy, 0, &ms[sb]);
         /* round-half-up of (mean_k - O_i) = floor((2(Sr_k - n4 O_i) + n4) / (2 n4)) */
         delta[sb] = floor_div(2 * (ms[sb].sr - n4 * Oi) + n4, 2 * n4);
@@ -578,8 +597,9 @@ int orc_decode(const orc_leaf *leaves, int nleaves, int W, int H, const orc_para
                 O[3] = 4 * Oi - (O[0] + O[1] + O[2]);
                 for (int sb = 0; sb < 4; sb++) {
                     int sx = lf->x + (sb & 1) * h, sy = lf->y + (sb >> 1) * h;
-                    apply_transform(cur, nxt, W, sx, sy, h, orc_centred(sx, h, W),
-                                    orc_centred(sy, h, H), 0,
+                    int dx, dy;
+                    phase2_domain_of(p, W, H, lf->x, lf->y, B, sb, &dx, &dy);
+                    apply_transform(cur, nxt, W, sx, sy, h, dx, dy, 0,
                                     orc_phase2_contrast(lf->level, (lf->k >> sb) & 1), O[sb]);
                 }
             }
@@ -821,5 +841,53 @@ int orc_parse(const uint32_t *words, int64_t nbits, int W, int H, const orc_para
     tile_bits[tw * th] = (uint64_t)pos;
     if (pos != nbits) return ORC_EBADPARAM;
     *nleaves = n;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Resolution-independent decoding (Section 1: the stored transforms are a
+ * description of the image at no particular resolution).  Rescaling a
+ * stream by 2^shift (shift = +1 or -1) multiplies every position, block
+ * side and domain position by 2^shift and keeps the codes; decoding the
+ * result renders the attractor on a grid 2^shift times finer or coarser.
+ * Returns ORC_EBADPARAM when a rescaled quantity is not an integer or the
+ * block sides leave 4 <= bmin, bmax <= 32 (the sides the decoder handles). */
+int orc_rescale(const orc_leaf *in, int n, int W, int H, const orc_params *p, int shift, orc_leaf *out,
+                orc_params *po, int *W2, int *H2) {
+    if (shift != 1 && shift != -1) return ORC_EBADPARAM;
+    *po = *p;
+    if (shift > 0) {
+        po->bmax = p->bmax * 2;
+        po->bmin = p->bmin * 2;
+        po->local_radius = p->local_radius * 2;
+        po->local_step = p->local_step * 2;
+        po->dom_step = p->dom_step * 2;
+        *W2 = W * 2;
+        *H2 = H * 2;
+    } else {
+        if (p->bmin % 2 || W % 2 || H % 2 || p->local_radius % 2 || p->local_step % 2 || p->dom_step % 2)
+            return ORC_EBADPARAM;
+        po->bmax = p->bmax / 2;
+        po->bmin = p->bmin / 2;
+        po->local_radius = p->local_radius / 2;
+        po->local_step = p->local_step / 2;
+        po->dom_step = p->dom_step / 2;
+        *W2 = W / 2;
+        *H2 = H / 2;
+    }
+    if (po->bmin < 4 || po->bmax > 32) return ORC_EBADPARAM;
+    for (int i = 0; i < n; i++) {
+        orc_leaf lf = in[i];
+        int v[4] = {lf.x, lf.y, lf.dx, lf.dy};
+        for (int k = 0; k < 4; k++) {
+            if (shift < 0 && v[k] % 2) return ORC_EBADPARAM;
+            v[k] = shift > 0 ? v[k] * 2 : v[k] / 2;
+        }
+        lf.x = (uint16_t)v[0];
+        lf.y = (uint16_t)v[1];
+        lf.dx = (uint16_t)v[2];
+        lf.dy = (uint16_t)v[3];
+        out[i] = lf;
+    }
     return ORC_OK;
 }

@@ -36,12 +36,12 @@ class OrcParams(ctypes.Structure):
         ("mode", ctypes.c_int32), ("bmax", ctypes.c_int32), ("bmin", ctypes.c_int32),
         ("thr_rms", ctypes.c_double * 4), ("s_bits", ctypes.c_int32), ("o_bits", ctypes.c_int32),
         ("phase2", ctypes.c_int32), ("local_radius", ctypes.c_int32), ("local_step", ctypes.c_int32),
-        ("dom_step", ctypes.c_int32), ("isometries", ctypes.c_int32),
+        ("dom_step", ctypes.c_int32), ("isometries", ctypes.c_int32), ("phase2_domain", ctypes.c_int32),
     ]
 
 
 def make_params(mode="mns", bmax=32, bmin=4, thr=8.0, s_bits=5, o_bits=7, phase2=True,
-                local_radius=16, local_step=4, dom_step=4, isometries=8) -> OrcParams:
+                local_radius=16, local_step=4, dom_step=4, isometries=8, phase2_domain=0) -> OrcParams:
     p = OrcParams()
     p.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     p.bmax, p.bmin = int(bmax), int(bmin)
@@ -51,6 +51,7 @@ def make_params(mode="mns", bmax=32, bmin=4, thr=8.0, s_bits=5, o_bits=7, phase2
         p.thr_rms[i] = float(thr[i])
     p.s_bits, p.o_bits = int(s_bits), int(o_bits)
     p.phase2 = 1 if phase2 else 0
+    p.phase2_domain = int(phase2_domain)
     p.local_radius, p.local_step = int(local_radius), int(local_step)
     p.dom_step, p.isometries = int(dom_step), int(isometries)
     return p
@@ -93,6 +94,9 @@ def lib():
         L.orc_parse.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, P(OrcParams), ctypes.c_int, vp,
                                 ctypes.c_int, vp, vp, P(ctypes.c_int)]
         L.orc_parse.restype = ctypes.c_int
+        L.orc_rescale.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(OrcParams), ctypes.c_int, vp,
+                                  P(OrcParams), P(ctypes.c_int), P(ctypes.c_int)]
+        L.orc_rescale.restype = ctypes.c_int
         L.orc_fit_pair.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, P(ctypes.c_int64), P(ctypes.c_int32),
@@ -209,6 +213,20 @@ def parse(words: np.ndarray, nbits: int, W: int, H: int, p: OrcParams, technique
     if rc:
         raise ValueError(f"orc_parse: malformed stream ({rc})")
     return out[: n.value].copy(), split, tile_bits
+
+
+def rescale(leaves: np.ndarray, W: int, H: int, p: OrcParams, shift: int):
+    """The stream at 2**shift times the resolution (shift = +1 or -1):
+    (leaves, params, W, H).  ValueError when it does not exist."""
+    leaves = np.ascontiguousarray(leaves, dtype=LEAF_DTYPE)
+    out = np.zeros_like(leaves)
+    po = OrcParams()
+    W2, H2 = ctypes.c_int(), ctypes.c_int()
+    rc = lib().orc_rescale(leaves.ctypes.data, len(leaves), W, H, ctypes.byref(p), int(shift), out.ctypes.data,
+                           ctypes.byref(po), ctypes.byref(W2), ctypes.byref(H2))
+    if rc:
+        raise ValueError(f"orc_rescale: no stream at this scale ({rc})")
+    return out, po, W2.value, H2.value
 
 
 def fit_pair(img, x, y, B, dx, dy, iso=0, s_bits=5, o_bits=7):

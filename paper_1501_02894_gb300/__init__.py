@@ -23,6 +23,9 @@ from .fic import (  # noqa: F401
     lib,
     offset_histogram,
     params,
+    parse,
+    rescale,
+    serialize,
     stream_sizes,
     validate,
 )

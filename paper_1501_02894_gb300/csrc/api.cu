@@ -117,6 +117,24 @@ int check_size(int W, int H, const fic_params *p) {
     return FIC_OK;
 }
 
+// Geometry and codebooks a stream must have to be stored, decoded,
+// serialised or rescaled (the encoder's mode-specific limits -- the
+// exhaustive search's 8x8 ranges, the local search's radius -- do not
+// apply to a stream that already exists, e.g. one rescaled by 2).
+int check_stream(int W, int H, const fic_params *p) {
+    if (!p) return FIC_EBADPARAM;
+    if (p->mode < FIC_NOSEARCH || p->mode > FIC_EXHAUSTIVE) return FIC_EBADPARAM;
+    if (!(p->bmax == 8 || p->bmax == 16 || p->bmax == 32)) return FIC_EBADPARAM;
+    if (!is_pow2(p->bmin) || p->bmin < 4 || p->bmin > p->bmax) return FIC_EBADPARAM;
+    if (levels_of(p) > 4) return FIC_EBADPARAM;
+    if (p->mode == FIC_EXHAUSTIVE && (p->bmin != p->bmax || p->isometries < 1 || p->isometries > 8 || p->dom_step < 1))
+        return FIC_EBADPARAM;
+    if (p->mode == FIC_LOCAL && (p->local_radius < 0 || p->local_step < 2 || (p->local_step & 1)))
+        return FIC_EBADPARAM;
+    if (p->s_bits < 1 || p->s_bits > 7 || p->o_bits < 1 || p->o_bits > 8) return FIC_EBADPARAM;
+    return check_size(W, H, p);
+}
+
 inline int64_t t2q_of(double t) { return (int64_t)(t * t * 256.0 + 0.5); }
 
 int strips_per_row(int W, int bmax) {
@@ -279,6 +297,8 @@ const char *fic_strerror(int code) {
     }
 }
 
+int fic_validate_stream(int width, int height, const fic_params *p) { return check_stream(width, height, p); }
+
 int fic_validate(int width, int height, const fic_params *p) {
     int rc = check_params(p);
     if (rc) return rc;
@@ -286,7 +306,7 @@ int fic_validate(int width, int height, const fic_params *p) {
 }
 
 int fic_stream_sizes(int width, int height, const fic_params *p, int32_t *ntop, int32_t *max_records) {
-    int rc = fic_validate(width, height, p);
+    int rc = check_stream(width, height, p);
     if (rc) return rc;
     if (ntop) *ntop = (width / p->bmax) * (height / p->bmax);
     if (max_records) *max_records = (width / p->bmin) * (height / p->bmin);
@@ -676,7 +696,7 @@ int decode_plan_create_staged(const fic_stream *sts, int count, uint8_t *const *
     int strips = 0;
     for (int i = 0; i < count; ++i) {
         const fic_stream *s = &sts[i];
-        int rc = fic_validate(s->width, s->height, &s->params);
+        int rc = check_stream(s->width, s->height, &s->params);
         if (rc == FIC_OK && s->params.bmax != bmax) rc = FIC_EBADPARAM;
         if (rc == FIC_OK && (!s->records || !s->tile_offsets || !d_outs[i] ||
                              (reinterpret_cast<uintptr_t>(d_outs[i]) & 15)))
@@ -802,6 +822,7 @@ int fic_stream_info(const fic_stream *st, int64_t *records, int64_t *fits, void 
     if (fits) *fits = (int64_t)h[FIC_INFO_FITS_LO] | ((int64_t)h[FIC_INFO_FITS_HI] << 32);
     if (h[FIC_INFO_ERROR] & FIC_DEVERR_TIMEOUT) return FIC_ETIMEOUT;
     if (h[FIC_INFO_ERROR] & FIC_DEVERR_CAPACITY) return FIC_ECAPACITY;
+    if (h[FIC_INFO_ERROR] & FIC_DEVERR_FORMAT) return FIC_EBADPARAM;
     return FIC_OK;
 }
 

@@ -657,7 +657,8 @@ int fic_submit(fic_server *S, const fic_job *job, int64_t *ticket) {
     if (job->kind == FIC_JOB_ENCODE && (!job->image || !job->out_records)) return FIC_EBADPARAM;
     if (job->kind == FIC_JOB_DECODE && (!job->records || job->nrecords <= 0 || !job->out_image || job->iters < 0))
         return FIC_EBADPARAM;
-    const int rc = fic_validate(job->width, job->height, &job->params);
+    const int rc = job->kind == FIC_JOB_ENCODE ? fic_validate(job->width, job->height, &job->params)
+                                               : fic_validate_stream(job->width, job->height, &job->params);
     if (rc) return rc;
     if (job->kind == FIC_JOB_DECODE && !records_valid(*job)) return FIC_EBADPARAM;
     Job *J = new (std::nothrow) Job();

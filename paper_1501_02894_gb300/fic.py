@@ -152,6 +152,16 @@ def lib():
         L.fic_server_get_stats.argtypes = [vp, P(ServerStats)]
         L.fic_server_destroy.argtypes = [vp]
         L.fic_offset_histogram.argtypes = [P(StreamC), vp, vp, vp]
+        L.fic_validate_stream.argtypes = [ctypes.c_int, ctypes.c_int, P(Params)]
+        L.fic_rescale_params.argtypes = [ctypes.c_int, ctypes.c_int, P(Params), ctypes.c_int, P(ctypes.c_int),
+                                         P(ctypes.c_int), P(Params)]
+        L.fic_stream_rescale.argtypes = [P(StreamC), ctypes.c_int, P(StreamC), vp]
+        L.fic_bitstream_max_words.argtypes = [ctypes.c_int, ctypes.c_int, P(Params)]
+        L.fic_bitstream_max_words.restype = ctypes.c_int64
+        L.fic_bitstream_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, P(Params)]
+        L.fic_bitstream_workspace_bytes.restype = ctypes.c_size_t
+        L.fic_serialize.argtypes = [P(StreamC), ctypes.c_int, vp, ctypes.c_int64, vp, vp, ctypes.c_size_t, vp]
+        L.fic_parse.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int, P(StreamC), vp, ctypes.c_size_t, vp]
         L.fic_strerror.argtypes = [ctypes.c_int]
         L.fic_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -435,6 +445,45 @@ def offset_histogram(st: Stream, stream=None):
     _check(lib().fic_offset_histogram(ctypes.byref(st.c), _ptr(hx), _ptr(hy), _stream_handle(stream)),
            "fic_offset_histogram")
     return hx, hy
+
+
+def serialize(st: Stream, technique2: bool = True, stream=None):
+    """Bitstream of a stream (Sections 3.3-3.4): (uint32 word tensor of the
+    maximal size, uint64 tile bit index).  The bit count is index[-1]."""
+    L = lib()
+    nw = int(L.fic_bitstream_max_words(st.width, st.height, ctypes.byref(st.params)))
+    ws_n = int(L.fic_bitstream_workspace_bytes(st.width, st.height, ctypes.byref(st.params)))
+    dev = st.records.device
+    words = torch.empty(nw, dtype=torch.int32, device=dev)
+    index = torch.empty(st.ntop + 1, dtype=torch.int64, device=dev)
+    ws = torch.empty(ws_n, dtype=torch.uint8, device=dev)
+    _check(L.fic_serialize(ctypes.byref(st.c), 1 if technique2 else 0, _ptr(words), nw, _ptr(index), _ptr(ws), ws_n,
+                           _stream_handle(stream)), "fic_serialize")
+    return words, index
+
+
+def parse(words: torch.Tensor, index: torch.Tensor, width: int, height: int, p: Params, technique2: bool = True,
+          stream=None) -> Stream:
+    """Read a bitstream back into a new Stream on the words' device."""
+    L = lib()
+    st = Stream(width, height, p, words.device)
+    ws_n = int(L.fic_bitstream_workspace_bytes(width, height, ctypes.byref(p)))
+    ws = torch.empty(ws_n, dtype=torch.uint8, device=words.device)
+    _check(L.fic_parse(_ptr(words), words.numel(), _ptr(index), 1 if technique2 else 0, ctypes.byref(st.c), _ptr(ws),
+                       ws_n, _stream_handle(stream)), "fic_parse")
+    return st
+
+
+def rescale(st: Stream, shift: int, stream=None) -> Stream:
+    """The stream at 2**shift times the resolution (shift +1 or -1), as a new
+    Stream on the same device (Section 1: resolution-independent decoding)."""
+    W, H, q = ctypes.c_int(), ctypes.c_int(), Params()
+    _check(lib().fic_rescale_params(st.width, st.height, ctypes.byref(st.params), int(shift), ctypes.byref(W),
+                                    ctypes.byref(H), ctypes.byref(q)), "fic_rescale_params")
+    out = Stream(W.value, H.value, q, st.records.device)
+    _check(lib().fic_stream_rescale(ctypes.byref(st.c), int(shift), ctypes.byref(out.c), _stream_handle(stream)),
+           "fic_stream_rescale")
+    return out
 
 
 def validate(width: int, height: int, p: Params) -> int:

@@ -76,3 +76,64 @@ def test_malformed_streams_rejected(orc):
         assert not np.array_equal(back.view(np.uint8), leaves.view(np.uint8))
     except ValueError:
         pass
+
+
+# ---------------------------------------------------------------------------
+# Device writer and reader against the oracle
+
+GPU_CASES = [c for c in CASES if c[2] >= 4]
+
+
+@pytest.fixture(scope="module")
+def fic():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1501_02894_gb300 as fic
+    fic.lib()
+    return fic
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", GPU_CASES, ids=[f"{c[0]}-{c[1]}-{c[2]}-{c[4]}" for c in GPU_CASES])
+@pytest.mark.parametrize("t2", [True, False])
+def test_device_bitstream_equals_oracle(fic, orc, case, t2):
+    import torch
+    mode, bmax, bmin, thr, N, kw = case
+    img = synth.gaussian_scene(N, 5)
+    op = orc.make_params(mode, bmax, bmin, thr, **kw)
+    p = fic.params(mode, bmax, bmin, thr, **kw)
+    leaves, split, _ = orc.encode(img, op)
+    want_words, want_index, nbits = orc.serialize(leaves, N, N, op, t2)
+    st = fic.fic_encode(torch.from_numpy(img).cuda(), p)
+    words, index = fic.serialize(st, t2)
+    torch.cuda.synchronize()
+    idx = index.cpu().numpy().view(np.uint64)
+    assert np.array_equal(idx, want_index)
+    w = words.cpu().numpy().view(np.uint32)
+    nw = (nbits + 31) // 32
+    assert np.array_equal(w[:nw], want_words) and not w[nw:].any()
+    back = fic.parse(words, index, N, N, p, t2)
+    got = back.to_host()
+    assert np.array_equal(got["records"].view(np.uint8), leaves.view(np.uint8))
+    assert np.array_equal(got["split"], split)
+    assert np.array_equal(got["tile_offsets"], st.to_host()["tile_offsets"])
+    # the oracle's words read by the device
+    back2 = fic.parse(torch.from_numpy(want_words.view(np.int32).copy()).cuda(),
+                      torch.from_numpy(want_index.view(np.int64).copy()).cuda(), N, N, p, t2)
+    assert np.array_equal(back2.to_host()["records"].view(np.uint8), leaves.view(np.uint8))
+
+
+@pytest.mark.gpu
+def test_device_parse_rejects_malformed(fic, orc):
+    import torch
+    img = synth.gaussian_scene(128, 9)
+    p = fic.params("mns", 32, 4, 8.0)
+    st = fic.fic_encode(torch.from_numpy(img).cuda(), p)
+    words, index = fic.serialize(st)
+    bad_index = index.clone()
+    bad_index[1] -= 3  # block 0 ends early: its leaves overrun
+    back = fic.parse(words, bad_index, 128, 128, p)
+    with pytest.raises(fic.FicError) as e:
+        back.info_host()
+    assert e.value.code == -2

@@ -238,6 +238,15 @@ def _mean_delta(img, x, y, h, Oi):
     return round_half_up(F(int(blk.sum()), h * h) - Oi)
 
 
+def _sub_domain(orc, p, x, y, B, sb, W, H):
+    """Phase-2 domain of sub-block sb: its own centred B x B domain, or (the
+    alternative reading) quadrant sb of the parent's centred 2B x 2B domain."""
+    h = B // 2
+    if p.phase2_domain:
+        return orc.centred(x, B, W) + (sb & 1) * B, orc.centred(y, B, H) + (sb >> 1) * B
+    return orc.centred(x + (sb & 1) * h, h, W), orc.centred(y + (sb >> 1) * h, h, H)
+
+
 def _check_encoding(orc, img, p):
     H, W = img.shape
     leaves, split, _ = orc.encode(img, p)
@@ -280,7 +289,7 @@ def _check_encoding(orc, img, p):
             assert F(sum(Os), 4) == Oi
             for sb in range(4):
                 sx, sy = x + (sb & 1) * h, y + (sb >> 1) * h
-                sdx, sdy = orc.centred(sx, h, W), orc.centred(sy, h, H)
+                sdx, sdy = _sub_domain(orc, p, x, y, B, sb, W, H)
                 e = [scaled_sse_int(img, sx, sy, h, sdx, sdy, orc.phase2_contrast(lvl, b), Os[sb])
                      for b in (0, 1)]
                 bit = (int(lf["k"]) >> sb) & 1
@@ -318,7 +327,7 @@ def _check_encoding(orc, img, p):
                         worst_ok = True
                         for sb in range(4):
                             sx, sy = x + (sb & 1) * h, y + (sb >> 1) * h
-                            sdx, sdy = orc.centred(sx, h, W), orc.centred(sy, h, H)
+                            sdx, sdy = _sub_domain(orc, p, x, y, B, sb, W, H)
                             e = min(scaled_sse_int(img, sx, sy, h, sdx, sdy,
                                                    orc.phase2_contrast(lvl, b), Os[sb]) for b in (0, 1))
                             worst_ok &= e < T2 * h * h * (512 * h * h) ** 2
@@ -338,9 +347,10 @@ def _check_encoding(orc, img, p):
 
 
 @pytest.mark.parametrize("thr", [8.0, 4.0])
-def test_decisions_rederived_cfg1(orc, thr):
+@pytest.mark.parametrize("p2d", [0, 1])
+def test_decisions_rederived_cfg1(orc, thr, p2d):
     img = synth.cfg1_image()
-    p = orc.make_params("mns", 16, 4, thr)
+    p = orc.make_params("mns", 16, 4, thr, phase2_domain=p2d)
     leaves = _check_encoding(orc, img, p)
     assert (leaves["phase"] == 2).any() or thr == 4.0
 
@@ -439,9 +449,10 @@ def test_decoder_first_iterate_is_luminance(orc):
                 assert np.all(x1[sy:sy + h, sx:sx + h] == min(255, max(0, Os[sb])))
 
 
-def test_decoder_second_iterate_direct(orc):
+@pytest.mark.parametrize("p2d", [0, 1])
+def test_decoder_second_iterate_direct(orc, p2d):
     img = synth.cfg1_image()
-    p = orc.make_params("mns", 16, 4, 8.0)
+    p = orc.make_params("mns", 16, 4, 8.0, phase2_domain=p2d)
     leaves, _, _ = orc.encode(img, p)
     x1 = orc.decode(leaves, 256, 256, p, 1)
     x2 = orc.decode(leaves, 256, 256, p, 2)
@@ -456,10 +467,12 @@ def test_decoder_second_iterate_direct(orc):
             Os = [Oi + int(lf["d"][0]), Oi + int(lf["d"][1]), Oi + int(lf["d"][2])]
             Os.append(4 * Oi - sum(Os))
             parts = [(x + (sb & 1) * h, y + (sb >> 1) * h, h,
-                      F(orc.phase2_contrast(lvl, (int(lf["k"]) >> sb) & 1), 128), Os[sb])
+                      F(orc.phase2_contrast(lvl, (int(lf["k"]) >> sb) & 1), 128), Os[sb],
+                      _sub_domain(orc, p, x, y, B, sb, 256, 256))
                      for sb in range(4)]
-        for (sx, sy, b, s, O) in parts:
-            dx, dy = orc.centred(sx, b, 256), orc.centred(sy, b, 256)
+        if lf["phase"] == 1:
+            parts = [parts[0] + ((orc.centred(x, B, 256), orc.centred(y, B, 256)),)]
+        for (sx, sy, b, s, O, (dx, dy)) in parts:
             D = decimate(x1, dx, dy, b)
             dbar = sum(sum(row) for row in D) / (b * b)
             for v in range(b):
@@ -590,3 +603,13 @@ def test_bad_sizes_rejected(orc):
     assert orc.check(500, 512, p) != 0
     assert orc.check(32, 64, p) != 0
     assert orc.check(64, 64, orc.make_params("mns", 64, 2, 8.0)) != 0   # more than 4 levels
+
+
+def test_phase2_domain_readings_differ(orc):
+    """The two readings of the phase-2 domain give different streams (both
+    re-derived above); phase 1 and the split rule are shared."""
+    img = synth.gaussian_scene(256, 2)
+    a, _, _ = orc.encode(img, orc.make_params("mns", 32, 4, 8.0, phase2_domain=0))
+    b, _, _ = orc.encode(img, orc.make_params("mns", 32, 4, 8.0, phase2_domain=1))
+    assert (a["phase"] == 2).any() and (b["phase"] == 2).any()
+    assert len(a) != len(b) or not np.array_equal(a.view(np.uint8), b.view(np.uint8))
