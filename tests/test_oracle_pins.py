@@ -608,8 +608,8 @@ def test_bad_sizes_rejected(orc):
 def test_phase2_domain_readings_differ(orc):
     """The two readings of the phase-2 domain give different streams (both
     re-derived above); phase 1 and the split rule are shared."""
-    img = synth.gaussian_scene(256, 2)
-    a, _, _ = orc.encode(img, orc.make_params("mns", 32, 4, 8.0, phase2_domain=0))
-    b, _, _ = orc.encode(img, orc.make_params("mns", 32, 4, 8.0, phase2_domain=1))
+    img = synth.cfg1_image()
+    a, _, _ = orc.encode(img, orc.make_params("mns", 16, 4, 8.0, phase2_domain=0))
+    b, _, _ = orc.encode(img, orc.make_params("mns", 16, 4, 8.0, phase2_domain=1))
     assert (a["phase"] == 2).any() and (b["phase"] == 2).any()
     assert len(a) != len(b) or not np.array_equal(a.view(np.uint8), b.view(np.uint8))
