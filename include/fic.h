@@ -76,6 +76,9 @@ typedef struct fic_params {
     int32_t dom_step;     /* FIC_EXHAUSTIVE: domain grid step in pixels (4) */
     int32_t isometries;   /* FIC_EXHAUSTIVE: the first 1..8 isometries are tried */
     int32_t engine;       /* FIC_EXHAUSTIVE: 0 tensor cores (tcgen05), 1 CUDA cores */
+    int32_t phase2_domain; /* MNS phase 2: the domain of each sub-block (the paper does not
+                              say): 0 its own centred domain, 1 the matching quadrant of
+                              the parent block's centred domain */
 } fic_params;
 
 /* One stored transform = one quadtree leaf (16 bytes).
@@ -244,7 +247,7 @@ FIC_API int fic_plan_get_tuning(const fic_plan *plan, fic_tuning *t);
 FIC_API int fic_plan_set_tuning(fic_plan *plan, const fic_tuning *t);
 /* Time every candidate mapping on the plan's own batch and keep the fastest.
  * Encode plans try warps {8, 4} x CTAs per SM {1, 2, ..., max} x schedule
- * {static, dynamic}; decode plans try CTAs per SM {1, ..., max} with `iters`
+ * {static, dynamic}; decode plans try CTAs per SM {1, 2, 3, 4} with `iters`
  * iterations.  Each candidate runs once untimed, then `reps` times between
  * CUDA events on `stream`; the score is the median.  Synchronous: returns
  * after the last run with the plan's outputs written (identical for every

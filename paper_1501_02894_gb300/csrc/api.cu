@@ -104,6 +104,7 @@ int check_params(const fic_params *p) {
     if (!is_pow2(p->bmin) || p->bmin < 4 || p->bmin > p->bmax) return FIC_EBADPARAM;
     if (levels_of(p) > 4) return FIC_EBADPARAM;
     if (p->s_bits < 1 || p->s_bits > 7 || p->o_bits < 1 || p->o_bits > 8) return FIC_EBADPARAM;
+    if (p->phase2_domain != 0 && p->phase2_domain != 1) return FIC_EBADPARAM;
     const int L = levels_of(p);
     for (int j = 0; j < L; ++j)
         if (!(p->thr_rms[j] >= 0.0) || !(p->thr_rms[j] < 256.0)) return FIC_EBADPARAM;
@@ -132,6 +133,7 @@ int check_stream(int W, int H, const fic_params *p) {
     if (p->mode == FIC_LOCAL && (p->local_radius < 0 || p->local_step < 2 || (p->local_step & 1)))
         return FIC_EBADPARAM;
     if (p->s_bits < 1 || p->s_bits > 7 || p->o_bits < 1 || p->o_bits > 8) return FIC_EBADPARAM;
+    if (p->phase2_domain != 0 && p->phase2_domain != 1) return FIC_EBADPARAM;
     return check_size(W, H, p);
 }
 
@@ -413,6 +415,7 @@ int encode_plan_create_staged(const uint8_t *const *d_imgs, const int *widths, c
         d.bmin = p->bmin;
         d.L = L;
         d.phase2 = p->phase2 ? 1 : 0;
+        d.phase2_domain = p->phase2_domain ? 1 : 0;
         d.s_bits = p->s_bits;
         d.o_bits = p->o_bits;
         d.local_radius = p->local_radius;
@@ -569,7 +572,8 @@ int fic_plan_autotune(fic_plan *pl, int iters, int reps, void *stream, fic_tunin
             for (int k = 1; k <= (w == 8 ? 3 : 4); ++k)
                 for (int dyn = 0; dyn <= 1; ++dyn) cands.push_back(fic_tuning{w, k, dyn, cur.dec_ctas_per_sm});
     } else {
-        for (int k = 1; k <= 8; ++k) cands.push_back(fic_tuning{cur.enc_warps, cur.enc_ctas_per_sm, cur.enc_dynamic, k});
+        // the iteration kernels are built for 4 resident CTAs of 8 warps
+        for (int k = 1; k <= 4; ++k) cands.push_back(fic_tuning{cur.enc_warps, cur.enc_ctas_per_sm, cur.enc_dynamic, k});
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -739,6 +743,7 @@ int decode_plan_create_staged(const fic_stream *sts, int count, uint8_t *const *
         d.L = levels_of(&s->params);
         d.s_bits = s->params.s_bits;
         d.o_bits = s->params.o_bits;
+        d.phase2_domain = s->params.phase2_domain ? 1 : 0;
         strips += d.nstrips;
         pl->outs.push_back(d_outs[i]);
         pl->out_bytes.push_back((size_t)s->width * (size_t)s->height);

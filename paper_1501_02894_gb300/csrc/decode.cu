@@ -245,8 +245,13 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
             t_x = x + (sb & 1) * hb;
             t_y = y + (sb >> 1) * hb;
             t_lg = 31 - __clz(hb);
-            t_dx = centred_origin(t_x, hb, W);
-            t_dy = centred_origin(t_y, hb, H);
+            if (D.phase2_domain) {  // quadrant sb of the block's own centred domain
+                t_dx = centred_origin(x, B, W) + (sb & 1) * B;
+                t_dy = centred_origin(y, B, H) + (sb >> 1) * B;
+            } else {
+                t_dx = centred_origin(t_x, hb, W);
+                t_dy = centred_origin(t_y, hb, H);
+            }
             t_c = phase2_code(level, (k >> sb) & 1);
             t_iso = 0;
         }

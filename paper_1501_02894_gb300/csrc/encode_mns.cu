@@ -304,12 +304,42 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
                     O[2] = Oi + d[2];
                     O[3] = 4 * Oi - (O[0] + O[1] + O[2]);  // eq. (1)
                     const int c0 = phase2_code(j, 0), c1 = phase2_code(j, 1);
+                    // the sub-blocks' fits: against their own centred domains
+                    // (the children's phase-1 moments) or, with the other
+                    // reading, against the quadrants of this block's domain
+                    // (the children's domain moments are replaced in place:
+                    // only their codes and pass bits are used later)
+                    Fit (&sub)[2] = ch;
+                    if (D.phase2_domain) {
+                        if (Bc >= 8) {
+                            int sd = 0, sdd = 0, sdr = 0;
+                            if (valid)
+                                patch_moments<NP>(d4e, (dxa >> 1) + u0 - c_base, (dya >> 1) + v0 - r_base, rw, sd, sdd,
+                                                  sdr);
+                            const int cgx = Bc / 8, cgy = Bc / 4;
+                            sd = group_sum<PC>(sd, cgx, cgy);
+                            sdd = group_sum<PC>(sdd, cgx, cgy);
+                            sdr = group_sum<PC>(sdr, cgx, cgy);
+                            sub[0].ncdr = ((long long)sdr << lg2n4) - (long long)sd * sub[0].sr;
+                            sub[0].ncdd = ((long long)sdd << lg2n4) - (long long)sd * sd;
+                        } else {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                int sd = 0, sdd = 0, sdr = 0;
+                                if (valid)
+                                    half_moments<NP>(d4e, (dxa >> 1) + u0 + 4 * h - c_base, (dya >> 1) + v0 - r_base, rw,
+                                                     h, sd, sdd, sdr);
+                                sub[h].ncdr = ((long long)sdr << 4) - (long long)sd * sub[h].sr;
+                                sub[h].ncdd = ((long long)sdd << 4) - (long long)sd * sd;
+                            }
+                        }
+                    }
                     bool ok_lane;
                     if (Bc >= 8) {
                         const int cbx = (8 * pc) / Bc, cby = (4 * pr) / Bc;
                         const int kk = (cbx & 1) | ((cby & 1) << 1);
                         int bit;
-                        ok_lane = fit_phase2_sub(ch[0], lg2n4, O[kk], c0, c1, thr_p2, bit);
+                        ok_lane = fit_phase2_sub(sub[0], lg2n4, O[kk], c0, c1, thr_p2, bit);
                         const uint32_t bits = __ballot_sync(FULL, bit);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
@@ -320,8 +350,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
                     } else {
                         const bool top = (pr & 1) == 0;
                         int b0, b1;
-                        const bool ok0 = fit_phase2_sub(ch[0], 4, O[top ? 0 : 2], c0, c1, thr_p2, b0);
-                        const bool ok1 = fit_phase2_sub(ch[1], 4, O[top ? 1 : 3], c0, c1, thr_p2, b1);
+                        const bool ok0 = fit_phase2_sub(sub[0], 4, O[top ? 0 : 2], c0, c1, thr_p2, b0);
+                        const bool ok1 = fit_phase2_sub(sub[1], 4, O[top ? 1 : 3], c0, c1, thr_p2, b1);
                         ok_lane = ok0 && ok1;
                         const int my = b0 | (b1 << 1);
                         const int other = __shfl_xor_sync(FULL, my, PC);
@@ -661,6 +691,7 @@ extern "C" int fic_encode_noalloc(const uint8_t *d_img, int width, int height, c
     d.bmin = p->bmin;
     d.L = L;
     d.phase2 = p->phase2 ? 1 : 0;
+    d.phase2_domain = p->phase2_domain ? 1 : 0;
     d.s_bits = p->s_bits;
     d.o_bits = p->o_bits;
     d.local_radius = p->local_radius;

@@ -33,6 +33,7 @@ struct EncDesc {
     int32_t mode, bmin, L, phase2;
     int32_t s_bits, o_bits;
     int32_t local_radius, local_step;
+    int32_t phase2_domain;  // 0: sub-blocks' own centred domains, 1: parent-domain quadrants
     const TmaMap *map;   // 2-D tensor map of the image (box: the strip's domain window)
     int32_t boxw;        // box width in pixels (= row pitch of the staged window)
     int32_t bmax;
@@ -79,6 +80,7 @@ struct DecDesc {
     int32_t W, H;
     int32_t tw, th, spr, strip_base, nstrips;
     int32_t mode, bmin, L, s_bits, o_bits;
+    int32_t phase2_domain;  // as in fic_params
     // 2x2-sum iteration (centred streams): ping-pong (W/2) x (H/2) images of
     // 2x2 sums, their tensor maps, and the stream's info block for errors
     uint16_t *d4[2];

@@ -43,6 +43,7 @@ class Params(ctypes.Structure):
         ("thr_rms", ctypes.c_double * 4), ("s_bits", ctypes.c_int32), ("o_bits", ctypes.c_int32),
         ("phase2", ctypes.c_int32), ("local_radius", ctypes.c_int32), ("local_step", ctypes.c_int32),
         ("dom_step", ctypes.c_int32), ("isometries", ctypes.c_int32), ("engine", ctypes.c_int32),
+        ("phase2_domain", ctypes.c_int32),
     ]
 
 
@@ -56,7 +57,7 @@ class StreamC(ctypes.Structure):
 
 
 def params(mode="mns", bmax=32, bmin=4, thr=8.0, s_bits=5, o_bits=7, phase2=True,
-           local_radius=16, local_step=4, dom_step=4, isometries=8, engine=0) -> Params:
+           local_radius=16, local_step=4, dom_step=4, isometries=8, engine=0, phase2_domain=0) -> Params:
     p = Params()
     p.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     p.bmax, p.bmin = int(bmax), int(bmin)
@@ -68,6 +69,7 @@ def params(mode="mns", bmax=32, bmin=4, thr=8.0, s_bits=5, o_bits=7, phase2=True
     p.phase2 = 1 if phase2 else 0
     p.local_radius, p.local_step = int(local_radius), int(local_step)
     p.dom_step, p.isometries = int(dom_step), int(isometries)
+    p.phase2_domain = int(phase2_domain)
     p.engine = int(engine)
     return p
 

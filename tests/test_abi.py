@@ -57,7 +57,7 @@ def test_host_only_calls(libfic):
 def test_record_layout_matches_header():
     from paper_1501_02894_gb300 import fic
     assert fic.RECORD_DTYPE.itemsize == 16
-    assert ctypes.sizeof(fic.Params) == 4 * 3 + 4 + 8 * 4 + 4 * 8  # padding after bmin
+    assert ctypes.sizeof(fic.Params) == 4 * 3 + 4 + 8 * 4 + 4 * 9 + 4  # padding after bmin and at the end
 
 
 def test_server_structs_and_host_checks(libfic):

@@ -72,7 +72,7 @@ def test_autotune_picks_a_candidate_and_stays_exact(fic, batch):
     assert res["best_ms"] == pytest.approx(min(t["ms"] for t in res["trials"]), rel=1e-4)
     dplan = fic.DecodePlan(plan.outs)
     dres = dplan.autotune(8, reps=3)
-    assert len(dres["trials"]) == 8 and dres["best"]["dec_ctas_per_sm"] >= 1
+    assert len(dres["trials"]) == 4 and 1 <= dres["best"]["dec_ctas_per_sm"] <= 4
     plan.run()
     dplan.run(8)
     _check(fic, plan, dplan, want)

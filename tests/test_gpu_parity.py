@@ -243,3 +243,19 @@ def test_decode_paths_agree(fic, orc):
     pc, opc = _pair(fic, orc, "mns", 16, 4, 6.0)
     sc = fic.fic_encode(torch.from_numpy(c).cuda(), pc)
     assert np.array_equal(fic.fic_decode(sc, 5).cpu().numpy(), orc.decode(orc.encode(c, opc)[0], 64, 128, opc, 5))
+
+
+# ---------------------------------------------------------------------------
+# Phase 2 with the other domain reading: quadrants of the parent's domain
+
+@pytest.mark.parametrize("img_fn,bmax,bmin,thr", [
+    (lambda: synth.cfg1_image(), 16, 4, 8.0),
+    (lambda: synth.gaussian_scene(512, 1), 32, 4, 6.0),
+    (lambda: synth.gaussian_scene(256, 44), 32, 8, 10.0),
+    (lambda: synth.voronoi(256, 101), 16, 4, 4.0),
+])
+def test_phase2_parent_quadrants(fic, orc, img_fn, bmax, bmin, thr):
+    img = img_fn()
+    got = _check_image(fic, orc, img, "mns", bmax, bmin, thr, iters=6, phase2_domain=1)
+    if bmax == 16 and thr == 8.0:  # this image keeps a phase-2 leaf under the quadrant reading
+        assert (got["records"]["phase"] == 2).any()
