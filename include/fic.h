@@ -240,6 +240,8 @@ typedef struct fic_tuning {
     int32_t enc_ctas_per_sm; /* encoder CTAs per SM; 0 = as many as fit */
     int32_t enc_dynamic;     /* 1: strips taken from an atomic counter; 0: static grid stride */
     int32_t dec_ctas_per_sm; /* decoder iteration kernel CTAs per SM; 0 = as many as fit */
+    int32_t enc_fused_pack;  /* 1: the encoder warp that finishes a 32-strip chunk packs it into
+                                the stream (no pack launch); 0: a separate pack kernel */
 } fic_tuning;
 
 FIC_API int fic_plan_get_tuning(const fic_plan *plan, fic_tuning *t);
@@ -247,14 +249,14 @@ FIC_API int fic_plan_get_tuning(const fic_plan *plan, fic_tuning *t);
 FIC_API int fic_plan_set_tuning(fic_plan *plan, const fic_tuning *t);
 /* Time every candidate mapping on the plan's own batch and keep the fastest.
  * Encode plans try warps {8, 4} x CTAs per SM {1, 2, ..., max} x schedule
- * {static, dynamic}; decode plans try CTAs per SM {1, 2, 3, 4} with `iters`
+ * {static, dynamic} x packing {fused, separate}; decode plans try CTAs per SM {1, 2, 3, 4} with `iters`
  * iterations.  Each candidate runs once untimed, then `reps` times between
  * CUDA events on `stream`; the score is the median.  Synchronous: returns
  * after the last run with the plan's outputs written (identical for every
  * candidate).  *best and *best_ms (either may be NULL) receive the choice
  * and its median time; `trace` (may be NULL) receives up to `trace_cap`
- * (candidate, ms) rows as 5 floats each: enc_warps, enc_ctas_per_sm,
- * enc_dynamic, dec_ctas_per_sm, ms, and *ntrace their number.
+ * (candidate, ms) rows as 6 floats each: enc_warps, enc_ctas_per_sm,
+ * enc_dynamic, dec_ctas_per_sm, enc_fused_pack, ms, and *ntrace their number.
  * Other encode families return FIC_EBADPARAM. */
 FIC_API int fic_plan_autotune(fic_plan *plan, int iters, int reps, void *stream, fic_tuning *best,
                               float *best_ms, float *trace, int trace_cap, int *ntrace);

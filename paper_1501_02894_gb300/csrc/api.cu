@@ -328,7 +328,7 @@ static EncLayout enc_layout(int count, size_t strips, size_t chunks) {
     L.descs = L.maps + align_up(sizeof(TmaMap) * (size_t)count);
     L.stats = L.descs + align_up(sizeof(EncDesc) * (size_t)count);
     L.pstatus = L.stats + align_up(8 * strips);
-    L.slots = L.pstatus + align_up(4 * (chunks + 1));
+    L.slots = L.pstatus + align_up(4 * (2 * chunks + 1));  // status, strip counter, chunk counters
     L.total = L.slots + align_up(sizeof(fic_record) * 64 * strips);
     return L;
 }
@@ -542,18 +542,21 @@ int fic_plan_get_tuning(const fic_plan *pl, fic_tuning *t) {
     t->enc_ctas_per_sm = pl->etune.ctas_per_sm;
     t->enc_dynamic = pl->etune.dynamic;
     t->dec_ctas_per_sm = pl->dtune.ctas_per_sm;
+    t->enc_fused_pack = pl->etune.fused_pack;
     return FIC_OK;
 }
 
 int fic_plan_set_tuning(fic_plan *pl, const fic_tuning *t) {
     if (!pl || !t) return FIC_EBADPARAM;
     if ((t->enc_warps != 8 && t->enc_warps != 4) || t->enc_ctas_per_sm < 0 || t->enc_ctas_per_sm > 64 ||
-        (t->enc_dynamic != 0 && t->enc_dynamic != 1) || t->dec_ctas_per_sm < 0 || t->dec_ctas_per_sm > 64)
+        (t->enc_dynamic != 0 && t->enc_dynamic != 1) || t->dec_ctas_per_sm < 0 || t->dec_ctas_per_sm > 64 ||
+        (t->enc_fused_pack != 0 && t->enc_fused_pack != 1))
         return FIC_EBADPARAM;
     pl->etune.warps = t->enc_warps;
     pl->etune.ctas_per_sm = t->enc_ctas_per_sm;
     pl->etune.dynamic = t->enc_dynamic;
     pl->dtune.ctas_per_sm = t->dec_ctas_per_sm;
+    pl->etune.fused_pack = t->enc_fused_pack;
     return FIC_OK;
 }
 
@@ -570,10 +573,12 @@ int fic_plan_autotune(fic_plan *pl, int iters, int reps, void *stream, fic_tunin
     if (pl->kind == 0) {
         for (int w : {8, 4})
             for (int k = 1; k <= (w == 8 ? 3 : 4); ++k)
-                for (int dyn = 0; dyn <= 1; ++dyn) cands.push_back(fic_tuning{w, k, dyn, cur.dec_ctas_per_sm});
+                for (int dyn = 0; dyn <= 1; ++dyn)
+                    for (int fp = 1; fp >= 0; --fp) cands.push_back(fic_tuning{w, k, dyn, cur.dec_ctas_per_sm, fp});
     } else {
         // the iteration kernels are built for 4 resident CTAs of 8 warps
-        for (int k = 1; k <= 4; ++k) cands.push_back(fic_tuning{cur.enc_warps, cur.enc_ctas_per_sm, cur.enc_dynamic, k});
+        for (int k = 1; k <= 4; ++k)
+            cands.push_back(fic_tuning{cur.enc_warps, cur.enc_ctas_per_sm, cur.enc_dynamic, k, cur.enc_fused_pack});
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -598,12 +603,13 @@ int fic_plan_autotune(fic_plan *pl, int iters, int reps, void *stream, fic_tunin
         std::sort(times.begin(), times.end());
         const float med = times[(size_t)reps / 2];
         if (trace && nt < trace_cap) {
-            float *row = trace + 5 * nt;
+            float *row = trace + 6 * nt;
             row[0] = (float)cands[c].enc_warps;
             row[1] = (float)cands[c].enc_ctas_per_sm;
             row[2] = (float)cands[c].enc_dynamic;
             row[3] = (float)cands[c].dec_ctas_per_sm;
-            row[4] = med;
+            row[4] = (float)cands[c].enc_fused_pack;
+            row[5] = med;
             ++nt;
         }
         if (bi < 0 || med < bms) {

@@ -30,6 +30,7 @@
 // the stream in place with a decoupled look-back over the strips (bounded
 // spin), so its only scratch is one status word per strip.
 #include "encode_common.cuh"
+#include "pack.cuh"
 
 namespace fic {
 
@@ -60,7 +61,8 @@ constexpr uint32_t kAgg = 1u << 30, kIncl = 2u << 30, kValMask = (1u << 30) - 1;
 template <int BMAX, bool SLOTS, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
     mns_encode_kernel(const EncDesc *__restrict__ descs, int count, int total_strips,
-                      uint32_t *__restrict__ status, uint32_t *__restrict__ ticket, int total_chunks, int dyn) {
+                      uint32_t *__restrict__ status, uint32_t *__restrict__ ticket, int total_chunks, int dyn,
+                      int fused) {
     using G = Geom<BMAX>;
     constexpr int PC = G::PC, NP = G::NP;
     constexpr int UPR = BMAX == 32 ? 4 : (BMAX == 16 ? 8 : 16);
@@ -79,11 +81,14 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
     const unsigned FULL = 0xffffffffu;
     if (count <= kImgTable)
         for (int i = threadIdx.x; i < count; i += blockDim.x) s_base[i] = descs[i].strip_base;
-    if (SLOTS) {
-        // clear the pack kernel's look-back words (it runs after this kernel)
+    if (SLOTS && !fused) {
+        // clear the pack kernel's look-back words (it runs after this kernel;
+        // fused packing needs them zero before the launch instead)
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total_chunks; i += gridDim.x * blockDim.x)
             status[i] = 0u;
     }
+    // fused packing: per-chunk count of finished strips, after the ticket
+    uint32_t *chunk_done = status + total_chunks + 1;
     if (lane == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
@@ -421,6 +426,19 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
                 D.tile_off[top0 + lane_top] = (uint32_t)__popcll(mask & ((1ull << (lane_top * cpt)) - 1ull));
             }
             if (lane == 0) D.stats[s] = make_uint2((uint32_t)cnt, ftot & 0x7fffffffu);
+            if (fused) {
+                // the warp that finishes a chunk's last strip packs the chunk
+                __syncwarp();
+                __threadfence();
+                const int cl = s >> 5;
+                uint32_t done = 0;
+                if (lane == 0) done = atomicAdd(chunk_done + D.chunk_base + cl, 1u) + 1u;
+                done = __shfl_sync(FULL, done, 0);
+                if ((int)done == min(32, D.nstrips - cl * 32)) {
+                    __threadfence();
+                    pack_chunk_warp(D, cl, status, lane);
+                }
+            }
             g = ticketed ? __shfl_sync(FULL, g_next, 0) : g_next;
             g_next = g_after;
             continue;
@@ -532,7 +550,8 @@ static int mns_occupancy(int &sms) {
 
 template <int BMAX, bool SLOTS, int NW>
 static cudaError_t launch_t(const EncDesc *descs, int count, int total_strips, uint32_t *status,
-                            uint32_t *ticket, int total_chunks, int ctas_per_sm, int dyn, cudaStream_t st) {
+                            uint32_t *ticket, int total_chunks, int ctas_per_sm, int dyn, int fused,
+                            cudaStream_t st) {
     int sms = 0;
     const int per = mns_occupancy<BMAX, SLOTS, NW>(sms);
     if (per == 0) return cudaErrorInvalidValue;
@@ -540,7 +559,7 @@ static cudaError_t launch_t(const EncDesc *descs, int count, int total_strips, u
     const int need = (total_strips + NW - 1) / NW;
     const int grid = need < sms * k ? need : sms * k;
     mns_encode_kernel<BMAX, SLOTS, NW><<<grid, NW * 32, mns_smem_bytes(BMAX, NW), st>>>(
-        descs, count, total_strips, status, ticket, total_chunks, dyn);
+        descs, count, total_strips, status, ticket, total_chunks, dyn, fused);
     stage_mark(st, "mns_encode_kernel");
     return cudaGetLastError();
 }
@@ -563,9 +582,9 @@ cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int t
     cudaError_t e = launch_init(d_descs, count, total_strips, status, ticket, st);
     if (e != cudaSuccess) return e;
     switch (bmax) {
-    case 32: return launch_t<32, false, kWarps>(d_descs, count, total_strips, status, ticket, 0, 0, 1, st);
-    case 16: return launch_t<16, false, kWarps>(d_descs, count, total_strips, status, ticket, 0, 0, 1, st);
-    case 8: return launch_t<8, false, kWarps>(d_descs, count, total_strips, status, ticket, 0, 0, 1, st);
+    case 32: return launch_t<32, false, kWarps>(d_descs, count, total_strips, status, ticket, 0, 0, 1, 0, st);
+    case 16: return launch_t<16, false, kWarps>(d_descs, count, total_strips, status, ticket, 0, 0, 1, 0, st);
+    case 8: return launch_t<8, false, kWarps>(d_descs, count, total_strips, status, ticket, 0, 0, 1, 0, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -579,12 +598,18 @@ cudaError_t launch_pack(const EncDesc *d_descs, int count, int total_chunks, uin
 cudaError_t launch_mns_encode_slots(int bmax, const EncDesc *d_descs, int count, int total_strips, int total_chunks,
                                     uint32_t *pack_status, uint32_t *ticket, const EncTune &tune, cudaStream_t st) {
     cudaError_t e;
-    const int k = tune.ctas_per_sm, dyn = tune.dynamic ? 1 : 0;
+    const int k = tune.ctas_per_sm, dyn = tune.dynamic ? 1 : 0, fused = tune.fused_pack ? 1 : 0;
     uint32_t *tk = dyn ? ticket : nullptr;
     const bool w4 = tune.warps == 4;
-#define FIC_SLOTS_LAUNCH(B)                                                                                    \
-    e = w4 ? launch_t<B, true, 4>(d_descs, count, total_strips, pack_status, tk, total_chunks, k, dyn, st)       \
-           : launch_t<B, true, kWarps>(d_descs, count, total_strips, pack_status, tk, total_chunks, k, dyn, st)
+    if (fused) {
+        // look-back status, strip counter and chunk counters start at zero
+        // (status, ticket and counters are contiguous in the workspace)
+        e = cudaMemsetAsync(pack_status, 0, (2 * (size_t)total_chunks + 1) * sizeof(uint32_t), st);
+        if (e != cudaSuccess) return e;
+    }
+#define FIC_SLOTS_LAUNCH(B)                                                                                       \
+    e = w4 ? launch_t<B, true, 4>(d_descs, count, total_strips, pack_status, tk, total_chunks, k, dyn, fused, st)   \
+           : launch_t<B, true, kWarps>(d_descs, count, total_strips, pack_status, tk, total_chunks, k, dyn, fused, st)
     switch (bmax) {
     case 32: FIC_SLOTS_LAUNCH(32); break;
     case 16: FIC_SLOTS_LAUNCH(16); break;
@@ -592,7 +617,7 @@ cudaError_t launch_mns_encode_slots(int bmax, const EncDesc *d_descs, int count,
     default: return cudaErrorInvalidValue;
     }
 #undef FIC_SLOTS_LAUNCH
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || fused) return e;
     return launch_pack(d_descs, count, total_chunks, pack_status, tk, st);
 }
 

@@ -51,8 +51,8 @@ def test_every_mapping_gives_the_same_output(fic, batch):
     dplan = fic.DecodePlan(plan.outs)
     for warps, kmax in ((8, 3), (4, 4)):
         for k in range(0, kmax + 1):
-            for dyn in (0, 1):
-                plan.set_tuning(enc_warps=warps, enc_ctas_per_sm=k, enc_dynamic=dyn)
+            for dyn, fp in ((0, 0), (1, 0), (0, 1), (1, 1)):
+                plan.set_tuning(enc_warps=warps, enc_ctas_per_sm=k, enc_dynamic=dyn, enc_fused_pack=fp)
                 for st in plan.outs:  # stale results must not survive
                     st.records.zero_()
                 plan.run()
@@ -67,7 +67,7 @@ def test_autotune_picks_a_candidate_and_stays_exact(fic, batch):
     p = fic.params("mns", 32, 4, 8.0)
     plan = fic.EncodePlan([torch.from_numpy(im).cuda() for im in imgs], p)
     res = plan.autotune(reps=3)
-    assert len(res["trials"]) == 2 * 3 + 4 * 2
+    assert len(res["trials"]) == 2 * 2 * 3 + 2 * 2 * 4
     assert res["best"] == plan.tuning
     assert res["best_ms"] == pytest.approx(min(t["ms"] for t in res["trials"]), rel=1e-4)
     dplan = fic.DecodePlan(plan.outs)
