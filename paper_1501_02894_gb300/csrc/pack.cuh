@@ -83,10 +83,12 @@ __device__ __forceinline__ bool pack_chunk_warp(const EncDesc &D, int cl, uint32
 #pragma unroll
         for (int m = 16; m >= 1; m >>= 1) fsum += __shfl_xor_sync(FULL, fsum, m);
         err = __reduce_or_sync(FULL, err);
+        if (ok && prefix + tot > (uint32_t)D.capacity) err |= FIC_DEVERR_CAPACITY;
         if (lane == 0) {
+            // the info block is written here only (it may hold anything before)
             D.info[FIC_INFO_FITS_LO] = (uint32_t)fsum;
             D.info[FIC_INFO_FITS_HI] = (uint32_t)(fsum >> 32);
-            if (err) raise_error(D.info, err);
+            D.info[FIC_INFO_ERROR] = err;
             if (ok) {
                 D.tile_off[D.tw * D.th] = prefix + tot;
                 D.info[FIC_INFO_RECORDS] = prefix + tot;
@@ -96,15 +98,13 @@ __device__ __forceinline__ bool pack_chunk_warp(const EncDesc &D, int cl, uint32
         raise_error(D.info, FIC_DEVERR_TIMEOUT);
     }
     if (!ok) return false;
+    // records past the capacity are dropped (the image's last chunk reports it)
     // copy the 32 slots: lane-strided over each slot's records
     for (int j = 0; j < 32 && cl * 32 + j < D.nstrips; ++j) {
         const uint32_t n = __shfl_sync(FULL, cnt, j), off = __shfl_sync(FULL, excl, j);
         const fic_record *src = D.slots + (size_t)(cl * 32 + j) * 64;
         for (uint32_t k = lane; k < n; k += 32) {
-            if (off + k < (uint32_t)D.capacity)
-                *reinterpret_cast<uint4 *>(D.rec + off + k) = ld_cg4(src + k);
-            else
-                raise_error(D.info, FIC_DEVERR_CAPACITY);
+            if (off + k < (uint32_t)D.capacity) *reinterpret_cast<uint4 *>(D.rec + off + k) = ld_cg4(src + k);
         }
     }
     return true;
