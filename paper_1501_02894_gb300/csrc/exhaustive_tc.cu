@@ -249,6 +249,32 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         best.thr = live ? -1.f : __int_as_float(0x7f800000);  // everything passes / dead rows never pass
         best.d = -1;
         best.k = 0;
+        if (live) {
+            // seed with the grid domain nearest the range's centred domain: a
+            // good candidate from the start lowers the screen's threshold at
+            // once (ties still go to the smaller domain index, so the result
+            // does not depend on the seed)
+            const int rx = (r % E.nrx) * kExhB, ry = (r / E.nrx) * kExhB;
+            const int cx = clampi(rx - kExhB / 2, 0, E.W - 2 * kExhB), cy = clampi(ry - kExhB / 2, 0, E.H - 2 * kExhB);
+            const int ix = min((cx + E.step / 2) / E.step, E.ndx - 1), iy = min((cy + E.step / 2) / E.step, E.ndy - 1);
+            const int d0 = iy * E.ndx + ix;
+            const uint4 *a = reinterpret_cast<const uint4 *>(E.afp16 + (size_t)row * kExhK);
+            const uint4 *bq = reinterpret_cast<const uint4 *>(E.dfp16 + (size_t)d0 * kExhK);
+            float acc = 0.f;  // integer products and sums below 2^24: exact
+#pragma unroll
+            for (int i = 0; i < kExhK / 8; ++i) {
+                const uint4 av = __ldg(a + i), bv = __ldg(bq + i);
+                const uint32_t aw[4] = {av.x, av.y, av.z, av.w}, bw[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float2 fa = __half22float2(*reinterpret_cast<const __half2 *>(&aw[j]));
+                    const float2 fb = __half22float2(*reinterpret_cast<const __half2 *>(&bw[j]));
+                    acc = fmaf(fa.x, fb.x, acc);
+                    acc = fmaf(fa.y, fb.y, acc);
+                }
+            }
+            best = tc_exact(best, d0, acc, sr, __ldg(E.dstat + d0), E.s_bits);
+        }
         // screening constants of each tile: staged in shared memory by the
         // epilogue threads (tile n+1's load is in flight while tile n is
         // screened); one named barrier per tile, which also makes leaving

@@ -67,7 +67,8 @@ struct EncTune {
     int warps = 8;        // warps per CTA: 8 or 4 (one strip per warp at a time)
     int ctas_per_sm = 0;  // resident CTAs per SM; 0 = the occupancy limit
     int dynamic = 0;      // 1: strips from an atomic counter, 0: static grid stride
-    int fused_pack = 1;   // 1: the warp finishing a chunk packs it; 0: a separate pack kernel
+    int fused_pack = 0;   // 1: the warp finishing a chunk packs it; 0: a separate pack kernel
+                          // (measured faster: the per-strip release fence costs more than the launch)
 };
 struct DecTune {
     int ctas_per_sm = 0;  // resident CTAs per SM of the iteration kernel; 0 = the occupancy limit
