@@ -332,6 +332,16 @@ FIC_API int fic_rescale_params(int width, int height, const fic_params *p, int s
                                int *height_out, fic_params *p_out);
 FIC_API int fic_stream_rescale(const fic_stream *in, int shift, fic_stream *out, void *stream);
 
+/* ---- Self-test of the bounded device waits ----
+ * Every wait in the library's kernels (look-back spins, mbarrier waits for
+ * TMA and tensor-core completions) gives up after an iteration limit and
+ * reports FIC_DEVERR_TIMEOUT instead of hanging.  This runs the same two
+ * helpers on a word that nothing writes (d_never: device memory holding 0)
+ * and on an mbarrier whose announced transfer never comes; d_out (3 uint32)
+ * receives 1, 1 when both gave up, and the spin's iteration count.  Takes
+ * about a second; the context stays usable. */
+FIC_API int fic_selftest_waits(const uint32_t *d_never, uint32_t *d_out, void *stream);
+
 /* ---- Position statistics (Section 2, Figs. 2 and 3) ----
  * Histograms of x_d - x_r and y_d - y_r over the stream's records: the
  * offset between each range block and its domain block.  hx has 2*width

@@ -194,14 +194,21 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
 
     const uint32_t rbeg = D.tile_off[top0], rend = D.tile_off[top0 + nvalid];
     const int nrec = min((int)(rend - rbeg), 64);
+    // the strip's leaves tile its (at most 64) bmin cells in canonical order:
+    // a 64-bit mask of their first cells ranks any cell's covering leaf
     __syncwarp();
+    unsigned long long occ = 0;
     for (int i = lane; i < nrec; i += 32) {
         const uint4 r = *reinterpret_cast<const uint4 *>(D.rec + rbeg + i);
         recs[i] = r;
         const int x = (int)(r.x & 0xffffu), y = (int)(r.x >> 16);
         const int lt = x / BMAX - sc * G::TOPS;
-        keys[i] = (uint8_t)(lt * cpt + (int)dmorton3((x % BMAX) / bmin, (y % BMAX) / bmin));
+        const int key = min(lt * cpt + (int)dmorton3((x % BMAX) / bmin, (y % BMAX) / bmin), 63);
+        occ |= 1ull << key;
     }
+    occ = ((unsigned long long)__reduce_or_sync(0xffffffffu, (uint32_t)(occ >> 32)) << 32) |
+          __reduce_or_sync(0xffffffffu, (uint32_t)occ);
+    (void)keys;
     __syncwarp();
     uint32_t fw[2] = {0u, 0u}, gw[2] = {0u, 0u}, hw[2] = {0u, 0u};
     int Ow[2] = {0, 0};
@@ -210,14 +217,10 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
         if (!valid || nrec <= 0) continue;
         const int px = 8 * pc + 4 * h, py = 4 * pr;  // in strip
         const int tx = px - lane_top * BMAX;
-        const int key = lane_top * cpt + (int)dmorton3(tx / bmin, py / bmin);
-        int lo = 0, hi = nrec - 1;
-        while (lo < hi) {  // last record with keys[i] <= key
-            const int mid = (lo + hi + 1) >> 1;
-            if ((int)keys[mid] <= key) lo = mid;
-            else hi = mid - 1;
-        }
-        const uint4 r = recs[lo];
+        const int key = min(lane_top * cpt + (int)dmorton3(tx / bmin, py / bmin), 63);
+        const unsigned long long upto = key == 63 ? ~0ull : ((2ull << key) - 1ull);
+        const int lo = max(__popcll(occ & upto) - 1, 0);  // last leaf starting at or before the cell
+        const uint4 r = recs[min(lo, nrec - 1)];
         const int x = (int)(r.x & 0xffffu), y = (int)(r.x >> 16);
         const int level = (int)(r.y & 0xffu), phase = (int)((r.y >> 8) & 0xffu);
         const int k = (int)((r.y >> 16) & 0xffu), q = (int)(r.y >> 24);

@@ -123,3 +123,34 @@ extern "C" int fic_offset_histogram(const fic_stream *st, uint32_t *d_hx, uint32
         st->records, st->info, st->capacity, st->width, st->height, d_hx, d_hy);
     return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
 }
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded device waits every kernel uses: a spin on a word
+// that nothing writes and an mbarrier wait for a transfer that never comes
+// must both give up after their iteration limits and report it, leaving the
+// context usable.  out[0] = 1 when the word spin gave up, out[1] = 1 when the
+// mbarrier wait gave up, out[2] = the spin's iterations.
+namespace fic {
+__global__ void selftest_waits_kernel(const uint32_t *never, uint32_t *out, unsigned spin_limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    unsigned it = 0;
+    uint32_t v = ld_volatile(never);
+    while (v == 0u && ++it < spin_limit) {
+        __nanosleep(32);
+        v = ld_volatile(never);
+    }
+    out[0] = v == 0u ? 1u : 0u;
+    out[2] = it;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, 16u);  // 16 bytes announced, none sent
+    out[1] = mbar_wait(&bar, 0u, kMbarLimit) ? 0u : 1u;
+}
+}  // namespace fic
+
+extern "C" int fic_selftest_waits(const uint32_t *d_never, uint32_t *d_out, void *stream) {
+    if (!d_never || !d_out) return FIC_EBADPARAM;
+    fic::selftest_waits_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(d_never, d_out, fic::kSpinLimit);
+    return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+}

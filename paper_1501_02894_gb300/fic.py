@@ -154,6 +154,7 @@ def lib():
         L.fic_server_get_stats.argtypes = [vp, P(ServerStats)]
         L.fic_server_destroy.argtypes = [vp]
         L.fic_offset_histogram.argtypes = [P(StreamC), vp, vp, vp]
+        L.fic_selftest_waits.argtypes = [vp, vp, vp]
         L.fic_validate_stream.argtypes = [ctypes.c_int, ctypes.c_int, P(Params)]
         L.fic_rescale_params.argtypes = [ctypes.c_int, ctypes.c_int, P(Params), ctypes.c_int, P(ctypes.c_int),
                                          P(ctypes.c_int), P(Params)]
