@@ -7,10 +7,11 @@
 // one image: warp 0 scans their counts and looks back over the image's
 // earlier chunks (their counts are already final, so the look-back resolves
 // in a few rounds), turns the encoder's per-strip tile offsets into stream
-// offsets and adds the fit counts to the stream's info block; then all eight
-// warps copy the 32 slots to their stream offsets with coalesced 16-byte
-// loads and stores.  The info block of each stream (record count, fits,
-// device error bits) is written here, by the image's last chunk.
+// offsets and adds the fit counts to the stream's info block; meanwhile the
+// other seven warps load the 32 slots' records into registers (coalesced
+// 16-byte loads), and store them at their stream offsets once warp 0 has
+// them.  The info block of each stream (record count, fits, device error
+// bits) is written here, by the image's last chunk.
 #include "fic_internal.cuh"
 
 namespace fic {
@@ -26,8 +27,8 @@ __global__ void __launch_bounds__(kPackWarps * 32)
     pack_kernel(const EncDesc *__restrict__ descs, int count, int total_chunks, uint32_t *__restrict__ pstatus,
                 uint32_t *__restrict__ ticket) {
     __shared__ int s_cb[kImgTable];
-    __shared__ int s_img, s_ok;
-    __shared__ uint32_t s_cnt[32], s_off[32];
+    __shared__ int s_ok;
+    __shared__ uint32_t s_off[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned FULL = 0xffffffffu;
     const int c = blockIdx.x;
@@ -37,14 +38,37 @@ __global__ void __launch_bounds__(kPackWarps * 32)
     if (count <= kImgTable)
         for (int i = threadIdx.x; i < count; i += blockDim.x) s_cb[i] = descs[i].chunk_base;
     __syncthreads();
-    if (warp == 0) {
-        int lo = 0, hi = count - 1;
+    // the chunk's image (every warp: the copy warps prefetch below)
+    int lo = 0;
+    {
+        int hi = count - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             const int cb = count <= kImgTable ? s_cb[mid] : descs[mid].chunk_base;
             if (cb <= c) lo = mid;
             else hi = mid - 1;
         }
+    }
+    // warps 1..7 load their slots' records while warp 0 resolves the offsets
+    constexpr int kPer = (32 + kPackWarps - 2) / (kPackWarps - 1);  // slots per copy warp (5)
+    uint4 pre[kPer][2];
+    uint32_t pre_n[kPer];
+    if (warp > 0) {
+        const EncDesc &D = descs[lo];
+        const int cl = c - D.chunk_base;
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            const int j = (warp - 1) + (kPackWarps - 1) * t;
+            const int sidx = cl * 32 + j;
+            const uint32_t n = (j < 32 && sidx < D.nstrips) ? D.stats[sidx].x : 0u;
+            pre_n[t] = n;
+            const fic_record *src = D.slots + (size_t)sidx * kSlotRecs;
+            pre[t][0] = (uint32_t)lane < n ? *reinterpret_cast<const uint4 *>(src + lane) : make_uint4(0u, 0u, 0u, 0u);
+            pre[t][1] = (uint32_t)lane + 32u < n ? *reinterpret_cast<const uint4 *>(src + lane + 32)
+                                                : make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    if (warp == 0) {
         const EncDesc &D = descs[lo];
         const int cl = c - D.chunk_base;
         const int s = cl * 32 + lane;
@@ -88,12 +112,8 @@ __global__ void __launch_bounds__(kPackWarps * 32)
             if (lane == 0 && ok) st_volatile(pstatus + c, kPIncl | (prefix + tot));
         }
         const uint32_t excl = prefix + incl - cnt;
-        s_cnt[lane] = ok ? cnt : 0u;
         s_off[lane] = excl;
-        if (lane == 0) {
-            s_img = lo;
-            s_ok = ok;
-        }
+        if (lane == 0) s_ok = ok;
         if (ok && in) {
             // tile offsets: the encoder stored offsets inside the strip
             const int tops = 1024 / (D.bmax * D.bmax);
@@ -129,18 +149,19 @@ __global__ void __launch_bounds__(kPackWarps * 32)
         }
     }
     __syncthreads();
-    if (!s_ok) return;
-    // copy: every warp takes four of the 32 slots
-    const EncDesc &D = descs[s_img];
-    const int cl = c - D.chunk_base;
-    for (int j = warp; j < 32; j += kPackWarps) {
-        const uint32_t n = s_cnt[j], off = s_off[j];
-        const fic_record *src = D.slots + (size_t)(cl * 32 + j) * kSlotRecs;
-        for (uint32_t k = lane; k < n; k += 32) {
-            // records past the capacity are dropped (the image's last chunk reports it)
-            if (off + k < (uint32_t)D.capacity)
-                *reinterpret_cast<uint4 *>(D.rec + off + k) = *reinterpret_cast<const uint4 *>(src + k);
-        }
+    if (!s_ok || warp == 0) return;
+    // store the prefetched records at their stream offsets (records past
+    // the capacity are dropped; the image's last chunk reports it)
+    const EncDesc &D = descs[lo];
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+        const int j = (warp - 1) + (kPackWarps - 1) * t;
+        if (j >= 32) break;
+        const uint32_t n = pre_n[t], off = s_off[j];
+        if ((uint32_t)lane < n && off + lane < (uint32_t)D.capacity)
+            *reinterpret_cast<uint4 *>(D.rec + off + lane) = pre[t][0];
+        if ((uint32_t)lane + 32u < n && off + lane + 32 < (uint32_t)D.capacity)
+            *reinterpret_cast<uint4 *>(D.rec + off + lane + 32) = pre[t][1];
     }
 }
 
