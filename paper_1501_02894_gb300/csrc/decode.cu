@@ -185,6 +185,8 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
     const int cpt_side = BMAX / bmin, cpt = cpt_side * cpt_side;
     const bool centred = (D.mode == FIC_NOSEARCH || D.mode == FIC_MNS);
     const int ko1 = (1 << D.o_bits) - 1;
+    // L(q) = floor((510 q + ko1) / (2 ko1)) by a multiply-high (exact for q <= ko1 <= 255)
+    const uint32_t lmagic = (uint32_t)((0x100000000ULL + 2 * ko1 - 1) / (2 * ko1));
     const int rx0 = clampi(sx0 - BMAX / 2, 0, W - 2 * BMAX);
     const int xl = sx0 + (nvalid - 1) * BMAX;
     const int rx1 = clampi(xl - BMAX / 2, 0, W - 2 * BMAX) + 2 * BMAX;
@@ -225,7 +227,7 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
         const int level = (int)(r.y & 0xffu), phase = (int)((r.y >> 8) & 0xffu);
         const int k = (int)((r.y >> 16) & 0xffu), q = (int)(r.y >> 24);
         const int B = BMAX >> (level - 1);
-        const int Oi = (510 * q + ko1) / (2 * ko1);
+        const int Oi = (int)__umulhi((uint32_t)(510 * q + ko1), lmagic);
         int t_x, t_y, t_lg, t_dx, t_dy, t_c, t_O, t_iso;
         if (phase == 1) {
             t_x = x;
@@ -602,15 +604,19 @@ __global__ void __launch_bounds__(kDecWarps * 32, 4)
     };
     uint32_t par0 = 0, par1 = 0;
     int b = 0;
-    const TmaMap *nmap = nullptr;
-    uint32_t nwxy = 0;
+    const TmaMap *nmap = nullptr, *m0 = nullptr;
+    uint32_t nwxy = 0, w0 = 0;
     if (lane == 0 && g < total_strips) {
-        const TmaMap *m0;
-        uint32_t w0;
         coords(g, m0, w0);
-        issue(0, m0, w0);
         if (g + gstep < total_strips) coords(g + gstep, nmap, nwxy);
     }
+    // Programmatic dependent launch: everything above (barriers, the strip
+    // tables written by the setup kernel) may overlap the previous
+    // iteration; the previous iterate is read only after it has completed.
+    // The next iteration may then be scheduled as this one's CTAs retire.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (lane == 0 && g < total_strips) issue(0, m0, w0);
     for (; g < total_strips; g += gstep) {
         const int gn = g + gstep;
         const StripD4Use si = strip_d4_use(sinfo + g, dst);
@@ -705,13 +711,25 @@ static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, 
         occupancy_of((const void *)decode_d4_iter_kernel<BMAX>, smem_d4, sms_d4, per_d4);
         const int k = tune.ctas_per_sm > 0 && tune.ctas_per_sm < per_d4 ? tune.ctas_per_sm : per_d4;
         const int grid = need < sms_d4 * k ? need : sms_d4 * k;
+        // iterations are launched as programmatic dependents of the previous
+        // kernel (their prologue overlaps its tail; see the kernel)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kDecWarps * 32);
+        cfg.dynamicSmemBytes = smem_d4;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
         for (int it = 1; it < iters; ++it) {
             // iteration it >= 1 reads image (it - 1) & 1; the first (in the setup kernel) wrote image 0
             const int kind = it == iters - 1 ? 2 : 0;
-            decode_d4_iter_kernel<BMAX><<<grid, kDecWarps * 32, smem_d4, st>>>(sinfo, tfw, total_strips,
-                                                                               (it - 1) & 1, kind);
+            e = cudaLaunchKernelEx(&cfg, decode_d4_iter_kernel<BMAX>, sinfo, (const uint4 *)tfw, total_strips,
+                                   (it - 1) & 1, kind);
             stage_mark(st, "decode_d4_iter_kernel");
-            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;

@@ -117,21 +117,6 @@ __device__ __noinline__ TcRow tc_exact(TcRow b, int d, float acc, int sr, int4 d
     return b;
 }
 
-// Named barrier of the epilogue warps that also ORs a flag over them, so
-// that leaving the tile loop is a uniform decision.
-__device__ __forceinline__ bool epi_bar_or(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "barrier.cta.red.or.pred q, 1, %2, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)v), "r"(kTcEpiWarps * 32)
-        : "memory");
-    return r != 0;
-}
-
 __global__ void __launch_bounds__(kTcThreads, 2)
     exh_tc_kernel(ExhDesc E, const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   uint32_t *err) {
@@ -144,7 +129,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     __shared__ TcRow s_half[kTcRows];  // the second epilogue warp of each lane quarter hands its state over
-    __shared__ float4 s_cst[2][kTcCols];  // screening constants of the tiles in the two accumulators
+    __shared__ float4 s_wc[kTcEpiWarps][2][kTcCols / 2];  // per epilogue warp: its half's constants, two tiles
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row0 = blockIdx.x * kTcRows;
@@ -275,26 +260,31 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             }
             best = tc_exact(best, d0, acc, sr, __ldg(E.dstat + d0), E.s_bits);
         }
-        // screening constants of each tile: staged in shared memory by the
-        // epilogue threads (tile n+1's load is in flight while tile n is
-        // screened); one named barrier per tile, which also makes leaving
-        // the loop after a timeout a uniform decision
-        const int et = threadIdx.x - 64;
-        float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (et < kTcCols && ntiles > 0) pre = __ldg(E.dscr + (size_t)t0 * kTcCols + et);
+        // screening constants of each tile: every epilogue warp stages the
+        // 64 columns of its half in a buffer of its own (tile n+1's load is in
+        // flight while tile n is screened), so the warps never wait on one
+        // another; a wait that runs out ends the warp's loop (warp-uniform)
+        float4 *wc = &s_wc[ew][0][0];
+        const float4 *gc = E.dscr + (size_t)h * (kTcCols / 2) + lane;
+        float4 pre0 = make_float4(0.f, 0.f, 0.f, 0.f), pre1 = pre0;
+        if (ntiles > 0) {
+            pre0 = __ldg(gc + (size_t)t0 * kTcCols);
+            pre1 = __ldg(gc + (size_t)t0 * kTcCols + 32);
+        }
         bool bad = false;
         for (int n = 0; n < ntiles; ++n) {
             const int acc = n & 1;
-            if (et < kTcCols) s_cst[acc][et] = pre;
-            if (epi_bar_or(bad || s_abort)) {
-                s_abort = 1;
-                break;
+            wc[acc * 64 + lane] = pre0;
+            wc[acc * 64 + 32 + lane] = pre1;
+            __syncwarp();
+            if (n + 1 < ntiles) {
+                pre0 = __ldg(gc + (size_t)(t0 + n + 1) * kTcCols);
+                pre1 = __ldg(gc + (size_t)(t0 + n + 1) * kTcCols + 32);
             }
-            if (et < kTcCols && n + 1 < ntiles) pre = __ldg(E.dscr + (size_t)(t0 + n + 1) * kTcCols + et);
-            if (!mbar_wait(&bar_acc_full[acc], (uint32_t)((n >> 1) & 1), kMbarLimit)) {
+            const bool got = mbar_wait(&bar_acc_full[acc], (uint32_t)((n >> 1) & 1), kMbarLimit);
+            if (!__all_sync(0xffffffffu, got) || s_abort) {
                 bad = true;
-                mbar_arrive(&bar_acc_empty[acc]);
-                continue;
+                break;
             }
             tc_fence_after();
 #pragma unroll 1
@@ -303,7 +293,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kTcCols + col), v);
                 const int dbase = (t0 + n) * kTcCols + col;
-                const float4 *cs = &s_cst[acc][col];
+                const float4 *cs = wc + acc * 64 + c0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     if (exh_screen(v[j], srf, cs[j]) >= best.thr)
@@ -312,6 +302,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             }
             tc_fence_before();
             mbar_arrive(&bar_acc_empty[acc]);
+            __syncwarp();  // this buffer is rewritten two tiles later
         }
         if (bad) s_abort = 1;
         // merge the two column halves of each row (the lower domain half wins ties)
