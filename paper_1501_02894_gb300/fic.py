@@ -294,6 +294,8 @@ def fic_encode_noalloc(img: torch.Tensor, p: Params, out: Stream | None = None, 
 def fic_encode_batch(imgs, plist, outs=None, workspace=None, stream=None):
     imgs = [_as_image(t) for t in imgs]
     n = len(imgs)
+    if n == 0:
+        raise FicError(-2, "fic_encode_batch")
     if isinstance(plist, Params):
         plist = [plist] * n
     Ws = [int(t.shape[1]) for t in imgs]
@@ -322,6 +324,8 @@ def fic_decode(st: Stream, iters: int, out: torch.Tensor | None = None, workspac
 
 def fic_decode_batch(sts, iters: int, outs=None, workspace=None, stream=None):
     n = len(sts)
+    if n == 0:
+        raise FicError(-2, "fic_decode_batch")
     dev = sts[0].records.device
     outs = outs or [torch.empty((s.height, s.width), dtype=torch.uint8, device=dev) for s in sts]
     ws = workspace if workspace is not None else decode_workspace([s.width for s in sts],

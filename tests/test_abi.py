@@ -78,3 +78,13 @@ def test_server_structs_and_host_checks(libfic):
     assert L.fic_poll(None, 1, None) == -2
     assert L.fic_wait(None, 1, 0, None) == -2
     assert L.fic_server_destroy(None) == -2
+
+
+def test_empty_batches_rejected_on_the_host(libfic):
+    import ctypes as C
+    from paper_1501_02894_gb300 import fic
+    L = fic.lib()
+    assert L.fic_encode_workspace_bytes(0, None, None, None) == 0
+    assert L.fic_decode_workspace_bytes(0, None, None) == 0
+    p = fic.params("mns", 32, 4, 8.0)
+    assert L.fic_encode_batch(None, None, None, 0, C.byref(p), None, None, 0, None) == -2
