@@ -12,14 +12,17 @@
 // GPU design: the same strip / patch geometry as the encoder (one warp per
 // 1024-pixel strip, lane = 8x4 patch, two 4x4 half-patches per lane).
 //   * decode_setup_kernel (once per decode): for every half-patch, the
-//     transform that covers it (binary search over the strip's canonical
-//     record keys) packed into one word: window column/row of its domain
-//     values, block side, contrast byte, luminance; plus a per-strip word.
-//   * decode_iter_kernel (once per iteration): stage the decimated window of
-//     the previous iterate in shared memory (packed 2x2 sums), read 16 domain
-//     values per half-patch, reduce Sd4 per transform with xor shuffles, then
-//     per pixel one dp2a (select + multiply + offset), one shift and half of
-//     a saturating pack; 8 pixels per row with one 8-byte store.
+//     transform that covers it (the strip's leaves tile its bmin cells in
+//     canonical order, so a 64-bit mask of their first cells ranks a cell's
+//     leaf with one popcount) packed into one word: window column/row of its
+//     domain values, block side, contrast byte, luminance; plus a per-strip
+//     word.  It also writes the first iterate (from 128: the luminances).
+//   * decode_d4_iter_kernel (centred streams, once per later iteration):
+//     iterates on 2x2-sum images (below); decode_iter_kernel (other streams):
+//     stages the decimated window of the previous pixel iterate.  Both read
+//     16 domain values per half-patch, reduce Sd4 per transform with xor
+//     shuffles, then per pixel one dp2a (select + multiply + offset), one
+//     shift and half of a saturating pack.
 // Domains that are not centred (local / exhaustive search, isometries) are
 // read from global memory instead of the staged window.
 #include "fic_internal.cuh"
@@ -166,7 +169,7 @@ __device__ __forceinline__ uint32_t fast_word(int c, int rr, int lg, int cc) {
 // in the strip's records), written to the decode tables.
 template <int BMAX, bool D4>
 __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, int count, const int *s_base, int g,
-                                            uint4 *recs, uint8_t *keys, void *sinfo, uint4 *tfw, uint4 *tgw,
+                                            uint4 *recs, void *sinfo, uint4 *tfw, uint4 *tgw,
                                             int first_kind, int lane) {
     using G = DGeom<BMAX>;
     constexpr int PC = G::PC;
@@ -210,7 +213,6 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
     }
     occ = ((unsigned long long)__reduce_or_sync(0xffffffffu, (uint32_t)(occ >> 32)) << 32) |
           __reduce_or_sync(0xffffffffu, (uint32_t)occ);
-    (void)keys;
     __syncwarp();
     uint32_t fw[2] = {0u, 0u}, gw[2] = {0u, 0u}, hw[2] = {0u, 0u};
     int Ow[2] = {0, 0};
@@ -315,14 +317,13 @@ __global__ void __launch_bounds__(kDecWarps * 32)
                         uint4 *tgw, int first_kind) {
     __shared__ int s_base[kImgTable];
     __shared__ uint4 s_recs[kDecWarps][64];
-    __shared__ uint8_t s_keys[kDecWarps][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (count <= kImgTable)
         for (int i = threadIdx.x; i < count; i += blockDim.x) s_base[i] = descs[i].strip_base;
     __syncthreads();
     const int gwarps = gridDim.x * kDecWarps;
     for (int g = blockIdx.x * kDecWarps + warp; g < total_strips; g += gwarps)
-        setup_strip<BMAX, D4>(descs, count, s_base, g, s_recs[warp], s_keys[warp], sinfo, tfw, tgw, first_kind, lane);
+        setup_strip<BMAX, D4>(descs, count, s_base, g, s_recs[warp], sinfo, tfw, tgw, first_kind, lane);
 }
 
 // First iteration from x0 = 128: d4 - mean d4 = 0, every pixel is its
