@@ -802,7 +802,7 @@ def run_serving(args):
 
     def serve_with_server():
         srv = fic.Server(hbm_budget_bytes=int(args.hbm_budget_gb * (1 << 30)), streams=4, max_batch=64,
-                         queue_capacity=1 << 20, host_staging_bytes=1 << 30)
+                         queue_capacity=1 << 20, host_staging_bytes=4 << 30)
         bufs = Buffers()
         live = {}  # ticket -> (i, key, bufs, submit lag)
         lat = np.zeros(nreq)
