@@ -11,6 +11,7 @@
 #include <cudaTypedefs.h>
 
 #include "exhaustive.cuh"
+#include "trace.cuh"
 
 namespace fic {
 cudaError_t launch_exhaustive(const ExhDesc &E, int engine, cudaStream_t st);
@@ -490,6 +491,7 @@ int fic_encode_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
 
 int fic_encode_plan_run(const fic_plan *pl, void *stream) {
     if (!pl || pl->kind != 0) return FIC_EBADPARAM;
+    fic::TraceRange tr("fic encode");
     if (pl->family == 2) {
         for (size_t i = 0; i < pl->hexh.size(); ++i) {
             const cudaError_t e = launch_exhaustive(pl->hexh[i], pl->engines[i], static_cast<cudaStream_t>(stream));
@@ -796,6 +798,7 @@ int fic_decode_plan_create(const fic_stream *sts, int count, uint8_t *const *d_o
 
 int fic_decode_plan_run(const fic_plan *pl, int iters, void *stream) {
     if (!pl || pl->kind != 1 || iters < 0) return FIC_EBADPARAM;
+    fic::TraceRange tr("fic decode");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (iters == 0) {
         for (size_t i = 0; i < pl->outs.size(); ++i) {

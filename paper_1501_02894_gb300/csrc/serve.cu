@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "fic_internal.cuh"
+#include "trace.cuh"
 
 namespace fic {
 size_t encode_plan_staging_bytes(int count);
@@ -248,6 +249,7 @@ void free_job(fic_server *S, Job *J) {
 
 // Allocate a job's buffers and stage its inputs (worker thread).
 bool prepare_job(fic_server *S, Job *J) {
+    fic::TraceRange tr("fic server: admit job");
     const fic_job &j = J->job;
     const size_t img = (size_t)j.width * j.height;
     auto dget = [&](Alloc &a, size_t n) {
@@ -358,6 +360,7 @@ bool records_valid(const fic_job &j) {
 
 // Enqueue one batch on its stream: inputs in, one batched launch, outputs out.
 int launch_batch(fic_server *S, Batch *B) {
+    fic::TraceRange tr(B->jobs[0]->job.kind == FIC_JOB_ENCODE ? "fic server: encode batch" : "fic server: decode batch");
     cudaStream_t s = S->streams[(size_t)B->stream];
     const int n = (int)B->jobs.size();
     const fic_job &j0 = B->jobs[0]->job;
@@ -426,6 +429,7 @@ int launch_batch(fic_server *S, Batch *B) {
 
 // Copy a finished job's outputs to the caller and fill its result.
 void finish_job(fic_server *S, Job *J, int status, Clock::time_point now) {
+    fic::TraceRange tr("fic server: complete job");
     const fic_job &j = J->job;
     const size_t img = (size_t)j.width * j.height;
     fic_job_result &r = J->res;
