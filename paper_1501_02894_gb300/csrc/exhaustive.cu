@@ -91,7 +91,6 @@ __device__ __forceinline__ void exh_row_init(ExhRow &b) {
 __device__ __forceinline__ void exh_exact(ExhRow &b, int d, int sdr, int sr, int4 ds, int s_bits) {
     const int ncdr = 64 * sdr - ds.x * sr;
     const uint32_t ncdd = (uint32_t)ds.y;
-    if (exh_tight_skip(ncdr, ncdd, b.g, s_bits)) return;
     const int k = best_contrast((long long)ncdr, (long long)ncdd, s_bits);
     const long long c = contrast_code(k, s_bits);
     const long long g = c * c * (long long)ncdd - 1024LL * c * ncdr;

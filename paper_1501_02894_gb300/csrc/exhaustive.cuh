@@ -76,32 +76,6 @@ __device__ __forceinline__ float exh_threshold(long long g) {
     return t > 0.f ? sqrtf(t) * (1.f - 1e-6f) : -1.f;
 }
 
-// Second, tighter screen for candidates that pass the first: the grid's
-// best code is no closer to c* than the grid code nearest to it, so over the
-// grid g >= nCdd (dist^2 - c*^2) with dist that distance.  Evaluated in float
-// with margins (dist shrunk by 1e-3 against a float slip to the farther code
-// near a grid midpoint; the result lowered by 1e-5 of its magnitude + 64);
-// a candidate whose bound exceeds the row's best (plus its float margin) is
-// dropped before the exact int64 evaluation.  nCdd > 0.
-__device__ __forceinline__ float exh_tight_bound(float ncdr_f, float ncdd_f, int s_bits) {
-    const int K = 1 << s_bits;
-    const float step = (float)(256 >> s_bits);
-    const float cmax = (float)((K - 1) * (128 >> s_bits));  // = 128 - step/2
-    const float cs = 512.f * ncdr_f / ncdd_f;
-    const float csc = fminf(fmaxf(cs, -cmax), cmax);
-    const float cnear = fmaf(rintf((csc + 128.f - 0.5f * step) / step), step, 0.5f * step - 128.f);
-    const float dd = fmaxf(fabsf(cs - cnear) - 1e-3f, 0.f);
-    const float g = ncdd_f * (dd * dd - cs * cs);
-    const float mag = ncdd_f * (dd * dd + cs * cs);
-    return g - (1e-5f * mag + 64.f);
-}
-
-__device__ __forceinline__ bool exh_tight_skip(int ncdr, uint32_t ncdd, long long best_g, int s_bits) {
-    if (ncdd == 0u || best_g == 0x7fffffffffffffffLL) return false;
-    const float bg = (float)best_g;
-    return exh_tight_bound((float)ncdr, (float)ncdd, s_bits) > bg + fabsf(bg) * 1e-6f + 1.f;
-}
-
 // (g, d) lexicographic improvement: the smaller domain index wins ties.
 __device__ __forceinline__ bool exh_better(long long g, int d, long long bg, int bd) {
     return g < bg || (g == bg && (unsigned)d < (unsigned)bd);
