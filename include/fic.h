@@ -242,6 +242,14 @@ typedef struct fic_tuning {
     int32_t dec_ctas_per_sm; /* decoder iteration kernel CTAs per SM; 0 = as many as fit */
     int32_t enc_fused_pack;  /* 1: the encoder warp that finishes a 32-strip chunk packs it into
                                 the stream (no pack launch); 0: a separate pack kernel */
+    int32_t dec_single_launch; /* decoders of centred streams (2x2-sum iteration): 1 = every
+                                  iteration after the first in one cooperative launch, a grid
+                                  barrier between iterations; 0 = one launch per iteration, each
+                                  a programmatic dependent of the previous one (default).  A
+                                  barrier wait is bounded: if another launch keeps some CTAs
+                                  from being resident it gives up and the streams report
+                                  FIC_DEVERR_TIMEOUT -- keep 0 for decodes that share the GPU
+                                  with concurrent kernels. */
 } fic_tuning;
 
 FIC_API int fic_plan_get_tuning(const fic_plan *plan, fic_tuning *t);
@@ -249,14 +257,15 @@ FIC_API int fic_plan_get_tuning(const fic_plan *plan, fic_tuning *t);
 FIC_API int fic_plan_set_tuning(fic_plan *plan, const fic_tuning *t);
 /* Time every candidate mapping on the plan's own batch and keep the fastest.
  * Encode plans try warps {8, 4} x CTAs per SM {1, 2, ..., max} x schedule
- * {static, dynamic} x packing {fused, separate}; decode plans try CTAs per SM {1, 2, 3, 4} with `iters`
- * iterations.  Each candidate runs once untimed, then `reps` times between
+ * {static, dynamic} x packing {fused, separate}; decode plans try CTAs per SM {1, 2, 3, 4} x
+ * {single launch, one launch per iteration} with `iters` iterations.  Each candidate runs once untimed, then `reps` times between
  * CUDA events on `stream`; the score is the median.  Synchronous: returns
  * after the last run with the plan's outputs written (identical for every
  * candidate).  *best and *best_ms (either may be NULL) receive the choice
  * and its median time; `trace` (may be NULL) receives up to `trace_cap`
- * (candidate, ms) rows as 6 floats each: enc_warps, enc_ctas_per_sm,
- * enc_dynamic, dec_ctas_per_sm, enc_fused_pack, ms, and *ntrace their number.
+ * (candidate, ms) rows as 7 floats each: enc_warps, enc_ctas_per_sm,
+ * enc_dynamic, dec_ctas_per_sm, enc_fused_pack, dec_single_launch, ms, and
+ * *ntrace their number.
  * Other encode families return FIC_EBADPARAM. */
 FIC_API int fic_plan_autotune(fic_plan *plan, int iters, int reps, void *stream, fic_tuning *best,
                               float *best_ms, float *trace, int trace_cap, int *ntrace);

@@ -31,18 +31,23 @@ void stage_mark(cudaStream_t st, const char *label) {
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library).
-int make_tma_map(TmaMap *out, const void *base, int W, int H, int boxw, int boxh, int elem_bytes) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        void *fn = nullptr;
+// against the driver library); the static is initialised once, thread safe.
+void *tensor_map_encoder() {
+    static void *const fn = [] {
+        void *f = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return FIC_ECUDA;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return f;
+    }();
+    return fn;
+}
+
+int make_tma_map(TmaMap *out, const void *base, int W, int H, int boxw, int boxh, int elem_bytes) {
+    const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+    if (!encode) return FIC_ECUDA;
     CUtensorMap m;
     const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
     const cuuint64_t strides[1] = {(cuuint64_t)W * (cuuint64_t)elem_bytes};
@@ -545,6 +550,7 @@ int fic_plan_get_tuning(const fic_plan *pl, fic_tuning *t) {
     t->enc_dynamic = pl->etune.dynamic;
     t->dec_ctas_per_sm = pl->dtune.ctas_per_sm;
     t->enc_fused_pack = pl->etune.fused_pack;
+    t->dec_single_launch = pl->dtune.single_launch;
     return FIC_OK;
 }
 
@@ -552,13 +558,15 @@ int fic_plan_set_tuning(fic_plan *pl, const fic_tuning *t) {
     if (!pl || !t) return FIC_EBADPARAM;
     if ((t->enc_warps != 8 && t->enc_warps != 4) || t->enc_ctas_per_sm < 0 || t->enc_ctas_per_sm > 64 ||
         (t->enc_dynamic != 0 && t->enc_dynamic != 1) || t->dec_ctas_per_sm < 0 || t->dec_ctas_per_sm > 64 ||
-        (t->enc_fused_pack != 0 && t->enc_fused_pack != 1))
+        (t->enc_fused_pack != 0 && t->enc_fused_pack != 1) ||
+        (t->dec_single_launch != 0 && t->dec_single_launch != 1))
         return FIC_EBADPARAM;
     pl->etune.warps = t->enc_warps;
     pl->etune.ctas_per_sm = t->enc_ctas_per_sm;
     pl->etune.dynamic = t->enc_dynamic;
     pl->dtune.ctas_per_sm = t->dec_ctas_per_sm;
     pl->etune.fused_pack = t->enc_fused_pack;
+    pl->dtune.single_launch = t->dec_single_launch;
     return FIC_OK;
 }
 
@@ -576,12 +584,15 @@ int fic_plan_autotune(fic_plan *pl, int iters, int reps, void *stream, fic_tunin
         for (int w : {8, 4})
             for (int k = 1; k <= (w == 8 ? 3 : 4); ++k)
                 for (int dyn = 0; dyn <= 1; ++dyn)
-                    for (int fp = 1; fp >= 0; --fp) cands.push_back(fic_tuning{w, k, dyn, cur.dec_ctas_per_sm, fp});
+                    for (int fp = 1; fp >= 0; --fp)
+                        cands.push_back(fic_tuning{w, k, dyn, cur.dec_ctas_per_sm, fp, cur.dec_single_launch});
     } else {
         // the iteration kernels are built for 4 resident CTAs of 8 warps (a
         // 48-register build for 5 measured slower: 113 vs 105 us per decode)
-        for (int k = 1; k <= 4; ++k)
-            cands.push_back(fic_tuning{cur.enc_warps, cur.enc_ctas_per_sm, cur.enc_dynamic, k, cur.enc_fused_pack});
+        for (int one = 1; one >= 0; --one)
+            for (int k = 1; k <= 4; ++k)
+                cands.push_back(
+                    fic_tuning{cur.enc_warps, cur.enc_ctas_per_sm, cur.enc_dynamic, k, cur.enc_fused_pack, one});
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -606,13 +617,14 @@ int fic_plan_autotune(fic_plan *pl, int iters, int reps, void *stream, fic_tunin
         std::sort(times.begin(), times.end());
         const float med = times[(size_t)reps / 2];
         if (trace && nt < trace_cap) {
-            float *row = trace + 6 * nt;
+            float *row = trace + 7 * nt;
             row[0] = (float)cands[c].enc_warps;
             row[1] = (float)cands[c].enc_ctas_per_sm;
             row[2] = (float)cands[c].enc_dynamic;
             row[3] = (float)cands[c].dec_ctas_per_sm;
             row[4] = (float)cands[c].enc_fused_pack;
-            row[5] = med;
+            row[5] = (float)cands[c].dec_single_launch;
+            row[6] = med;
             ++nt;
         }
         if (bi < 0 || med < bms) {

@@ -35,9 +35,16 @@ struct DGeom {
     static constexpr int PC = SW / 8;
     static constexpr int PR = BMAX / 4;
     static constexpr int TOPS = SW / BMAX;
-    static constexpr int NP = BMAX == 32 ? 16 : (BMAX == 16 ? 24 : 40);
+    // words per window row: the window's width (32, 48, 80 2x2 sums) and,
+    // for BMAX 32, 4 words of padding so that the lanes of patch rows 4
+    // apart (rows 16 words apart) fall in different shared-memory banks
+    static constexpr int NP = BMAX == 32 ? 20 : (BMAX == 16 ? 24 : 40);
     static constexpr int WORDS = BMAX * NP;
     static constexpr int UPR = BMAX == 32 ? 4 : (BMAX == 16 ? 8 : 16);
+    // lane bit that swaps the order of a row's two word loads, so that one
+    // load instruction touches words of both parities: with the padding
+    // above, at most two lanes of a leaf share a bank
+    __device__ static int bank_key(int pr) { return BMAX == 32 ? (pr >> 1) & 1 : pr & 1; }
 };
 
 constexpr int kDecWarps = 8;
@@ -314,10 +321,14 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
 template <int BMAX, bool D4>
 __global__ void __launch_bounds__(kDecWarps * 32)
     decode_setup_kernel(const DecDesc *__restrict__ descs, int count, int total_strips, void *sinfo, uint4 *tfw,
-                        uint4 *tgw, int first_kind) {
+                        uint4 *tgw, int first_kind, uint32_t *bar) {
     __shared__ int s_base[kImgTable];
     __shared__ uint4 s_recs[kDecWarps][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (bar && blockIdx.x == 0 && threadIdx.x == 0) {
+        bar[0] = 0u;  // grid-barrier words of the single-launch iterations
+        bar[1] = 0u;
+    }
     if (count <= kImgTable)
         for (int i = threadIdx.x; i < count; i += blockDim.x) s_base[i] = descs[i].strip_base;
     __syncthreads();
@@ -348,16 +359,18 @@ __device__ __forceinline__ void first_strip(const StripInfo &si, uint4 tf, int s
 // transforms, read from the staged window, and the halves' partial Sd4.
 template <int BMAX>
 __device__ __forceinline__ void load_centred(const uint32_t (&fw)[2], const uint32_t *d4e, uint32_t (&dv)[2][4][2],
-                                             int (&part)[2]) {
+                                             int (&part)[2], int key) {
     constexpr int NP = DGeom<BMAX>::NP;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int c = (int)(fw[h] & 0xffu), rr = (int)((fw[h] >> 8) & 0xffu);
         const uint32_t *base = d4e + rr * NP + (c >> 1);
+        const uint32_t *bk = base + key, *bn = base + (key ^ 1);
         const bool odd = c & 1;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const uint32_t e0 = base[i * NP], e1 = base[i * NP + 1];
+            const uint32_t t0 = bk[i * NP], t1 = bn[i * NP];
+            const uint32_t e0 = key ? t1 : t0, e1 = key ? t0 : t1;
             if (odd) {
                 const uint32_t e2 = base[i * NP + 2];
                 dv[h][i][0] = __funnelshift_r(e0, e1, 16);
@@ -446,7 +459,7 @@ __device__ __forceinline__ void iterate_strip(const StripInfo &si, uint4 tf, con
 #pragma unroll
             for (int i = 0; i < 4; ++i) dv[h][i][0] = dv[h][i][1] = 0u;
     } else if (centred) {
-        load_centred<BMAX>(fw, d4e, dv, part);
+        load_centred<BMAX>(fw, d4e, dv, part, G::bank_key(pr));
     } else {
         // domains outside the window (local / exhaustive search, isometries)
 #pragma unroll
@@ -534,7 +547,7 @@ __device__ __forceinline__ void iterate_d4(const StripD4Use &si, uint4 tf, const
     uint32_t dv[2][4][2];
     int part[2] = {0, 0};
     if (valid) {
-        load_centred<BMAX>(fw, win, dv, part);
+        load_centred<BMAX>(fw, win, dv, part, DGeom<BMAX>::bank_key(pr));
     } else {
 #pragma unroll
         for (int h = 0; h < 2; ++h)
@@ -558,6 +571,99 @@ __device__ __forceinline__ void iterate_d4(const StripD4Use &si, uint4 tf, const
     }
 }
 
+// Window double buffer of one warp across the iterations of a launch: the
+// buffer the next copy lands in and the phase each buffer's barrier waits for.
+struct D4Ring {
+    uint32_t par0 = 0, par1 = 0;
+    int b = 0;
+};
+
+// One iteration over this warp's strips (strips g, g + gstep, ...): reads the
+// 2x2-sum image `src`, writes the other one (or the pixels when `last`).
+// Lane 0 loads the box coordinates of a strip two strips ahead and issues
+// each window copy one strip ahead, so that issuing never waits on a global
+// load.  With PDL the previous kernel's output is read only after
+// griddepcontrol.wait.  Returns false if a copy did not land (the stream's
+// error bit is raised and the warp's copies in flight are waited for, bounded).
+template <int BMAX, bool PDL>
+__device__ __forceinline__ bool d4_pass(const StripD4 *__restrict__ sinfo, const uint4 *__restrict__ tfw,
+                                        int total_strips, int g, int gstep, int src, bool last, uint32_t *win0,
+                                        uint32_t *win1, uint64_t *bar, D4Ring &R, int lane) {
+    constexpr uint32_t WB = (uint32_t)DGeom<BMAX>::WORDS * 4u;  // one window: BMAX rows x NP words
+    const unsigned FULL = 0xffffffffu;
+    const int dst = src ^ 1;
+    auto coords = [&](int gi, const TmaMap *&map, uint32_t &wxy) {
+        const StripD4 *sn = sinfo + gi;
+        map = src ? sn->map[1] : sn->map[0];
+        wxy = sn->wxy;
+    };
+    auto issue = [&](int b, const TmaMap *map, uint32_t wxy) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar + b, WB);
+        tma_load_2d(b ? win1 : win0, map, (int)(wxy & 0xffffu), (int)(wxy >> 16), bar + b);
+    };
+    const TmaMap *nmap = nullptr, *m0 = nullptr;
+    uint32_t nwxy = 0, w0 = 0;
+    if (lane == 0 && g < total_strips) {
+        coords(g, m0, w0);
+        if (g + gstep < total_strips) coords(g + gstep, nmap, nwxy);
+    }
+    if (PDL) {
+        // everything above (barriers, the strip tables written by the setup
+        // kernel) may overlap the previous kernel; its output is read only
+        // after it has completed, and the next kernel may be scheduled as
+        // this one's CTAs retire
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    }
+    if (lane == 0 && g < total_strips) issue(R.b, m0, w0);
+    for (; g < total_strips; g += gstep) {
+        const int gn = g + gstep;
+        const int b = R.b;
+        const StripD4Use si = strip_d4_use(sinfo + g, dst);
+        const uint4 tf = tfw[(size_t)g * 32 + lane];
+        if (lane == 0 && gn < total_strips) {
+            issue(b ^ 1, nmap, nwxy);
+            if (gn + gstep < total_strips) coords(gn + gstep, nmap, nwxy);
+        }
+        const uint32_t par = b ? R.par1 : R.par0;
+        const bool arrived = mbar_wait(bar + b, par, kMbarLimit);
+        if (!__all_sync(FULL, arrived)) {
+            // give both buffers' copies a bounded chance to land, then leave
+            if (lane == 0) {
+                raise_error(si.info, FIC_DEVERR_TIMEOUT);
+                mbar_wait(bar + b, par, kMbarLimit);
+                if (gn < total_strips) mbar_wait(bar + (b ^ 1), b ? R.par0 : R.par1, kMbarLimit);
+            }
+            __syncwarp();
+            return false;
+        }
+        if (b) R.par1 ^= 1u;
+        else R.par0 ^= 1u;
+        iterate_d4<BMAX>(si, tf, b ? win1 : win0, last, lane);
+        __syncwarp();
+        R.b = b ^ 1;
+    }
+    return true;
+}
+
+// Per-warp windows of the 2x2-sum kernels (two buffers of BMAX rows x NP
+// words, 128-byte aligned) and their barriers.
+template <int BMAX>
+__device__ __forceinline__ void d4_windows(uint8_t *smem, uint64_t (*s_bar)[2], int warp, int lane, uint32_t *&win0,
+                                           uint32_t *&win1) {
+    constexpr uint32_t WB = (uint32_t)DGeom<BMAX>::WORDS * 4u;
+    uint8_t *base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
+    win0 = reinterpret_cast<uint32_t *>(base + (size_t)(2 * warp) * WB);
+    win1 = reinterpret_cast<uint32_t *>(base + (size_t)(2 * warp + 1) * WB);
+    if (lane == 0) {
+        mbar_init(&s_bar[warp][0], 1);
+        mbar_init(&s_bar[warp][1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
 // kind bit 0: first iteration (from 128, reads nothing); bit 1: last
 // iteration (writes pixels).  src: the 2x2-sum image read (0/1); the other
 // one is written.
@@ -565,84 +671,92 @@ template <int BMAX>
 __global__ void __launch_bounds__(kDecWarps * 32, 4)
     decode_d4_iter_kernel(const StripD4 *__restrict__ sinfo, const uint4 *__restrict__ tfw, int total_strips, int src,
                           int kind) {
-    using G = DGeom<BMAX>;
-    constexpr uint32_t WB = (uint32_t)G::WORDS * 4u;  // one window: BMAX rows x NP words
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_bar[kDecWarps][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned FULL = 0xffffffffu;
-    uint8_t *base = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
-    uint32_t *win0 = reinterpret_cast<uint32_t *>(base + (size_t)(2 * warp) * WB);
-    uint32_t *win1 = reinterpret_cast<uint32_t *>(base + (size_t)(2 * warp + 1) * WB);
     const bool first = kind & 1, last = (kind >> 1) & 1;
-    const int dst = first ? 0 : src ^ 1;
-    if (lane == 0) {
-        mbar_init(&s_bar[warp][0], 1);
-        mbar_init(&s_bar[warp][1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
     const int gstep = gridDim.x * kDecWarps;
     int g = blockIdx.x * kDecWarps + warp;
     if (first) {
         for (; g < total_strips; g += gstep)
-            first_d4<BMAX>(strip_d4_use(sinfo + g, dst), tfw[(size_t)g * 32 + lane], last, lane);
+            first_d4<BMAX>(strip_d4_use(sinfo + g, 0), tfw[(size_t)g * 32 + lane], last, lane);
         return;
     }
-    // lane 0: box coordinates of a strip's window (map of the image read,
-    // origin); those of the strip after next are loaded one strip ahead so
-    // that issuing a copy never waits on a global load
-    auto coords = [&](int gi, const TmaMap *&map, uint32_t &wxy) {
-        const StripD4 *sn = sinfo + gi;
-        map = src ? sn->map[1] : sn->map[0];
-        wxy = sn->wxy;
-    };
-    auto issue = [&](int b, const TmaMap *map, uint32_t wxy) {
-        uint64_t *bar = &s_bar[warp][b];
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(bar, WB);
-        tma_load_2d(b ? win1 : win0, map, (int)(wxy & 0xffffu), (int)(wxy >> 16), bar);
-    };
-    uint32_t par0 = 0, par1 = 0;
-    int b = 0;
-    const TmaMap *nmap = nullptr, *m0 = nullptr;
-    uint32_t nwxy = 0, w0 = 0;
-    if (lane == 0 && g < total_strips) {
-        coords(g, m0, w0);
-        if (g + gstep < total_strips) coords(g + gstep, nmap, nwxy);
+    uint32_t *win0, *win1;
+    d4_windows<BMAX>(smem, s_bar, warp, lane, win0, win1);
+    D4Ring R;
+    d4_pass<BMAX, true>(sinfo, tfw, total_strips, g, gstep, src, last, win0, win1, s_bar[warp], R, lane);
+}
+
+// Grid barrier of the single-launch decoder: one arrival per CTA on a
+// counter, then a bounded wait until every CTA of the launch has arrived
+// `round` times (the grid is co-resident: cooperative launch).  bar[0]:
+// arrivals, bar[1]: abort flag (a CTA that failed sets it so that the others
+// leave at their next barrier instead of waiting out the limit).  Called by
+// one thread per CTA between __syncthreads; false on abort or timeout.
+__device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t target) {
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    for (unsigned n = 0; n < kSpinLimit; ++n) {
+        uint32_t v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+        if (v >= target) return true;
+        if (ld_volatile(bar + 1)) return false;
+        if (n > 4) __nanosleep(32);
     }
-    // Programmatic dependent launch: everything above (barriers, the strip
-    // tables written by the setup kernel) may overlap the previous
-    // iteration; the previous iterate is read only after it has completed.
-    // The next iteration may then be scheduled as this one's CTAs retire.
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    if (lane == 0 && g < total_strips) issue(0, m0, w0);
-    for (; g < total_strips; g += gstep) {
-        const int gn = g + gstep;
-        const StripD4Use si = strip_d4_use(sinfo + g, dst);
-        const uint4 tf = tfw[(size_t)g * 32 + lane];
-        if (lane == 0 && gn < total_strips) {
-            issue(b ^ 1, nmap, nwxy);
-            if (gn + gstep < total_strips) coords(gn + gstep, nmap, nwxy);
-        }
-        const uint32_t par = b ? par1 : par0;
-        const bool arrived = mbar_wait(&s_bar[warp][b], par, kMbarLimit);
-        if (!__all_sync(FULL, arrived)) {
-            // give both buffers' copies a bounded chance to land, then leave
-            if (lane == 0) {
-                raise_error(si.info, FIC_DEVERR_TIMEOUT);
-                mbar_wait(&s_bar[warp][b], par, kMbarLimit);
-                if (gn < total_strips) mbar_wait(&s_bar[warp][b ^ 1], b ? par0 : par1, kMbarLimit);
+    return false;
+}
+
+// All iterations after the first in one cooperative launch: iteration it
+// (1 <= it < iters) reads 2x2-sum image (it - 1) & 1 and writes the other,
+// the last one writes the pixels; a grid barrier separates iterations (every
+// write of one iteration before any read of the next, every read of one
+// before the next overwrites its source).  The same strips stay with the
+// same warp throughout, and the launches and grid ramps of the
+// one-launch-per-iteration schedule are saved.  bar[0..1] are zeroed by the
+// setup kernel.
+template <int BMAX>
+__global__ void __launch_bounds__(kDecWarps * 32, 4)
+    decode_d4_loop_kernel(const StripD4 *__restrict__ sinfo, const uint4 *__restrict__ tfw, int total_strips,
+                          int iters, uint32_t *bar) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t s_bar[kDecWarps][2];
+    __shared__ int s_abort;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gstep = gridDim.x * kDecWarps;
+    const int g0 = blockIdx.x * kDecWarps + warp;
+    if (threadIdx.x == 0) s_abort = 0;
+    uint32_t *win0, *win1;
+    d4_windows<BMAX>(smem, s_bar, warp, lane, win0, win1);
+    D4Ring R;
+    uint32_t target = 0;
+    for (int it = 1; it < iters; ++it) {
+        const bool last = it == iters - 1;
+        if (!d4_pass<BMAX, false>(sinfo, tfw, total_strips, g0, gstep, (it - 1) & 1, last, win0, win1, s_bar[warp],
+                                  R, lane) &&
+            lane == 0)
+            atomicExch(&s_abort, 1);
+        if (last) break;
+        // this thread's stores (generic proxy) before the next iteration's
+        // window copies (async proxy) on any SM
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_abort) st_volatile(bar + 1, 1u);
+            target += gridDim.x;
+            if (!grid_barrier(bar, target)) {
+                st_volatile(bar + 1, 1u);
+                s_abort = 1;
             }
-            __syncwarp();
+        }
+        __syncthreads();
+        if (s_abort) {
+            // every stream with a strip here learns that the decode stopped
+            if (lane == 0)
+                for (int g = g0; g < total_strips; g += gstep) raise_error(sinfo[g].info, FIC_DEVERR_TIMEOUT);
             return;
         }
-        if (b) par1 ^= 1u;
-        else par0 ^= 1u;
-        iterate_d4<BMAX>(si, tf, b ? win1 : win0, last, lane);
-        __syncwarp();
-        b ^= 1;
+        if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
     }
 }
 
@@ -661,57 +775,69 @@ size_t decode_smem_bytes(int bmax) {
     return (size_t)kDecWarps * words * sizeof(uint32_t);
 }
 
-// SM count and resident CTAs per SM of a kernel (cached by the caller).
-static void occupancy_of(const void *fn, size_t smem, int &sms, int &per) {
-    if (per == 0) {
-        int dev = 0, p = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, kDecWarps * 32, smem);
-        per = p > 0 ? p : 1;
-    }
-}
-
 // Decode: the table setup kernel, then one launch per iteration.
 template <int BMAX>
 static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, void *tables, int iters, bool d4,
                              const DecTune &tune, cudaStream_t st) {
-    static int sms_setup = 0, per_setup = 0, sms_iter = 0, per_iter = 0, sms_d4 = 0, per_d4 = 0;
-    static bool attr = false;
+    // launch facts per kernel and device (the iteration kernels also get their shared-memory limit)
+    static KernelSlots ks_setup_d4, ks_setup_px, ks_iter, ks_d4, ks_loop;
     const size_t smem = decode_smem_bytes(BMAX), smem_d4 = decode_d4_smem_bytes(BMAX);
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(decode_iter_kernel<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(decode_d4_iter_kernel<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_d4);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    int sms = 0, per = 0;
     const size_t info_bytes = d4 ? sizeof(StripD4) : sizeof(StripInfo);
     uint4 *tfw = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(tables) + info_bytes * (size_t)total_strips);
     uint4 *tgw = tfw + (size_t)total_strips * 32;
     const int need = (total_strips + kDecWarps - 1) / kDecWarps;
+    // the 2x2-sum path keeps no far-domain words: its grid-barrier words sit there
+    const bool single = d4 && tune.single_launch && iters >= 2;
+    uint32_t *bar = single ? reinterpret_cast<uint32_t *>(tgw) : nullptr;
     if (d4) {
-        occupancy_of((const void *)decode_setup_kernel<BMAX, true>, 0, sms_setup, per_setup);
-        const int gs = sms_setup * per_setup;
+        cudaError_t e = kernel_slots(ks_setup_d4, (const void *)decode_setup_kernel<BMAX, true>, kDecWarps * 32, 0,
+                                     sms, per);
+        if (e != cudaSuccess) return e;
+        const int gs = sms * per;
         // the setup kernel also writes the first iterate (pixels when it is the only one)
         decode_setup_kernel<BMAX, true><<<need < gs ? need : gs, kDecWarps * 32, 0, st>>>(
-            descs, count, total_strips, tables, tfw, tgw, iters == 1 ? 3 : 1);
+            descs, count, total_strips, tables, tfw, tgw, iters == 1 ? 3 : 1, bar);
     } else {
-        occupancy_of((const void *)decode_setup_kernel<BMAX, false>, 0, sms_setup, per_setup);
-        const int gs = sms_setup * per_setup;
+        cudaError_t e = kernel_slots(ks_setup_px, (const void *)decode_setup_kernel<BMAX, false>, kDecWarps * 32, 0,
+                                     sms, per);
+        if (e != cudaSuccess) return e;
+        const int gs = sms * per;
         decode_setup_kernel<BMAX, false><<<need < gs ? need : gs, kDecWarps * 32, 0, st>>>(descs, count, total_strips,
-                                                                                         tables, tfw, tgw, 0);
+                                                                                         tables, tfw, tgw, 0, nullptr);
     }
     stage_mark(st, "decode_setup_kernel");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (single) {
+        // iterations 1 .. iters-1 in one cooperative launch (grid barriers
+        // between iterations need every CTA resident)
+        const StripD4 *sinfo = static_cast<const StripD4 *>(tables);
+        e = kernel_slots(ks_loop, (const void *)decode_d4_loop_kernel<BMAX>, kDecWarps * 32, smem_d4, sms, per);
+        if (e != cudaSuccess) return e;
+        const int k = tune.ctas_per_sm > 0 && tune.ctas_per_sm < per ? tune.ctas_per_sm : per;
+        const int grid = need < sms * k ? need : sms * k;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kDecWarps * 32);
+        cfg.dynamicSmemBytes = smem_d4;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, decode_d4_loop_kernel<BMAX>, sinfo, (const uint4 *)tfw, total_strips, iters, bar);
+        stage_mark(st, "decode_d4_loop_kernel");
+        if (e == cudaSuccess) e = cudaGetLastError();
+        return e;
+    }
     if (d4) {
         const StripD4 *sinfo = static_cast<const StripD4 *>(tables);
-        occupancy_of((const void *)decode_d4_iter_kernel<BMAX>, smem_d4, sms_d4, per_d4);
-        const int k = tune.ctas_per_sm > 0 && tune.ctas_per_sm < per_d4 ? tune.ctas_per_sm : per_d4;
-        const int grid = need < sms_d4 * k ? need : sms_d4 * k;
+        e = kernel_slots(ks_d4, (const void *)decode_d4_iter_kernel<BMAX>, kDecWarps * 32, smem_d4, sms, per);
+        if (e != cudaSuccess) return e;
+        const int k = tune.ctas_per_sm > 0 && tune.ctas_per_sm < per ? tune.ctas_per_sm : per;
+        const int grid = need < sms * k ? need : sms * k;
         // iterations are launched as programmatic dependents of the previous
         // kernel (their prologue overlaps its tail; see the kernel)
         cudaLaunchConfig_t cfg = {};
@@ -736,9 +862,10 @@ static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, 
         return cudaSuccess;
     }
     const StripInfo *sinfo = static_cast<const StripInfo *>(tables);
-    occupancy_of((const void *)decode_iter_kernel<BMAX>, smem, sms_iter, per_iter);
-    const int k = tune.ctas_per_sm > 0 && tune.ctas_per_sm < per_iter ? tune.ctas_per_sm : per_iter;
-    const int gi = sms_iter * k;
+    e = kernel_slots(ks_iter, (const void *)decode_iter_kernel<BMAX>, kDecWarps * 32, smem, sms, per);
+    if (e != cudaSuccess) return e;
+    const int k = tune.ctas_per_sm > 0 && tune.ctas_per_sm < per ? tune.ctas_per_sm : per;
+    const int gi = sms * k;
     const int grid = need < gi ? need : gi;
     for (int it = 0; it < iters; ++it) {
         const int src_sel = (iters - it) & 1;  // the last iteration writes buf[0] (the output)

@@ -303,20 +303,13 @@ size_t local_smem_bytes(int bmax) {
 template <int BMAX>
 static cudaError_t llaunch_t(const EncDesc *descs, int count, int total_strips, uint32_t *pack_status,
                              int total_chunks, cudaStream_t st) {
-    static int grid_cache = 0;
+    static KernelSlots ks;
     const size_t smem = local_smem_bytes(BMAX);
-    if (grid_cache == 0) {
-        cudaError_t e = cudaFuncSetAttribute(local_encode_kernel<BMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, local_encode_kernel<BMAX>, kLWarps * 32, smem);
-        grid_cache = sms * (per > 0 ? per : 1);
-    }
+    int sms = 0, per = 0;
+    cudaError_t e = kernel_slots(ks, (const void *)local_encode_kernel<BMAX>, kLWarps * 32, smem, sms, per);
+    if (e != cudaSuccess) return e;
     const int need = (total_strips + kLWarps - 1) / kLWarps;
-    const int grid = need < grid_cache ? need : grid_cache;
+    const int grid = need < sms * per ? need : sms * per;
     local_encode_kernel<BMAX><<<grid, kLWarps * 32, smem, st>>>(descs, count, total_strips, pack_status, total_chunks);
     stage_mark(st, "local_encode_kernel");
     return cudaGetLastError();

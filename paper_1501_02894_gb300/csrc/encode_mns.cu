@@ -529,23 +529,15 @@ size_t mns_smem_bytes(int bmax, int nw) {
 
 int mns_strip_width(int bmax) { return 1024 / bmax; }
 
-// Resident CTAs per SM of one instantiation (its occupancy limit, cached).
+// Resident CTAs per SM of one instantiation (its occupancy limit, per device).
 template <int BMAX, bool SLOTS, int NW>
 static int mns_occupancy(int &sms) {
-    static int per_cache = 0, sms_cache = 0;
-    if (per_cache == 0) {
-        const size_t smem = mns_smem_bytes(BMAX, NW);
-        if (cudaFuncSetAttribute(mns_encode_kernel<BMAX, SLOTS, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
-            return 0;
-        int dev = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms_cache, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mns_encode_kernel<BMAX, SLOTS, NW>, NW * 32, smem);
-        per_cache = per > 0 ? per : 1;
-    }
-    sms = sms_cache;
-    return per_cache;
+    static KernelSlots ks;
+    int per = 0;
+    if (kernel_slots(ks, (const void *)mns_encode_kernel<BMAX, SLOTS, NW>, NW * 32, mns_smem_bytes(BMAX, NW), sms,
+                     per) != cudaSuccess)
+        return 0;
+    return per;
 }
 
 template <int BMAX, bool SLOTS, int NW>
@@ -649,15 +641,14 @@ struct NoAllocScratch {
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-NoAllocScratch *g_noalloc_addr[kMaxDevices] = {};
+NoAllocScratch *g_noalloc_addr[fic::kMaxDevices] = {};
 
 // The array's name is only a host-side stand-in: the device address must be
 // asked for, once per device, with that device current.
 int noalloc_scratch_for_current_device(NoAllocScratch **out) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FIC_ECUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= fic::kMaxDevices) return FIC_ECUDA;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     if (!g_noalloc_addr[dev]) {
         void *p = nullptr;

@@ -327,16 +327,8 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 
 // Tensor maps of the two operands (fp16, 128-byte swizzle, 64 x 128 boxes).
 static int make_f16_map(CUtensorMap *m, const void *base, int rows) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult qr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) !=
-                cudaSuccess ||
-            qr != cudaDriverEntryPointSuccess || !fn)
-            return -1;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
+    const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+    if (!encode) return -1;
     const cuuint64_t dims[2] = {(cuuint64_t)kExhK, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)kExhK * 2};
     const cuuint32_t box[2] = {(cuuint32_t)kExhK, (cuuint32_t)kTcRows};
@@ -354,25 +346,16 @@ size_t exh_tc_smem_bytes() { return (size_t)(1 + kTcStages) * kTileBytes + 1024;
 // tile and segment) so that small images still give every SM several CTAs;
 // *nseg receives the count for exh_finalize.
 cudaError_t launch_exh_tc(const ExhDesc &E, uint32_t *err, int *nseg, cudaStream_t st) {
-    static bool attr = false;
+    static KernelSlots ks;
     const size_t smem = exh_tc_smem_bytes();
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(exh_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    int sms = 0, per = 0;
+    cudaError_t e = kernel_slots(ks, (const void *)exh_tc_kernel, kTcThreads, smem, sms, per);
+    if (e != cudaSuccess) return e;
+    const int slots = sms * per;
     CUtensorMap ma, mb;
     // rows past the end of A read as zeros (TMA out-of-bounds fill)
     if (make_f16_map(&ma, E.afp16, E.nr * 8) || make_f16_map(&mb, E.dfp16, E.nd_pad)) return cudaErrorInvalidValue;
     const int ctas = (E.nr * 8 + kTcRows - 1) / kTcRows;
-    static int slots = 0;
-    if (slots == 0) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, exh_tc_kernel, kTcThreads, smem);
-        slots = sms * (per > 0 ? per : 1);
-    }
     const int ntiles = E.nd_pad / kTcCols;
     int seg = (4 * slots + ctas - 1) / ctas;  // about four waves of CTAs
     seg = seg < 1 ? 1 : (seg > kExhMaxSeg ? kExhMaxSeg : seg);

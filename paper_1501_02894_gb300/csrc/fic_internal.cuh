@@ -2,6 +2,7 @@
 // libfic.so (not part of the public ABI).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -51,10 +52,46 @@ struct WinBox {
     static constexpr int H = 2 * BMAX;
 };
 
+// The driver's cuTensorMapEncodeTiled, looked up once per process through
+// the runtime's entry-point query (thread safe); null if unavailable.
+void *tensor_map_encoder();
+
 // Build the tensor map of a W x H image of uint8 (elem_bytes 1) or uint16
 // (elem_bytes 2) elements, rows W elements apart, for boxes of boxw x boxh
 // elements (host side; the driver entry point is looked up once).
 int make_tma_map(TmaMap *out, const void *base, int W, int H, int boxw, int boxh, int elem_bytes = 1);
+
+// Launch facts of one kernel, per device: its dynamic shared-memory limit is
+// set on each device once (a per-device attribute) and the SM count and
+// resident CTAs per SM are kept.  Thread safe: the setup is idempotent and
+// the results are atomics.
+constexpr int kMaxDevices = 64;
+struct KernelSlots {
+    std::atomic<int> sms[kMaxDevices];
+    std::atomic<int> per[kMaxDevices];
+};
+
+inline cudaError_t kernel_slots(KernelSlots &ks, const void *fn, int threads, size_t smem, int &sms, int &per) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    int p = ks.per[dev].load(std::memory_order_acquire);
+    if (p == 0) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int s = 0, q = 0;
+        e = cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, fn, threads, smem);
+        if (e != cudaSuccess) return e;
+        ks.sms[dev].store(s, std::memory_order_relaxed);
+        p = q > 0 ? q : 1;
+        ks.per[dev].store(p, std::memory_order_release);
+    }
+    sms = ks.sms[dev].load(std::memory_order_relaxed);
+    per = p;
+    return cudaSuccess;
+}
 
 // Per-kernel timing of a plan run (fic_plan_run_timed): launchers call this
 // after every kernel launch; it records an event only while a timed run is
@@ -71,7 +108,11 @@ struct EncTune {
                           // (measured faster: the per-strip release fence costs more than the launch)
 };
 struct DecTune {
-    int ctas_per_sm = 0;  // resident CTAs per SM of the iteration kernel; 0 = the occupancy limit
+    int ctas_per_sm = 0;    // resident CTAs per SM of the iteration kernel; 0 = the occupancy limit
+    int single_launch = 0;  // 2x2-sum path: 1 = iterations after the first in one cooperative launch
+                            // with grid barriers, 0 = one launch per iteration (measured faster: the
+                            // dependent launches overlap each iteration's ramp with the previous tail
+                            // better than a grid barrier does)
 };
 
 // One image of a decode launch.

@@ -398,6 +398,13 @@ int launch_batch(fic_server *S, Batch *B) {
         if (rc == FIC_OK) rc = fic_encode_plan_run(plan, s);
     } else {
         rc = fic::decode_plan_create_staged(sts.data(), n, outs.data(), B->d_ws.p, B->d_ws.n, s, B->h_desc.p, &plan);
+        if (rc == FIC_OK && S->streams.size() > 1) {
+            // batches on other streams run beside this one: no grid barriers
+            fic_tuning t;
+            fic_plan_get_tuning(plan, &t);
+            t.dec_single_launch = 0;
+            rc = fic_plan_set_tuning(plan, &t);
+        }
         if (rc == FIC_OK) rc = fic_decode_plan_run(plan, j0.iters, s);
     }
     if (plan) fic_plan_destroy(plan);

@@ -76,7 +76,8 @@ def params(mode="mns", bmax=32, bmin=4, thr=8.0, s_bits=5, o_bits=7, phase2=True
 
 class Tuning(ctypes.Structure):
     _fields_ = [("enc_warps", ctypes.c_int32), ("enc_ctas_per_sm", ctypes.c_int32), ("enc_dynamic", ctypes.c_int32),
-                ("dec_ctas_per_sm", ctypes.c_int32), ("enc_fused_pack", ctypes.c_int32)]
+                ("dec_ctas_per_sm", ctypes.c_int32), ("enc_fused_pack", ctypes.c_int32),
+                ("dec_single_launch", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -364,13 +365,14 @@ class _Tunable:
     def _autotune(self, iters, reps, stream):
         best, ms, n = Tuning(), ctypes.c_float(), ctypes.c_int()
         cap = 64
-        trace = (ctypes.c_float * (6 * cap))()
+        trace = (ctypes.c_float * (7 * cap))()
         _check(lib().fic_plan_autotune(self.handle, int(iters), int(reps), _stream_handle(stream), ctypes.byref(best),
                                        ctypes.byref(ms), trace, cap, ctypes.byref(n)), "fic_plan_autotune")
-        rows = [tuple(trace[6 * i: 6 * i + 6]) for i in range(n.value)]
-        keys = ("enc_warps", "enc_ctas_per_sm", "enc_dynamic", "dec_ctas_per_sm", "enc_fused_pack")
+        rows = [tuple(trace[7 * i: 7 * i + 7]) for i in range(n.value)]
+        keys = ("enc_warps", "enc_ctas_per_sm", "enc_dynamic", "dec_ctas_per_sm", "enc_fused_pack",
+                "dec_single_launch")
         return {"best": best.as_dict(), "best_ms": ms.value,
-                "trials": [dict({k: int(r[j]) for j, k in enumerate(keys)}, ms=float(r[5])) for r in rows]}
+                "trials": [dict({k: int(r[j]) for j, k in enumerate(keys)}, ms=float(r[6])) for r in rows]}
 
 
 class EncodePlan(_Tunable):

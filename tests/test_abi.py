@@ -66,6 +66,7 @@ def test_server_structs_and_host_checks(libfic):
     assert C.sizeof(fic.ServerConfig) == 4 * 4 + 8 * 2
     assert C.sizeof(fic.JobC) == 4 * 3 + 4 + C.sizeof(fic.Params) + 4 * 2 + 8 * 5  # padding before params
     assert C.sizeof(fic.JobResult) == 4 * 2 + 8 * 3
+    assert C.sizeof(fic.Tuning) == 4 * 6
     assert C.sizeof(fic.ServerStats) == 8 * 5 + 8 * 5
     L = fic.lib()
     cfg = fic.ServerConfig(0, 0, 8, 16, 1 << 20, 1 << 20)  # no streams

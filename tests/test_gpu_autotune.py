@@ -57,7 +57,7 @@ def test_every_mapping_gives_the_same_output(fic, batch):
                     st.records.zero_()
                 plan.run()
                 plan.run()  # the dynamic counter is reset between runs
-                dplan.set_tuning(dec_ctas_per_sm=1 + (k % 4))
+                dplan.set_tuning(dec_ctas_per_sm=1 + (k % 4), dec_single_launch=(k + dyn) % 2)
                 dplan.run(8)
                 _check(fic, plan, dplan, want)
 
@@ -72,7 +72,8 @@ def test_autotune_picks_a_candidate_and_stays_exact(fic, batch):
     assert res["best_ms"] == pytest.approx(min(t["ms"] for t in res["trials"]), rel=1e-4)
     dplan = fic.DecodePlan(plan.outs)
     dres = dplan.autotune(8, reps=3)
-    assert len(dres["trials"]) == 4 and 1 <= dres["best"]["dec_ctas_per_sm"] <= 4
+    assert len(dres["trials"]) == 8 and 1 <= dres["best"]["dec_ctas_per_sm"] <= 4
+    assert {t["dec_single_launch"] for t in dres["trials"]} == {0, 1}
     plan.run()
     dplan.run(8)
     _check(fic, plan, dplan, want)
@@ -85,6 +86,8 @@ def test_bad_tuning_rejected(fic):
         plan.set_tuning(enc_warps=6)
     with pytest.raises(fic.FicError):
         plan.set_tuning(enc_dynamic=2)
+    with pytest.raises(fic.FicError):
+        plan.set_tuning(dec_single_launch=2)
     lplan = fic.EncodePlan([img], fic.params("local", 32, 4, 8.0))
     with pytest.raises(fic.FicError):
         lplan.autotune()

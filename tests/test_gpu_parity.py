@@ -245,6 +245,32 @@ def test_decode_paths_agree(fic, orc):
     assert np.array_equal(fic.fic_decode(sc, 5).cpu().numpy(), orc.decode(orc.encode(c, opc)[0], 64, 128, opc, 5))
 
 
+@pytest.mark.parametrize("bmax,bmin,side", [(32, 4, 512), (16, 4, 256), (8, 4, 192)])
+def test_decode_single_launch_and_per_iteration_launches(fic, orc, bmax, bmin, side):
+    """The 2x2-sum iterations after the first run either in one cooperative
+    launch (grid barrier between iterations) or one launch per iteration;
+    both equal the oracle for every iteration count, including 2 (no
+    barrier) and 3 (one barrier), and a batch of several streams."""
+    imgs = [synth.gaussian_scene(side, 70 + bmax), synth.voronoi(side, 80 + bmax)]
+    p, op = _pair(fic, orc, "mns", bmax, bmin, 6.0)
+    sts = [fic.fic_encode(torch.from_numpy(im).cuda(), p) for im in imgs]
+    leaves = [orc.encode(im, op)[0] for im in imgs]
+    plan = fic.DecodePlan(sts)
+    for iters in (1, 2, 3, 4, 9):
+        want = [orc.decode(lv, side, side, op, iters) for lv in leaves]
+        for single in (1, 0):
+            for k in (0, 1):
+                plan.set_tuning(dec_single_launch=single, dec_ctas_per_sm=k)
+                for o in plan.outs:
+                    o.zero_()
+                plan.run(iters)
+                torch.cuda.synchronize()
+                for o, w in zip(plan.outs, want):
+                    assert np.array_equal(o.cpu().numpy(), w), (iters, single, k)
+    for st in sts:
+        st.info_host()  # no device error bit
+
+
 # ---------------------------------------------------------------------------
 # Phase 2 with the other domain reading: quadrants of the parent's domain
 
