@@ -54,15 +54,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const TmaMap *map, int x,
         : "memory");
 }
 
-// Contiguous global -> shared copy (16-byte aligned addresses, size a
-// multiple of 16), completing on `bar` like a tensor copy.
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-        "l"(static_cast<uint64_t>(__cvta_generic_to_global(src))), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
 __device__ __forceinline__ bool mbar_test_parity(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
