@@ -609,10 +609,13 @@ __device__ __forceinline__ bool d4_pass(const StripD4 *__restrict__ sinfo, const
         if (g + gstep < total_strips) coords(g + gstep, nmap, nwxy);
     }
     if (PDL) {
-        // everything above (barriers, the strip tables written by the setup
-        // kernel) may overlap the previous kernel; its output is read only
-        // after it has completed, and the next kernel may be scheduled as
-        // this one's CTAs retire
+        // everything above may overlap the previous kernel; its output is
+        // read only after it has completed, and the next kernel may be
+        // scheduled as this one's CTAs retire.  The strip tables read above
+        // were written by the setup kernel: they are complete because the
+        // setup kernel never triggers its dependents early (it completes
+        // before the first iteration starts) and every later iteration
+        // triggers only after its own wait.
         asm volatile("griddepcontrol.wait;" ::: "memory");
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     }

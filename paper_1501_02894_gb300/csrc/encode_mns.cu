@@ -79,6 +79,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
     uint64_t *bar = &s_bar[warp];
     const int pr = lane / PC, pc = lane % PC;
     const unsigned FULL = 0xffffffffu;
+    // the pack kernel may be scheduled as this grid's CTAs retire (it waits
+    // for this grid's completion before reading anything it wrote)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (count <= kImgTable)
         for (int i = threadIdx.x; i < count; i += blockDim.x) s_base[i] = descs[i].strip_base;
     if (SLOTS && !fused) {

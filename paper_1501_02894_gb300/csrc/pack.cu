@@ -32,9 +32,6 @@ __global__ void __launch_bounds__(kPackWarps * 32)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned FULL = 0xffffffffu;
     const int c = blockIdx.x;
-    // the encoder's strip counter (dynamic schedule) is free again: reset it
-    // for the next launch
-    if (ticket && c == 0 && threadIdx.x == 0) *ticket = 0u;
     if (count <= kImgTable)
         for (int i = threadIdx.x; i < count; i += blockDim.x) s_cb[i] = descs[i].chunk_base;
     __syncthreads();
@@ -49,6 +46,13 @@ __global__ void __launch_bounds__(kPackWarps * 32)
             else hi = mid - 1;
         }
     }
+    // Programmatic dependent launch: the prologue above (descriptors written
+    // by the host) may overlap the encoder's tail; everything the encoder
+    // wrote is read after it has completed.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // the encoder's strip counter (dynamic schedule) is free again: reset it
+    // for the next launch
+    if (ticket && c == 0 && threadIdx.x == 0) *ticket = 0u;
     // warps 1..7 load their slots' records while warp 0 resolves the offsets
     constexpr int kPer = (32 + kPackWarps - 2) / (kPackWarps - 1);  // slots per copy warp (5)
     uint4 pre[kPer][2];
@@ -168,9 +172,20 @@ __global__ void __launch_bounds__(kPackWarps * 32)
 cudaError_t launch_pack(const EncDesc *d_descs, int count, int total_chunks, uint32_t *pack_status,
                         uint32_t *ticket, cudaStream_t st) {
     if (total_chunks <= 0) return cudaSuccess;
-    pack_kernel<<<total_chunks, kPackWarps * 32, 0, st>>>(d_descs, count, total_chunks, pack_status, ticket);
+    // a programmatic dependent of the encoder kernel (see griddepcontrol.wait above)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(total_chunks);
+    cfg.blockDim = dim3(kPackWarps * 32);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, pack_kernel, d_descs, count, total_chunks, pack_status, ticket);
     stage_mark(st, "pack_kernel");
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace fic
