@@ -196,7 +196,7 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
     const bool centred = (D.mode == FIC_NOSEARCH || D.mode == FIC_MNS);
     const int ko1 = (1 << D.o_bits) - 1;
     // L(q) = floor((510 q + ko1) / (2 ko1)) by a multiply-high (exact for q <= ko1 <= 255)
-    const uint32_t lmagic = (uint32_t)((0x100000000ULL + 2 * ko1 - 1) / (2 * ko1));
+    const uint32_t lmagic = c_lum_magic[D.o_bits];
     const int rx0 = clampi(sx0 - BMAX / 2, 0, W - 2 * BMAX);
     const int xl = sx0 + (nvalid - 1) * BMAX;
     const int rx1 = clampi(xl - BMAX / 2, 0, W - 2 * BMAX) + 2 * BMAX;

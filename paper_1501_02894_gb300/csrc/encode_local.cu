@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(kLWarps * 32, 2)
         const bool valid = lane_top < nvalid;
         const int L = D.L, bmin = D.bmin, s_bits = D.s_bits;
         const int ko1 = (1 << D.o_bits) - 1;
-        const uint32_t magic = (uint32_t)((0x100000000ULL + 2 * ko1 - 1) / (2 * ko1));
-        const float qscale = (float)ko1 / 255.f;
+        const uint32_t magic = c_lum_magic[D.o_bits];
+        const float qscale = c_lum_qscale[D.o_bits];
         const int R = D.local_radius, S = D.local_step;
 
         // ---- window: the level-1 domains of the strip, widened by R

@@ -146,8 +146,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
         const bool valid = lane_top < nvalid;
         const int L = D.L, bmin = D.bmin, s_bits = D.s_bits;
         const int ko1 = (1 << D.o_bits) - 1;
-        const uint32_t magic = (uint32_t)((0x100000000ULL + 2 * ko1 - 1) / (2 * ko1));
-        const float qscale = (float)ko1 / 255.f;
+        const uint32_t magic = c_lum_magic[D.o_bits];
+        const float qscale = c_lum_qscale[D.o_bits];
         const bool ph2 = (D.mode == FIC_MNS) && D.phase2;
         const int pitch = D.boxw;
         const int rx0 = clampi(sx0 - BMAX / 2, 0, W - 2 * BMAX);
@@ -347,7 +347,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
                         const int cbx = (8 * pc) / Bc, cby = (4 * pr) / Bc;
                         const int kk = (cbx & 1) | ((cby & 1) << 1);
                         int bit;
-                        ok_lane = fit_phase2_sub(sub[0], lg2n4, O[kk], c0, c1, thr_p2, bit);
+                        // (selects: an indexed array would live in local memory)
+                        const int Ok = kk == 0 ? O[0] : (kk == 1 ? O[1] : (kk == 2 ? O[2] : O[3]));
+                        ok_lane = fit_phase2_sub(sub[0], lg2n4, Ok, c0, c1, thr_p2, bit);
                         const uint32_t bits = __ballot_sync(FULL, bit);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
@@ -358,8 +360,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
                     } else {
                         const bool top = (pr & 1) == 0;
                         int b0, b1;
-                        const bool ok0 = fit_phase2_sub(sub[0], 4, O[top ? 0 : 2], c0, c1, thr_p2, b0);
-                        const bool ok1 = fit_phase2_sub(sub[1], 4, O[top ? 1 : 3], c0, c1, thr_p2, b1);
+                        const bool ok0 = fit_phase2_sub(sub[0], 4, top ? O[0] : O[2], c0, c1, thr_p2, b0);
+                        const bool ok1 = fit_phase2_sub(sub[1], 4, top ? O[1] : O[3], c0, c1, thr_p2, b1);
                         ok_lane = ok0 && ok1;
                         const int my = b0 | (b1 << 1);
                         const int other = __shfl_xor_sync(FULL, my, PC);

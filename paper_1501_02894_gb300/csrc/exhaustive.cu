@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
 // order).  Ties: smaller domain index, then smaller isometry.
 __global__ void exh_finalize(ExhDesc E) {
     const int ko1 = (1 << E.o_bits) - 1;
-    const uint32_t magic = (uint32_t)((0x100000000ULL + 2 * ko1 - 1) / (2 * ko1));
-    const float qscale = (float)ko1 / 255.f;
+    const uint32_t magic = c_lum_magic[E.o_bits];
+    const float qscale = c_lum_qscale[E.o_bits];
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < E.nr; r += gridDim.x * blockDim.x) {
         long long bg = 0x7fffffffffffffffLL;
         int bd = 0x7fffffff, bt = 0, bk = 0;

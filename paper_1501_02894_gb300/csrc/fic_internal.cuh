@@ -141,11 +141,35 @@ __host__ __device__ inline int contrast_code(int k, int s_bits) {
 // Phase-2 contrast sets of Section 3.2 in the c = round(128 s) fixed point:
 // level 1 {.2, .5}, level 2 {.4, .65}, level 3 {.5, .9}.
 __host__ __device__ inline int phase2_code(int level, int bit) {
-    // packed: level-1 (26, 64), level-2 (51, 83), level-3 (64, 115)
-    const int lo[3] = {26, 51, 64};
-    const int hi[3] = {64, 83, 115};
-    return bit ? hi[level - 1] : lo[level - 1];
+    // level 1 (26, 64), level 2 (51, 83), level 3 (64, 115); selects, not a
+    // table (an indexed local array would live in local memory)
+    const int lo = level == 1 ? 26 : (level == 2 ? 51 : 64);
+    const int hi = level == 1 ? 64 : (level == 2 ? 83 : 115);
+    return bit ? hi : lo;
 }
+
+// Multiplier of the luminance level L(q) = floor((510 q + ko1) / (2 ko1))
+// by a multiply-high, ko1 = 2^o_bits - 1: ceil(2^32 / (2 ko1)), exact for
+// q <= ko1 <= 255.  A table over o_bits = 1..8 (the encoders and the decoder
+// would otherwise do a 64-bit division per strip).
+constexpr uint32_t lum_magic_of(int o_bits) {
+    return (uint32_t)((0x100000000ULL + 2ULL * ((1ULL << o_bits) - 1) - 1) / (2ULL * ((1ULL << o_bits) - 1)));
+}
+constexpr bool lum_magic_exact(int o_bits) {
+    const uint64_t ko1 = (1ULL << o_bits) - 1, m = lum_magic_of(o_bits);
+    for (uint64_t q = 0; q <= ko1; ++q)
+        if ((((510 * q + ko1) * m) >> 32) != (510 * q + ko1) / (2 * ko1)) return false;
+    return true;
+}
+static_assert(lum_magic_exact(1) && lum_magic_exact(2) && lum_magic_exact(3) && lum_magic_exact(4) &&
+                  lum_magic_exact(5) && lum_magic_exact(6) && lum_magic_exact(7) && lum_magic_exact(8),
+              "multiply-high luminance levels are exact for every code");
+__constant__ const uint32_t c_lum_magic[9] = {0u,              lum_magic_of(1), lum_magic_of(2),
+                                              lum_magic_of(3), lum_magic_of(4), lum_magic_of(5),
+                                              lum_magic_of(6), lum_magic_of(7), lum_magic_of(8)};
+// ko1 / 255 for the encoders' float estimate of the luminance code.
+__constant__ const float c_lum_qscale[9] = {0.f,          1.f / 255.f,  3.f / 255.f,  7.f / 255.f,  15.f / 255.f,
+                                            31.f / 255.f, 63.f / 255.f, 127.f / 255.f, 255.f / 255.f};
 
 __host__ __device__ inline int clampi(int v, int lo, int hi) {
     return v < lo ? lo : (v > hi ? hi : v);
