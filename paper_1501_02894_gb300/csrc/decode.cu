@@ -117,9 +117,9 @@ static_assert(sizeof(StripD4) == 64, "strip word: one 64-byte bulk copy");
 
 // 2x2 sums of two rows of four pixels each: (p0+p1+q0+q1) | (p2+p3+q2+q3) << 16.
 __device__ __forceinline__ uint32_t sum2x2(uint32_t a, uint32_t b) {
-    const uint32_t ha = (a & 0x00ff00ffu) + ((a >> 8) & 0x00ff00ffu);
-    const uint32_t hb = (b & 0x00ff00ffu) + ((b >> 8) & 0x00ff00ffu);
-    return ha + hb;
+    const uint32_t lo = __dp4a(a, 0x00000101u, __dp4a(b, 0x00000101u, 0u));
+    const uint32_t hi = __dp4a(a, 0x01010000u, __dp4a(b, 0x01010000u, 0u));
+    return __byte_perm(lo, hi, 0x5410);
 }
 
 // First iteration from x0 = 128: every pixel is its transform's luminance.
@@ -367,18 +367,17 @@ __device__ __forceinline__ void load_centred(const uint32_t (&fw)[2], const uint
         const uint32_t *base = d4e + rr * NP + (c >> 1);
         const uint32_t *bk = base + key, *bn = base + (key ^ 1);
         const bool odd = c & 1;
+        // the pair at 16-bit offset `odd` of (e1:e0) and of (e2:e1) by byte
+        // permutes; (t0, t1) hold (e0, e1), or (e1, e0) when key is set
+        const uint32_t s0 = key ? (odd ? 0x1076u : 0x7654u) : (odd ? 0x5432u : 0x3210u);
+        const uint32_t s1 = odd ? 0x5432u : 0x3210u;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const uint32_t t0 = bk[i * NP], t1 = bn[i * NP];
-            const uint32_t e0 = key ? t1 : t0, e1 = key ? t0 : t1;
-            if (odd) {
-                const uint32_t e2 = base[i * NP + 2];
-                dv[h][i][0] = __funnelshift_r(e0, e1, 16);
-                dv[h][i][1] = __funnelshift_r(e1, e2, 16);
-            } else {
-                dv[h][i][0] = e0;
-                dv[h][i][1] = e1;
-            }
+            const uint32_t t2 = odd ? base[i * NP + 2] : 0u;
+            const uint32_t e1 = key ? t0 : t1;
+            dv[h][i][0] = __byte_perm(t0, t1, s0);
+            dv[h][i][1] = __byte_perm(e1, t2, s1);
         }
         uint32_t pk = 0;
 #pragma unroll
@@ -608,6 +607,10 @@ __device__ __forceinline__ bool d4_pass(const StripD4 *__restrict__ sinfo, const
         coords(g, m0, w0);
         if (g + gstep < total_strips) coords(g + gstep, nmap, nwxy);
     }
+    if (g < total_strips) {
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(tfw + (size_t)g * 32 + lane));
+        if (lane == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(sinfo + g));
+    }
     if (PDL) {
         // everything above may overlap the previous kernel; its output is
         // read only after it has completed, and the next kernel may be
@@ -625,9 +628,15 @@ __device__ __forceinline__ bool d4_pass(const StripD4 *__restrict__ sinfo, const
         const int b = R.b;
         const StripD4Use si = strip_d4_use(sinfo + g, dst);
         const uint4 tf = tfw[(size_t)g * 32 + lane];
-        if (lane == 0 && gn < total_strips) {
-            issue(b ^ 1, nmap, nwxy);
-            if (gn + gstep < total_strips) coords(gn + gstep, nmap, nwxy);
+        if (gn < total_strips) {
+            if (lane == 0) {
+                issue(b ^ 1, nmap, nwxy);
+                if (gn + gstep < total_strips) coords(gn + gstep, nmap, nwxy);
+            }
+            // the next strip's tables into L1 (no registers held): its loads
+            // then wait on L1 instead of L2
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(tfw + (size_t)gn * 32 + lane));
+            if (lane == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(sinfo + gn));
         }
         const uint32_t par = b ? R.par1 : R.par0;
         const bool arrived = mbar_wait(bar + b, par, kMbarLimit);
