@@ -122,44 +122,36 @@ __device__ __forceinline__ uint32_t sum2x2(uint32_t a, uint32_t b) {
     return __byte_perm(lo, hi, 0x5410);
 }
 
+// Per-lane transform words of the 2x2-sum path (one uint4 per lane and
+// strip, written by the setup kernel):
+//   x, y  fast words of the two half-patches (c | rr << 8 | lg << 16 | cbyte << 24)
+//   z     their luminances O0 | O1 << 16 (signed 16-bit)
+//   w     the lane's element offset in the (W/2) x (H/2) 2x2-sum images (its
+//         top-left 2x2 sum), or kNoLane for a lane outside the image
+// so that an iteration needs, per strip, only the image's 2x2-sum base and
+// width besides its window.
+constexpr uint32_t kNoLane = 0xffffffffu;
+
+__device__ __forceinline__ int lum16(uint32_t z, int h) { return (int)(int16_t)(h ? (z >> 16) : (z & 0xffffu)); }
+
 // First iteration from x0 = 128: every pixel is its transform's luminance.
-// Fields of a strip's StripD4 the lanes use (loaded field by field: the
-// ping-pong selection must not index the struct's arrays dynamically).
-struct StripD4Use {
-    uint8_t *out;
-    uint16_t *d4o;  // 2x2-sum image written by this iteration
-    uint32_t *info;
-    int W;
-    uint32_t sxy, misc;
-};
-
-__device__ __forceinline__ StripD4Use strip_d4_use(const StripD4 *sp, int dst) {
-    StripD4Use u;
-    u.out = sp->out;
-    u.d4o = dst ? sp->d4[1] : sp->d4[0];
-    u.info = sp->info;
-    u.W = sp->W;
-    u.sxy = sp->sxy;
-    u.misc = sp->misc;
-    return u;
-}
-
+// `last`: write the pixels (the only iteration) instead of their 2x2 sums.
 template <int BMAX>
-__device__ __forceinline__ void first_d4(const StripD4Use &si, uint4 tf, bool last, int lane) {
+__device__ __forceinline__ void first_d4(uint4 tf, uint16_t *d4o, uint8_t *out, int W, uint32_t sxy, bool last,
+                                         int lane) {
     constexpr int PC = DGeom<BMAX>::PC;
-    const int pr = lane / PC, pc = lane % PC;
-    const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
-    const int nvalid = (int)((si.misc >> 8) & 0xffu);
-    if ((8 * pc) / BMAX >= nvalid) return;
-    const int O0 = min(max((int)tf.y, 0), 255), O1 = min(max((int)tf.w, 0), 255);
+    if (tf.w == kNoLane) return;
+    const int O0 = min(max(lum16(tf.z, 0), 0), 255), O1 = min(max(lum16(tf.z, 1), 0), 255);
     if (last) {
-        uint8_t *out = si.out + (size_t)(sy0 + 4 * pr) * si.W + sx0 + 8 * pc;
+        const int pr = lane / PC, pc = lane % PC;
+        const int sx0 = (int)(sxy & 0xffffu), sy0 = (int)(sxy >> 16);
+        uint8_t *o = out + (size_t)(sy0 + 4 * pr) * W + sx0 + 8 * pc;
         const uint32_t w0 = (uint32_t)O0 * 0x01010101u, w1 = (uint32_t)O1 * 0x01010101u;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(out + (size_t)i * si.W) = make_uint2(w0, w1);
+        for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(o + (size_t)i * W) = make_uint2(w0, w1);
     } else {
-        const int W2 = si.W >> 1;
-        uint16_t *o = si.d4o + (size_t)((sy0 >> 1) + 2 * pr) * W2 + (sx0 >> 1) + 4 * pc;
+        const int W2 = W >> 1;
+        uint16_t *o = d4o + tf.w;
         const uint32_t w0 = (uint32_t)(4 * O0) * 0x00010001u, w1 = (uint32_t)(4 * O1) * 0x00010001u;
 #pragma unroll
         for (int j = 0; j < 2; ++j) *reinterpret_cast<uint2 *>(o + (size_t)j * W2) = make_uint2(w0, w1);
@@ -277,19 +269,17 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
         gw[h] = (uint32_t)t_dx | ((uint32_t)t_dy << 16);
         hw[h] = (uint32_t)u0 | ((uint32_t)v0 << 8) | ((uint32_t)t_iso << 16);
     }
-    const uint4 tf = make_uint4(fw[0], (uint32_t)Ow[0], fw[1], (uint32_t)Ow[1]);
-    tfw[(size_t)g * 32 + lane] = tf;
-    if (!centred) tgw[(size_t)g * 32 + lane] = make_uint4(gw[0], hw[0], gw[1], hw[1]);
-    if (D4 && first_kind) {
+    if (D4) {
+        const uint32_t off =
+            valid ? (uint32_t)(((sy0 >> 1) + 2 * pr) * (W >> 1) + (sx0 >> 1) + 4 * pc) : kNoLane;
+        const uint4 tf = make_uint4(fw[0], fw[1], ((uint32_t)Ow[0] & 0xffffu) | ((uint32_t)Ow[1] << 16), off);
+        tfw[(size_t)g * 32 + lane] = tf;
         // the first iteration from 128 needs only the luminance: written here
-        StripD4Use u;
-        u.out = D.buf[0];
-        u.d4o = D.d4[0];
-        u.info = D.info;
-        u.W = W;
-        u.sxy = (uint32_t)sx0 | ((uint32_t)sy0 << 16);
-        u.misc = (uint32_t)nvalid << 8;
-        first_d4<BMAX>(u, tf, first_kind == 3, lane);
+        if (first_kind)
+            first_d4<BMAX>(tf, D.d4[0], D.buf[0], W, (uint32_t)sx0 | ((uint32_t)sy0 << 16), first_kind == 3, lane);
+    } else {
+        tfw[(size_t)g * 32 + lane] = make_uint4(fw[0], (uint32_t)Ow[0], fw[1], (uint32_t)Ow[1]);
+        if (!centred) tgw[(size_t)g * 32 + lane] = make_uint4(gw[0], hw[0], gw[1], hw[1]);
     }
     if (lane == 0) {
         if (D4) {
@@ -535,14 +525,13 @@ __global__ void __launch_bounds__(kDecWarps * 32, 4)
 // its next strip's window into a second buffer while it computes.
 
 template <int BMAX>
-__device__ __forceinline__ void iterate_d4(const StripD4Use &si, uint4 tf, const uint32_t *win, bool last, int lane) {
+__device__ __forceinline__ void iterate_d4(uint4 tf, const uint32_t *win, uint16_t *d4o, int W, bool last,
+                                           const StripD4 *sp, int lane) {
     constexpr int PC = DGeom<BMAX>::PC;
     const int pr = lane / PC, pc = lane % PC;
-    const int sx0 = (int)(si.sxy & 0xffffu), sy0 = (int)(si.sxy >> 16);
-    const int nvalid = (int)((si.misc >> 8) & 0xffu);
-    const bool valid = (8 * pc) / BMAX < nvalid;
-    const uint32_t fw[2] = {tf.x, tf.z};
-    const int Ov[2] = {(int)tf.y, (int)tf.w};
+    const bool valid = tf.w != kNoLane;
+    const uint32_t fw[2] = {tf.x, tf.y};
+    const int Ov[2] = {lum16(tf.z, 0), lum16(tf.z, 1)};
     uint32_t dv[2][4][2];
     int part[2] = {0, 0};
     if (valid) {
@@ -557,12 +546,14 @@ __device__ __forceinline__ void iterate_d4(const StripD4Use &si, uint4 tf, const
     transform_rows<BMAX>(fw, Ov, dv, part, w);
     if (!valid) return;
     if (last) {
-        uint8_t *out = si.out + (size_t)(sy0 + 4 * pr) * si.W + sx0 + 8 * pc;
+        const uint32_t sxy = sp->sxy;
+        const int sx0 = (int)(sxy & 0xffffu), sy0 = (int)(sxy >> 16);
+        uint8_t *out = sp->out + (size_t)(sy0 + 4 * pr) * W + sx0 + 8 * pc;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(out + (size_t)i * si.W) = make_uint2(w[i][0], w[i][1]);
+        for (int i = 0; i < 4; ++i) *reinterpret_cast<uint2 *>(out + (size_t)i * W) = make_uint2(w[i][0], w[i][1]);
     } else {
-        const int W2 = si.W >> 1;
-        uint16_t *o = si.d4o + (size_t)((sy0 >> 1) + 2 * pr) * W2 + (sx0 >> 1) + 4 * pc;
+        const int W2 = W >> 1;
+        uint16_t *o = d4o + tf.w;
 #pragma unroll
         for (int j = 0; j < 2; ++j)
             *reinterpret_cast<uint2 *>(o + (size_t)j * W2) =
@@ -626,7 +617,9 @@ __device__ __forceinline__ bool d4_pass(const StripD4 *__restrict__ sinfo, const
     for (; g < total_strips; g += gstep) {
         const int gn = g + gstep;
         const int b = R.b;
-        const StripD4Use si = strip_d4_use(sinfo + g, dst);
+        const StripD4 *sp = sinfo + g;
+        uint16_t *const d4o = dst ? sp->d4[1] : sp->d4[0];
+        const int W = sp->W;
         const uint4 tf = tfw[(size_t)g * 32 + lane];
         if (gn < total_strips) {
             if (lane == 0) {
@@ -643,7 +636,7 @@ __device__ __forceinline__ bool d4_pass(const StripD4 *__restrict__ sinfo, const
         if (!__all_sync(FULL, arrived)) {
             // give both buffers' copies a bounded chance to land, then leave
             if (lane == 0) {
-                raise_error(si.info, FIC_DEVERR_TIMEOUT);
+                raise_error(sp->info, FIC_DEVERR_TIMEOUT);
                 mbar_wait(bar + b, par, kMbarLimit);
                 if (gn < total_strips) mbar_wait(bar + (b ^ 1), b ? R.par0 : R.par1, kMbarLimit);
             }
@@ -652,7 +645,7 @@ __device__ __forceinline__ bool d4_pass(const StripD4 *__restrict__ sinfo, const
         }
         if (b) R.par1 ^= 1u;
         else R.par0 ^= 1u;
-        iterate_d4<BMAX>(si, tf, b ? win1 : win0, last, lane);
+        iterate_d4<BMAX>(tf, b ? win1 : win0, d4o, W, last, sp, lane);
         __syncwarp();
         R.b = b ^ 1;
     }
@@ -676,9 +669,9 @@ __device__ __forceinline__ void d4_windows(uint8_t *smem, uint64_t (*s_bar)[2], 
     __syncthreads();
 }
 
-// kind bit 0: first iteration (from 128, reads nothing); bit 1: last
-// iteration (writes pixels).  src: the 2x2-sum image read (0/1); the other
-// one is written.
+// One iteration after the first (the setup kernel writes the first).  kind
+// bit 1: the last iteration (writes pixels).  src: the 2x2-sum image read
+// (0/1); the other one is written.
 template <int BMAX>
 __global__ void __launch_bounds__(kDecWarps * 32, 4)
     decode_d4_iter_kernel(const StripD4 *__restrict__ sinfo, const uint4 *__restrict__ tfw, int total_strips, int src,
@@ -686,14 +679,9 @@ __global__ void __launch_bounds__(kDecWarps * 32, 4)
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_bar[kDecWarps][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool first = kind & 1, last = (kind >> 1) & 1;
+    const bool last = (kind >> 1) & 1;
     const int gstep = gridDim.x * kDecWarps;
-    int g = blockIdx.x * kDecWarps + warp;
-    if (first) {
-        for (; g < total_strips; g += gstep)
-            first_d4<BMAX>(strip_d4_use(sinfo + g, 0), tfw[(size_t)g * 32 + lane], last, lane);
-        return;
-    }
+    const int g = blockIdx.x * kDecWarps + warp;
     uint32_t *win0, *win1;
     d4_windows<BMAX>(smem, s_bar, warp, lane, win0, win1);
     D4Ring R;
