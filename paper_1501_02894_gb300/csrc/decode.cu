@@ -598,10 +598,6 @@ __device__ __forceinline__ bool d4_pass(const StripD4 *__restrict__ sinfo, const
         coords(g, m0, w0);
         if (g + gstep < total_strips) coords(g + gstep, nmap, nwxy);
     }
-    if (g < total_strips) {
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(tfw + (size_t)g * 32 + lane));
-        if (lane == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(sinfo + g));
-    }
     if (PDL) {
         // everything above may overlap the previous kernel; its output is
         // read only after it has completed, and the next kernel may be
@@ -626,10 +622,6 @@ __device__ __forceinline__ bool d4_pass(const StripD4 *__restrict__ sinfo, const
                 issue(b ^ 1, nmap, nwxy);
                 if (gn + gstep < total_strips) coords(gn + gstep, nmap, nwxy);
             }
-            // the next strip's tables into L1 (no registers held): its loads
-            // then wait on L1 instead of L2
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(tfw + (size_t)gn * 32 + lane));
-            if (lane == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(sinfo + gn));
         }
         const uint32_t par = b ? R.par1 : R.par0;
         const bool arrived = mbar_wait(bar + b, par, kMbarLimit);
