@@ -49,12 +49,6 @@ struct DGeom {
 
 constexpr int kDecWarps = 8;
 
-__device__ __forceinline__ uint32_t dmorton3(uint32_t x, uint32_t y) {
-    uint32_t z = 0;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) z |= (((x >> b) & 1u) << (2 * b)) | (((y >> b) & 1u) << (2 * b + 1));
-    return z;
-}
 
 // Source element of an isometry (column u, row v of a B x B block):
 // 0 identity, 1 quarter turn clockwise, 2 half turn, 3 quarter turn
@@ -207,7 +201,7 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
         recs[i] = r;
         const int x = (int)(r.x & 0xffffu), y = (int)(r.x >> 16);
         const int lt = x / BMAX - sc * G::TOPS;
-        const int key = min(lt * cpt + (int)dmorton3((x % BMAX) / bmin, (y % BMAX) / bmin), 63);
+        const int key = min(lt * cpt + (int)morton3((x % BMAX) / bmin, (y % BMAX) / bmin), 63);
         occ |= 1ull << key;
     }
     occ = ((unsigned long long)__reduce_or_sync(0xffffffffu, (uint32_t)(occ >> 32)) << 32) |
@@ -220,7 +214,7 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
         if (!valid || nrec <= 0) continue;
         const int px = 8 * pc + 4 * h, py = 4 * pr;  // in strip
         const int tx = px - lane_top * BMAX;
-        const int key = min(lane_top * cpt + (int)dmorton3(tx / bmin, py / bmin), 63);
+        const int key = min(lane_top * cpt + (int)morton3(tx / bmin, py / bmin), 63);
         const unsigned long long upto = key == 63 ? ~0ull : ((2ull << key) - 1ull);
         const int lo = max(__popcll(occ & upto) - 1, 0);  // last leaf starting at or before the cell
         const uint4 r = recs[min(lo, nrec - 1)];

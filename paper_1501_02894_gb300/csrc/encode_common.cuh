@@ -107,13 +107,6 @@ __device__ __forceinline__ bool fit_phase2_sub(const Fit &f, int lg2n, int O, in
     return E < thr;
 }
 
-__device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y) {
-    uint32_t z = 0;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) z |= (((x >> b) & 1u) << (2 * b)) | (((y >> b) & 1u) << (2 * b + 1));
-    return z;
-}
-
 // Bitmask of the lanes that form the lane's block when a block spans gx patch
 // columns and gy patch rows.
 template <int PC>

@@ -203,6 +203,15 @@ __device__ __forceinline__ void acc_sq(unsigned p, unsigned &sq_lo, unsigned &sq
     sq_hi = dp2a_hi(p, w, sq_hi);
 }
 
+// Morton (Z-order) index of a cell (x, y), x, y < 8: bits of x at even and
+// of y at odd positions.  Each 3-bit coordinate is spread by one byte
+// permute from the table {0, 1, 4, 5, 16, 17, 20, 21} held in two words.
+__device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y) {
+    const uint32_t sx = __byte_perm(0x05040100u, 0x15141110u, x & 7u);
+    const uint32_t sy = __byte_perm(0x05040100u, 0x15141110u, y & 7u);
+    return sx | (sy << 1);
+}
+
 // Record the first device error bit of a stream.
 __device__ __forceinline__ void raise_error(uint32_t *info, uint32_t bit) {
     atomicOr(info + FIC_INFO_ERROR, bit);
