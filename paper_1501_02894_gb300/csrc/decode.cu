@@ -571,8 +571,8 @@ struct D4Ring {
 // error bit is raised and the warp's copies in flight are waited for, bounded).
 template <int BMAX, bool PDL>
 __device__ __forceinline__ bool d4_pass(const StripD4 *__restrict__ sinfo, const uint4 *__restrict__ tfw,
-                                        int total_strips, int g, int gstep, int src, bool last, uint32_t *win0,
-                                        uint32_t *win1, uint64_t *bar, D4Ring &R, int lane) {
+                                        int total_strips, int g, int gstep, int src, bool last, bool after_setup,
+                                        uint32_t *win0, uint32_t *win1, uint64_t *bar, D4Ring &R, int lane) {
     constexpr uint32_t WB = (uint32_t)DGeom<BMAX>::WORDS * 4u;  // one window: BMAX rows x NP words
     const unsigned FULL = 0xffffffffu;
     const int dst = src ^ 1;
@@ -588,20 +588,25 @@ __device__ __forceinline__ bool d4_pass(const StripD4 *__restrict__ sinfo, const
     };
     const TmaMap *nmap = nullptr, *m0 = nullptr;
     uint32_t nwxy = 0, w0 = 0;
-    if (lane == 0 && g < total_strips) {
+    // With PDL, everything before griddepcontrol.wait may overlap the
+    // previous kernel, whose output is read only after the wait.  The strip
+    // tables come from the setup kernel: right after it (`after_setup`) they
+    // are that kernel's output and are read after the wait like the rest;
+    // in later iterations an earlier iteration's wait has already made them
+    // visible, so their first coordinates are fetched before the wait.
+    const bool early = !PDL || !after_setup;
+    if (early && lane == 0 && g < total_strips) {
         coords(g, m0, w0);
         if (g + gstep < total_strips) coords(g + gstep, nmap, nwxy);
     }
     if (PDL) {
-        // everything above may overlap the previous kernel; its output is
-        // read only after it has completed, and the next kernel may be
-        // scheduled as this one's CTAs retire.  The strip tables read above
-        // were written by the setup kernel: they are complete because the
-        // setup kernel never triggers its dependents early (it completes
-        // before the first iteration starts) and every later iteration
-        // triggers only after its own wait.
+        // the next kernel may be scheduled as this one's CTAs retire
         asm volatile("griddepcontrol.wait;" ::: "memory");
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    }
+    if (!early && lane == 0 && g < total_strips) {
+        coords(g, m0, w0);
+        if (g + gstep < total_strips) coords(g + gstep, nmap, nwxy);
     }
     if (lane == 0 && g < total_strips) issue(R.b, m0, w0);
     for (; g < total_strips; g += gstep) {
@@ -656,8 +661,9 @@ __device__ __forceinline__ void d4_windows(uint8_t *smem, uint64_t (*s_bar)[2], 
 }
 
 // One iteration after the first (the setup kernel writes the first).  kind
-// bit 1: the last iteration (writes pixels).  src: the 2x2-sum image read
-// (0/1); the other one is written.
+// bit 1: the last iteration (writes pixels); bit 2: the launch right after
+// the setup kernel.  src: the 2x2-sum image read (0/1); the other one is
+// written.
 template <int BMAX>
 __global__ void __launch_bounds__(kDecWarps * 32, 4)
     decode_d4_iter_kernel(const StripD4 *__restrict__ sinfo, const uint4 *__restrict__ tfw, int total_strips, int src,
@@ -665,13 +671,14 @@ __global__ void __launch_bounds__(kDecWarps * 32, 4)
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_bar[kDecWarps][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool last = (kind >> 1) & 1;
+    const bool last = (kind >> 1) & 1, after_setup = (kind >> 2) & 1;
     const int gstep = gridDim.x * kDecWarps;
     const int g = blockIdx.x * kDecWarps + warp;
     uint32_t *win0, *win1;
     d4_windows<BMAX>(smem, s_bar, warp, lane, win0, win1);
     D4Ring R;
-    d4_pass<BMAX, true>(sinfo, tfw, total_strips, g, gstep, src, last, win0, win1, s_bar[warp], R, lane);
+    d4_pass<BMAX, true>(sinfo, tfw, total_strips, g, gstep, src, last, after_setup, win0, win1, s_bar[warp], R,
+                        lane);
 }
 
 // Grid barrier of the single-launch decoder: one arrival per CTA on a
@@ -718,8 +725,8 @@ __global__ void __launch_bounds__(kDecWarps * 32, 4)
     uint32_t target = 0;
     for (int it = 1; it < iters; ++it) {
         const bool last = it == iters - 1;
-        if (!d4_pass<BMAX, false>(sinfo, tfw, total_strips, g0, gstep, (it - 1) & 1, last, win0, win1, s_bar[warp],
-                                  R, lane) &&
+        if (!d4_pass<BMAX, false>(sinfo, tfw, total_strips, g0, gstep, (it - 1) & 1, last, false, win0, win1,
+                                  s_bar[warp], R, lane) &&
             lane == 0)
             atomicExch(&s_abort, 1);
         if (last) break;
@@ -838,7 +845,7 @@ static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, 
         cfg.numAttrs = 1;
         for (int it = 1; it < iters; ++it) {
             // iteration it >= 1 reads image (it - 1) & 1; the first (in the setup kernel) wrote image 0
-            const int kind = it == iters - 1 ? 2 : 0;
+            const int kind = (it == iters - 1 ? 2 : 0) | (it == 1 ? 4 : 0);
             e = cudaLaunchKernelEx(&cfg, decode_d4_iter_kernel<BMAX>, sinfo, (const uint4 *)tfw, total_strips,
                                    (it - 1) & 1, kind);
             stage_mark(st, "decode_d4_iter_kernel");
