@@ -520,8 +520,94 @@ def run_batched(args, spec: Spec):
             e2e_ev.append((s0, s1))
     stream.synchronize()
     assert np.array_equal(rec_host[: 16 * nrec[0]].numpy(), ref0["records"].view(np.uint8)), "e2e copy differs"
-    e2e_ms, e2e_px_s = replica_throughput(world, dev, statistics.mean(a.elapsed_time(b) for a, b in e2e_ev[warm:]),
-                                          pixels)
+    e2e_serial_ms, e2e_serial_px_s = replica_throughput(
+        world, dev, statistics.mean(a.elapsed_time(b) for a, b in e2e_ev[warm:]), pixels)
+
+    # ---- end to end, pipelined: a second set of device buffers, plans and
+    # graphs; step i copies its inputs in on one stream, encodes and decodes
+    # on a second and copies its results out on a third, so that the copies
+    # of neighbouring steps overlap the compute.  Every step still moves its
+    # own inputs in and its own results out inside the timed region.
+    class Slot:
+        pass
+
+    def make_slot():
+        sl = Slot()
+        sl.dev_in = torch.empty_like(dev_in)
+        imgs_s = [sl.dev_in[int(o): int(o) + it[0].size].view(it[0].shape) for it, o in zip(items, offs)]
+        sl.rec = torch.empty_like(rec_arena)
+        sl.info = torch.zeros_like(info_arena)
+        outs_ss = [fic.Stream(it[0].shape[1], it[0].shape[0], p, dev, records=sl.rec[int(a): int(b)], info=sl.info[i])
+                   for i, (it, p, a, b) in enumerate(zip(items, plist, roffs[:-1], roffs[1:]))]
+        sl.dec = torch.empty_like(dec_arena)
+        dec_outs_s = [sl.dec[int(o): int(o) + it[0].size].view(it[0].shape) for it, o in zip(items, offs)]
+        with torch.cuda.stream(stream):
+            sl.enc_plan = fic.EncodePlan(imgs_s, plist, outs=outs_ss, stream=stream)
+            sl.enc_plan.set_tuning(**enc.tuning)
+            sl.enc_plan.run(stream)
+            sl.dec_plan = fic.DecodePlan(sl.enc_plan.outs, outs=dec_outs_s, stream=stream)
+            sl.dec_plan.set_tuning(**dec.tuning)
+        sl.g_enc, sl.g_dec = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            with torch.cuda.graph(sl.g_enc, stream=stream):
+                sl.enc_plan.run(stream)
+            with torch.cuda.graph(sl.g_dec, stream=stream):
+                sl.dec_plan.run(iters, stream)
+        stream.synchronize()
+        sl.out_host = torch.empty(int(offs[-1]), dtype=torch.uint8).pin_memory()
+        sl.rec_host = torch.empty(rec_arena.numel(), dtype=torch.uint8).pin_memory()
+        sl.info_host = torch.empty((n, fic.INFO_WORDS), dtype=torch.int32).pin_memory()
+        return sl
+
+    slot0 = Slot()
+    slot0.dev_in, slot0.rec, slot0.info, slot0.dec = dev_in, rec_arena, info_arena, dec_arena
+    slot0.g_enc, slot0.g_dec = g_enc, g_dec
+    slot0.out_host, slot0.rec_host, slot0.info_host = out_host, rec_host, info_host
+    slots = [slot0, make_slot()]
+    s_in, s_cmp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_cmp = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+
+    def pipe(steps):
+        for i in range(steps):
+            k = i & 1
+            sl = slots[k]
+            with torch.cuda.stream(s_in):
+                if i >= 2:
+                    s_in.wait_event(ev_cmp[k])  # the slot's previous inputs are consumed
+                sl.dev_in.copy_(host_in, non_blocking=True)
+                ev_in[k].record(s_in)
+            with torch.cuda.stream(s_cmp):
+                s_cmp.wait_event(ev_in[k])
+                if i >= 2:
+                    s_cmp.wait_event(ev_out[k])  # the slot's previous results are out
+                sl.g_enc.replay()
+                sl.g_dec.replay()
+                ev_cmp[k].record(s_cmp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ev_cmp[k])
+                sl.info_host.copy_(sl.info, non_blocking=True)
+                sl.rec_host.copy_(sl.rec, non_blocking=True)
+                sl.out_host.copy_(sl.dec, non_blocking=True)
+                ev_out[k].record(s_out)
+
+    torch.cuda.synchronize(dev)
+    pipe(warm)
+    torch.cuda.synchronize(dev)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    p0.record(s_in)
+    pipe(args.steps)
+    p1.record(s_out)  # the last step's last copy depends on all earlier work
+    torch.cuda.synchronize(dev)
+    for sl in slots:
+        assert np.array_equal(sl.rec_host[: 16 * nrec[0]].numpy(), ref0["records"].view(np.uint8)), \
+            "pipelined e2e copy differs"
+        assert torch.equal(sl.out_host, slots[0].out_host), "pipelined decodes differ between slots"
+    e2e_ms, e2e_px_s = replica_throughput(world, dev, p0.elapsed_time(p1) / args.steps, pixels)
     e2e_value = e2e_px_s / 1e6
 
     # ---- roofline of the dominant kernel (HBM bound): algorithmic bytes per launch
@@ -529,7 +615,9 @@ def run_batched(args, spec: Spec):
     peak = float(peaks["hbm_gbs"])
     enc_bytes = pixels + sum(16 * r for r in nrec) + sum(8 * t + 4 for t in ntops)
     dec_bytes_iter = 2 * pixels + sum(16 * r for r in nrec) + sum(4 * (t + 1) for t in ntops)
-    alg = {"mns_encode_kernel": enc_bytes, "decode_iter_kernel": dec_bytes_iter, "decode_d4_iter_kernel": dec_bytes_iter}
+    alg = {"mns_encode_kernel": enc_bytes, "decode_iter_kernel": dec_bytes_iter, "decode_d4_iter_kernel": dec_bytes_iter,
+           # the cooperative single launch runs every iteration after the first
+           "decode_d4_loop_kernel": max(iters - 1, 0) * dec_bytes_iter}
     dom = max((k for k in ktab if k in alg), key=lambda k: ktab[k]["share"])
     dur_ms, dur_src = ktab[dom]["ms_per_launch"], "CUDA events around every launch (serialised)"
     if dom in ("decode_d4_iter_kernel", "decode_iter_kernel") and iter_graph_ms:
@@ -559,7 +647,11 @@ def run_batched(args, spec: Spec):
         "wall_s_timed": round(t_wall, 3),
         "roofline": roofline,
         "e2e": {"value": round(e2e_value, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 5),
+                "mode": "pipelined over steps: inputs in, encode + decode, results out on three streams "
+                        "with two buffer sets; no L2 flush (every step's inputs arrive by copy)",
+                "serial": {"value": round(e2e_serial_px_s / 1e6, 3), "ms_per_step": round(e2e_serial_ms, 5),
+                           "mode": "one step at a time on one stream, L2 flushed before each step"}},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
