@@ -29,7 +29,8 @@ __device__ __forceinline__ int lum(int q, int ko1, uint32_t magic) {
 __device__ __forceinline__ int best_contrast(long long ncdr, long long ncdd, int s_bits) {
     const int K = 1 << s_bits, step = 256 >> s_bits;
     if (ncdd <= 0) return K >> 1;
-    float cs = 512.f * (float)ncdr / (float)ncdd;
+    // an estimate only (settled exactly below): the fast division suffices
+    float cs = __fdividef(512.f * (float)ncdr, (float)ncdd);
     float kf = (cs + 128.f) / (float)step - 0.5f;
     kf = fminf(fmaxf(kf, 0.f), (float)(K - 1));
     int k = __float2int_rn(kf);
@@ -120,6 +121,8 @@ __device__ __forceinline__ uint32_t group_mask(int pc, int pr, int gx, int gy) {
 
 template <int PC>
 __device__ __forceinline__ int group_sum(int v, int gx, int gy) {
+    // a block spanning the whole warp (warp-uniform): one reduction
+    if (gx * gy == 32) return __reduce_add_sync(0xffffffffu, v);
     for (int m = 1; m < gx; m <<= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
     for (int m = 1; m < gy; m <<= 1) v += __shfl_xor_sync(0xffffffffu, v, m * PC);
     return v;
@@ -127,6 +130,7 @@ __device__ __forceinline__ int group_sum(int v, int gx, int gy) {
 
 template <int PC>
 __device__ __forceinline__ uint32_t group_or(uint32_t v, int gx, int gy) {
+    if (gx * gy == 32) return __reduce_or_sync(0xffffffffu, v);  // the whole warp (warp-uniform)
     for (int m = 1; m < gx; m <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, m);
     for (int m = 1; m < gy; m <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, m * PC);
     return v;
