@@ -387,15 +387,20 @@ __device__ __forceinline__ void transform_rows(const uint32_t (&fw)[2], const in
         const int B = 1 << lg0;
         const int gx = big ? B / 8 : 1, gy = big ? B / 4 : 1;
         int v = part[0] + part[1];
+        if (BMAX == 32 && __all_sync(FULL, lg0 == 5)) {
+            // one transform covers the whole strip (a 32x32 leaf): one reduction
+            v = __reduce_add_sync(FULL, v);
+        } else {
 #pragma unroll
-        for (int m = 1; m < 4; m <<= 1) {
-            const int o = __shfl_xor_sync(FULL, v, m);
-            if (m < gx) v += o;
-        }
+            for (int m = 1; m < 4; m <<= 1) {
+                const int o = __shfl_xor_sync(FULL, v, m);
+                if (m < gx) v += o;
+            }
 #pragma unroll
-        for (int m = 1; m < 8; m <<= 1) {
-            const int o = __shfl_xor_sync(FULL, v, (m * PC) & 31);
-            if (m < gy && m * PC < 32) v += o;
+            for (int m = 1; m < 8; m <<= 1) {
+                const int o = __shfl_xor_sync(FULL, v, (m * PC) & 31);
+                if (m < gy && m * PC < 32) v += o;
+            }
         }
         sd4[0] = big ? v : part[0];
         sd4[1] = big ? v : part[1];
