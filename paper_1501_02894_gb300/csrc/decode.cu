@@ -178,7 +178,8 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
     const int lane_top = (8 * pc) / BMAX;
     const bool valid = lane_top < nvalid;
     const int bmin = D.bmin;
-    const int cpt_side = BMAX / bmin, cpt = cpt_side * cpt_side;
+    const int lgbmin = 31 - __clz(bmin);  // bmin is a power of two: divisions are shifts
+    const int cpt_side = BMAX >> lgbmin, cpt = cpt_side * cpt_side;
     const bool centred = (D.mode == FIC_NOSEARCH || D.mode == FIC_MNS);
     const int ko1 = (1 << D.o_bits) - 1;
     // L(q) = floor((510 q + ko1) / (2 ko1)) by a multiply-high (exact for q <= ko1 <= 255)
@@ -201,7 +202,7 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
         recs[i] = r;
         const int x = (int)(r.x & 0xffffu), y = (int)(r.x >> 16);
         const int lt = x / BMAX - sc * G::TOPS;
-        const int key = min(lt * cpt + (int)morton3((x % BMAX) / bmin, (y % BMAX) / bmin), 63);
+        const int key = min(lt * cpt + (int)morton3((x % BMAX) >> lgbmin, (y % BMAX) >> lgbmin), 63);
         occ |= 1ull << key;
     }
     occ = ((unsigned long long)__reduce_or_sync(0xffffffffu, (uint32_t)(occ >> 32)) << 32) |
@@ -214,7 +215,7 @@ __device__ __forceinline__ void setup_strip(const DecDesc *__restrict__ descs, i
         if (!valid || nrec <= 0) continue;
         const int px = 8 * pc + 4 * h, py = 4 * pr;  // in strip
         const int tx = px - lane_top * BMAX;
-        const int key = min(lane_top * cpt + (int)morton3(tx / bmin, py / bmin), 63);
+        const int key = min(lane_top * cpt + (int)morton3(tx >> lgbmin, py >> lgbmin), 63);
         const unsigned long long upto = key == 63 ? ~0ull : ((2ull << key) - 1ull);
         const int lo = max(__popcll(occ & upto) - 1, 0);  // last leaf starting at or before the cell
         const uint4 r = recs[min(lo, nrec - 1)];

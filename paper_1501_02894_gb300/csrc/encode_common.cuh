@@ -112,11 +112,13 @@ __device__ __forceinline__ bool fit_phase2_sub(const Fit &f, int lg2n, int O, in
 // columns and gy patch rows.
 template <int PC>
 __device__ __forceinline__ uint32_t group_mask(int pc, int pr, int gx, int gy) {
-    int base = (pr - pr % gy) * PC + (pc - pc % gx);
-    uint32_t row = (gx >= 32) ? 0xffffffffu : ((1u << gx) - 1u);
-    uint32_t m = 0;
-    for (int i = 0; i < gy; ++i) m |= row << (base + i * PC);
-    return m;
+    // gy rows of gx bits, PC apart: the row pattern times a comb of gy ones
+    // spaced PC apart (gx <= PC, so the copies do not overlap)
+    static_assert(PC == 4 || PC == 8 || PC == 16, "patch columns per strip");
+    constexpr uint32_t COMB = PC == 4 ? 0x11111111u : (PC == 8 ? 0x01010101u : 0x00010001u);
+    const int base = (pr & ~(gy - 1)) * PC + (pc & ~(gx - 1));  // gx, gy powers of two
+    const uint32_t row = (1u << gx) - 1u;
+    return (row * (COMB >> (32 - PC * gy))) << base;
 }
 
 template <int PC>

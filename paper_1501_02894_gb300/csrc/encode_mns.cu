@@ -197,16 +197,19 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
         leaf[1].pos = -1;
         uint32_t splitbits = 0;
         unsigned fits = 0;
-        const int cpt_side = BMAX / bmin;  // bmin cells per top side
+        // sides are powers of two: divisions by them are shifts (a division by
+        // a run-time value would cost a few dozen instructions)
+        const int lgbmin = 31 - __clz(bmin);
+        const int cpt_side = BMAX >> lgbmin;  // bmin cells per top side
         const int cpt = cpt_side * cpt_side;
         bool act = valid;
         Code cur;       // phase-1 codes of the lane's level-j block (side >= 8)
         Code cur4[2];   // the two 4x4 blocks of the last level
         Fit ch[2];      // children's fits (ch[0] for side >= 8, both for the 4x4 halves)
-        int B = BMAX;
+        int B = BMAX, lgB = 31 - __clz(BMAX);
         {
             const int gx = B / 8, gy = B / 4;
-            const int bx = (8 * pc) / B, by = (4 * pr) / B;
+            const int bx = (8 * pc) >> lgB, by = (4 * pr) >> lgB;
             const int xa = sx0 + bx * B, ya = sy0 + by * B;
             const int dxa = centred_origin(xa, B, W), dya = centred_origin(ya, B, H);
             const int u0 = 8 * pc - bx * B, v0 = 4 * pr - by * B;
@@ -224,16 +227,16 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
             cur.q = f.q;
             cur.pass = f.pass;
         }
-        for (int j = 1; j <= L; ++j, B >>= 1) {
+        for (int j = 1; j <= L; ++j, B >>= 1, --lgB) {
             if (B >= 8) {
                 const int gx = B / 8, gy = B / 4;
-                const int bx = (8 * pc) / B, by = (4 * pr) / B;
+                const int bx = (8 * pc) >> lgB, by = (4 * pr) >> lgB;
                 const int xa = sx0 + bx * B, ya = sy0 + by * B;
                 const int u0 = 8 * pc - bx * B, v0 = 4 * pr - by * B;
                 const bool rep = act && u0 == 0 && v0 == 0;
                 if (rep) fits += 1;
                 const int tx = bx * B - lane_top * BMAX, ty = by * B;  // inside the top block
-                const int pos = lane_top * cpt + (int)morton3(tx / bmin, ty / bmin);
+                const int pos = lane_top * cpt + (int)morton3(tx >> lgbmin, ty >> lgbmin);
                 const int dxa = centred_origin(xa, B, W), dya = centred_origin(ya, B, H);
                 if (j == L) {
                     if (rep) make_leaf(leaf[0], xa, ya, j, 1, cur.k, cur.q, 0, 0, 0, dxa, dya, pos);
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
                 const long long thr_p2 = D.t2q[j - 1] << (2 * lg2c + 10); // sub-blocks coded at level j
                 if (Bc >= 8) {
                     const int cgx = Bc / 8, cgy = Bc / 4;
-                    const int cbx = (8 * pc) / Bc, cby = (4 * pr) / Bc;
+                    const int cbx = (8 * pc) >> (lgB - 1), cby = (4 * pr) >> (lgB - 1);
                     const int cxa = sx0 + cbx * Bc, cya = sy0 + cby * Bc;
                     const int cdx = centred_origin(cxa, Bc, W), cdy = centred_origin(cya, Bc, H);
                     const int cu0 = 8 * pc - cbx * Bc, cv0 = 4 * pr - cby * Bc;
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
                     }
                     bool ok_lane;
                     if (Bc >= 8) {
-                        const int cbx = (8 * pc) / Bc, cby = (4 * pr) / Bc;
+                        const int cbx = (8 * pc) >> (lgB - 1), cby = (4 * pr) >> (lgB - 1);
                         const int kk = (cbx & 1) | ((cby & 1) << 1);
                         int bit;
                         // (selects: an indexed array would live in local memory)
@@ -374,7 +377,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
                 if (rep && p2) make_leaf(leaf[0], xa, ya, j, 2, sbits, cur.q, d[0], d[1], d[2], dxa, dya, pos);
                 const bool split = need && !p2;
                 if (rep && split) {
-                    const uint32_t z = morton3(tx / B, ty / B);
+                    const uint32_t z = morton3(tx >> lgB, ty >> lgB);
                     splitbits |= 1u << (((1u << (2 * (j - 1))) - 1) / 3 + z);
                 }
                 act = split;
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
                     fits += 1;
                     const int xa = sx0 + 8 * pc + 4 * h, ya = sy0 + 4 * pr;
                     const int tx = 8 * pc + 4 * h - lane_top * BMAX, ty = 4 * pr;
-                    const int pos = lane_top * cpt + (int)morton3(tx / bmin, ty / bmin);
+                    const int pos = lane_top * cpt + (int)morton3(tx >> lgbmin, ty >> lgbmin);
                     make_leaf(leaf[h], xa, ya, j, 1, cur4[h].k, cur4[h].q, 0, 0, 0, centred_origin(xa, 4, W),
                               centred_origin(ya, 4, H), pos);
                 }
