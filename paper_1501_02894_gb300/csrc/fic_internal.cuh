@@ -134,8 +134,8 @@ struct DecDesc {
 // Fixed-point codebooks (Section 3.3): c = 128 s on 2^s_bits cell midpoints
 // of [-1, 1); luminance levels round(255 q / (2^o_bits - 1)).
 __host__ __device__ inline int contrast_code(int k, int s_bits) {
-    int K = 1 << s_bits;
-    return (2 * k - (K - 1)) * (128 / K);
+    const int K = 1 << s_bits;
+    return (2 * k - (K - 1)) * (128 >> s_bits);  // 128 / K, K a power of two <= 128
 }
 
 // Phase-2 contrast sets of Section 3.2 in the c = round(128 s) fixed point:
