@@ -162,10 +162,12 @@ __global__ void __launch_bounds__(kLWarps * 32, 2)
         leaf[1].pos = -1;
         uint32_t splitbits = 0;
         unsigned fits = 0;
-        const int cpt_side = BMAX / bmin, cpt = cpt_side * cpt_side;
+        // sides are powers of two: divisions by them are shifts
+        const int lgbmin = 31 - __clz(bmin);
+        const int cpt_side = BMAX >> lgbmin, cpt = cpt_side * cpt_side;
         bool act = valid;
-        int B = BMAX;
-        for (int j = 1; j <= L; ++j, B >>= 1) {
+        int B = BMAX, lgB = 31 - __clz(BMAX);
+        for (int j = 1; j <= L; ++j, B >>= 1, --lgB) {
             if (!__any_sync(FULL, act)) break;
             const int lg2n = 2 * (31 - __clz(B));
             const long long thr = D.t2q[j - 1] << (2 * lg2n + 10);
@@ -178,11 +180,11 @@ __global__ void __launch_bounds__(kLWarps * 32, 2)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (B >= 8) {
-                    bxs[h] = (8 * pc) / B;
+                    bxs[h] = (8 * pc) >> lgB;
                 } else {
                     bxs[h] = 2 * pc + h;
                 }
-                bys[h] = (4 * pr) / B;
+                bys[h] = (4 * pr) >> lgB;
                 best[h].g = 0x7fffffffffffffffLL;
                 best[h].k = 0;
                 best[h].dx = best[h].dy = 0;
@@ -257,12 +259,12 @@ __global__ void __launch_bounds__(kLWarps * 32, 2)
                 const bool pass = (j == L) || E < thr;
                 const int tx = bxs[h] * B - lane_top * BMAX, ty = bys[h] * B;
                 if (rep && pass) {
-                    const int pos = lane_top * cpt + (int)morton3(tx / bmin, ty / bmin);
+                    const int pos = lane_top * cpt + (int)morton3(tx >> lgbmin, ty >> lgbmin);
                     make_leaf(leaf[B >= 8 ? 0 : h], xa, ya, j, 1, best[h].k, bq, 0, 0, 0, best[h].dx, best[h].dy, pos);
                 }
                 const bool split = act && !pass;
                 if (rep && split) {
-                    const uint32_t z = morton3(tx / B, ty / B);
+                    const uint32_t z = morton3(tx >> lgB, ty >> lgB);
                     splitbits |= 1u << (((1u << (2 * (j - 1))) - 1) / 3 + z);
                 }
                 split_any = split_any || split;
