@@ -1,6 +1,6 @@
 """Benchmark of the MNS fractal coder on GB300.
 
-Default workload (cfg2): one step = the whole hot path over one batch: the
+Default workload (batch40x512): one step = the whole hot path over one batch: the
 MNS quadtree encode (moments, phase 1, phase 2, split, stream packing) of the
 ten 512x512 synthetic images shaped like the paper's test images (8 scenes +
 2 Voronoi images) at each RMS threshold of the sweep {4, 8, 12, 16} -- 40
@@ -10,18 +10,18 @@ flushed (a 256 MiB write) before every timed step because the inputs
 (10.5 MB) are far smaller than L2.
 
 Other workloads (`--workload`), one JSON line each:
-  cfg1  one 256x256 image, MNS 16->4, RMS 8, decode 10 iterations
-  cfg3  exhaustive search (8 isometries, domain step 4, 8x8 ranges) of a
-        512x512 and a 1024x1024 image: tensor-core and CUDA-core engines
-  cfg4  512 images of mixed sides {256..2048} in one persistent launch per
-        pass (CUDA graphs, autotuned launch mapping), MNS 32->4, RMS 8,
-        decode 8 iterations; against per-image launches with the same output
-  cfg5  serving: Poisson arrivals (2000/s), 80 % encode / 20 % decode,
-        sides log-uniform in [128, 4096], through the library's request
-        server; p50/p99 latency and Mpixel/s against a per-request loop
+  one256      one 256x256 image, MNS 16->4, RMS 8, decode 10 iterations
+  exhaustive  exhaustive search (8 isometries, domain step 4, 8x8 ranges) of a
+              512x512 and a 1024x1024 image: tensor-core and CUDA-core engines
+  mixed512    512 images of mixed sides {256..2048} in one persistent launch per
+              pass (CUDA graphs, autotuned launch mapping), MNS 32->4, RMS 8,
+              decode 8 iterations; against per-image launches with the same output
+  serving     serving: Poisson arrivals (2000/s), 80 % encode / 20 % decode,
+              sides log-uniform in [128, 4096], through the library's request
+              server; p50/p99 latency and Mpixel/s against a per-request loop
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload cfg2|cfg1|cfg3|cfg4|cfg5]
+                  [--workload batch40x512|one256|exhaustive|mixed512|serving]
 
 With N > 1 (torchrun) every rank runs the same workload on its own GPU
 (replicas, weak scaling); rank 0 prints one JSON line.  `--impl reference`
@@ -96,18 +96,18 @@ def gen_images(specs, workers=None):
 
 
 def make_spec(name):
-    if name == "cfg1":
-        return Spec(name, "cfg1: 256x256 scene seed 0, MNS 16->8->4, RMS 8 + decode 10 it",
-                    [(synth.cfg1_image(), "mns", 16, 4, 8.0)], 10)
-    if name == "cfg2":
-        imgs = [im for _, im in synth.cfg2_images()]
-        return Spec(name, "cfg2: 10 x 512x512 (8 scenes seeds 1-8 + 2 Voronoi 101/102) x RMS {4,8,12,16}, "
+    if name == "one256":
+        return Spec(name, "one256: 256x256 scene seed 0, MNS 16->8->4, RMS 8 + decode 10 it",
+                    [(synth.scene256_image(), "mns", 16, 4, 8.0)], 10)
+    if name == "batch40x512":
+        imgs = [im for _, im in synth.scenes512_images()]
+        return Spec(name, "batch40x512: 10 x 512x512 (8 scenes seeds 1-8 + 2 Voronoi 101/102) x RMS {4,8,12,16}, "
                           "MNS 32->4 + decode 10 it",
                     [(im, "mns", 32, 4, t) for t in THRESHOLDS for im in imgs], 10)
-    if name == "cfg4":
-        sides = synth.cfg4_sides()
+    if name == "mixed512":
+        sides = synth.mixed_sides()
         imgs = gen_images([("g", int(s), 1000 + i) for i, s in enumerate(sides)])
-        return Spec(name, "cfg4: 512 scenes, sides {256,512,1024,2048} w .4/.3/.2/.1 (rng 4, seed 1000+i), "
+        return Spec(name, "mixed512: 512 scenes, sides {256,512,1024,2048} w .4/.3/.2/.1 (rng 4, seed 1000+i), "
                           "MNS 32->4, RMS 8 + decode 8 it, one persistent launch per pass",
                     [(im, "mns", 32, 4, 8.0) for im in imgs], 8, autotune=True, plain=True)
     raise ValueError(name)
@@ -316,16 +316,16 @@ def run_reference(args):
         return 0
     threads = os.cpu_count() or 1
     step_s = max(0.5, min(args.ref_step_s, 150.0 / max(1, args.steps + args.warmup)))
-    if args.workload == "cfg3":
-        img = synth.cfg3_images()[1][1]
+    if args.workload == "exhaustive":
+        img = synth.exhaustive_images()[1][1]
         for _ in range(args.warmup):
             time_oracle_exhaustive(img, min(0.5, step_s), threads)
         vals = [time_oracle_exhaustive(img, step_s, threads)[0] for _ in range(args.steps)]
         value, unit, desc = statistics.mean(vals), "fits/s", "exhaustive search, sampled 8x8 ranges of the 1024x1024 image"
         ms, metric = None, "exhaustive-search range-domain fits/s (bit-exact)"
-    elif args.workload == "cfg5":
+    elif args.workload == "serving":
         print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no CPU counterpart; "
-                                                              "the oracle arm covers cfg1-cfg4"}), flush=True)
+                                                              "the oracle arm covers one256-mixed512"}), flush=True)
         return 0
     else:
         spec = make_spec(args.workload)
@@ -348,7 +348,7 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
-# GPU arm: batched encode + decode (cfg1, cfg2, cfg4)
+# GPU arm: batched encode + decode (one256, batch40x512, mixed512)
 
 def run_batched(args, spec: Spec):
     import torch
@@ -655,7 +655,7 @@ def run_batched(args, spec: Spec):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
-    if spec.name in ("cfg1", "cfg2"):
+    if spec.name in ("one256", "batch40x512"):
         line["rate_distortion"], line["bitstream"] = rate_distortion(fic, torch, stream, items, enc, dec, nrec)
     if tuning:
         line["autotune"] = {"encode_best": tuning["encode"]["best"], "encode_best_ms": round(tuning["encode"]["best_ms"], 4),
@@ -767,7 +767,7 @@ def plain_per_image(fic, torch, stream, dimgs, plist, iters, enc, dec, pixels, b
 
 
 # --------------------------------------------------------------------------
-# GPU arm: exhaustive search (cfg3)
+# GPU arm: exhaustive search (exhaustive)
 
 def run_exhaustive(args):
     import torch
@@ -776,7 +776,7 @@ def run_exhaustive(args):
     import paper_1501_02894_gb300 as fic
 
     fic.lib()
-    imgs = synth.cfg3_images()
+    imgs = synth.exhaustive_images()
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     peaks, peak_kind = load_peaks()
@@ -863,7 +863,7 @@ def run_exhaustive(args):
         "n_gpus": world, "steps": max(1, min(args.steps, 20)), "warmup": max(args.warmup, 3),
         "ms_per_step": round(tot_ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f16 operands, f32 accumulate (exact integers), int64 decisions", "data": "synthetic",
-        "config": {"workload": "cfg3: 512x512 seed 1 + 1024x1024 seed 9, 8x8 ranges, domain step 4, 8 isometries",
+        "config": {"workload": "exhaustive: 512x512 seed 1 + 1024x1024 seed 9, 8x8 ranges, domain step 4, 8 isometries",
                    "l2": "flushed (256 MiB write) before every step", "parallelism": f"replicas x{world}"},
         "engines": res, "engines_identical_output": bool(same), "offset_stats": offset_stats,
         "cuda_core_over_tensor_time": round(sum(v["ms"] for v in res["cuda_cores"].values()) / tot_ms, 3),
@@ -883,11 +883,11 @@ def run_exhaustive(args):
 
 
 # --------------------------------------------------------------------------
-# GPU arm: serving (cfg5)
+# GPU arm: serving (serving)
 
 def run_serving(args):
     t_setup = time.perf_counter()
-    t_arr, is_enc, side, seeds = synth.cfg5_requests(rate=args.rate, seconds=args.serve_s)
+    t_arr, is_enc, side, seeds = synth.serving_requests(rate=args.rate, seconds=args.serve_s)
     nreq = len(t_arr)
     # image pool: one image per distinct side, from the seed of the first
     # request of that side (generating every request's own image is
@@ -1027,7 +1027,7 @@ def run_serving(args):
         "metric": "served MNS encode/decode Mpixel/s with p50/p99 latency (bit-exact)", "value": round(value, 3),
         "unit": "Mpixel/s", "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": round(t_s * 1e3, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"cfg5: Poisson {args.rate:.0f} req/s for {args.serve_s:.0f} s, 80% encode / 20% "
+        "config": {"workload": f"serving: Poisson {args.rate:.0f} req/s for {args.serve_s:.0f} s, 80% encode / 20% "
                                f"decode (8 it), sides log-uniform [128,4096] step 32, MNS 32->4 RMS 8; one pool image "
                                f"per side", "requests": nreq, "distinct_sides": len(sides),
                    "hbm_budget_gb": args.hbm_budget_gb, "server": "4 streams, batches of <= 64 jobs"},
@@ -1061,20 +1061,20 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"])
+    ap.add_argument("--workload", default="batch40x512", choices=["one256", "batch40x512", "exhaustive", "mixed512", "serving"])
     ap.add_argument("--cpu-s", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=10.0, help="oracle seconds per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--heat-s", type=float, default=2.0, help="busy seconds before the timed steps (clock sampling)")
-    ap.add_argument("--rate", type=float, default=2000.0, help="cfg5: arrivals per second")
-    ap.add_argument("--serve-s", type=float, default=60.0, help="cfg5: seconds of arrivals")
-    ap.add_argument("--hbm-budget-gb", type=float, default=40.0, help="cfg5: server device memory")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: arrivals per second")
+    ap.add_argument("--serve-s", type=float, default=60.0, help="serving: seconds of arrivals")
+    ap.add_argument("--hbm-budget-gb", type=float, default=40.0, help="serving: server device memory")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "cfg3":
+    if args.workload == "exhaustive":
         return run_exhaustive(args)
-    if args.workload == "cfg5":
+    if args.workload == "serving":
         return run_serving(args)
     return run_batched(args, make_spec(args.workload))
 

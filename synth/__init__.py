@@ -9,10 +9,10 @@ from .images import (  # noqa: F401
     gaussian_scene,
     voronoi,
     constant,
-    cfg1_image,
-    cfg2_images,
-    cfg3_images,
-    cfg4_sides,
-    cfg4_images,
-    cfg5_requests,
+    scene256_image,
+    scenes512_images,
+    exhaustive_images,
+    mixed_sides,
+    mixed_images,
+    serving_requests,
 )

@@ -23,8 +23,8 @@ import math
 import numpy as np
 
 __all__ = [
-    "gaussian_scene", "voronoi", "constant", "cfg1_image", "cfg2_images",
-    "cfg3_images", "cfg4_sides", "cfg4_images", "cfg5_requests",
+    "gaussian_scene", "voronoi", "constant", "scene256_image", "scenes512_images",
+    "exhaustive_images", "mixed_sides", "mixed_images", "serving_requests",
 ]
 
 
@@ -88,36 +88,36 @@ def constant(N: int, value: int, H: int | None = None) -> np.ndarray:
 
 # ---- workload recipes (one per measured configuration) -------------------
 
-def cfg1_image() -> np.ndarray:
+def scene256_image() -> np.ndarray:
     """256x256 scene, seed 0 (MNS 16->8->4, RMS threshold 8, decode 10 its)."""
     return gaussian_scene(256, 0)
 
 
-def cfg2_images() -> list[tuple[str, np.ndarray]]:
+def scenes512_images() -> list[tuple[str, np.ndarray]]:
     """512x512: scenes with seeds 1..8 and Voronoi images with seeds 101, 102."""
     out = [(f"scene{s}", gaussian_scene(512, s)) for s in range(1, 9)]
     out += [(f"voronoi{s}", voronoi(512, s)) for s in (101, 102)]
     return out
 
 
-def cfg3_images() -> list[tuple[str, np.ndarray]]:
+def exhaustive_images() -> list[tuple[str, np.ndarray]]:
     """Exhaustive-search workloads: 512x512 seed 1 and 1024x1024 seed 9."""
     return [("scene1_512", gaussian_scene(512, 1)), ("scene9_1024", gaussian_scene(1024, 9))]
 
 
-def cfg4_sides(count: int = 512) -> np.ndarray:
+def mixed_sides(count: int = 512) -> np.ndarray:
     """Mixed sides {256,512,1024,2048} with weights .4/.3/.2/.1 from rng(4)."""
     rng = np.random.default_rng(4)
     return rng.choice(np.array([256, 512, 1024, 2048]), size=count, p=[0.4, 0.3, 0.2, 0.1])
 
 
-def cfg4_images(count: int = 512):
+def mixed_images(count: int = 512):
     """Yield (index, image) for the mixed-size batch; image i uses seed 1000+i."""
-    for i, s in enumerate(cfg4_sides(count)):
+    for i, s in enumerate(mixed_sides(count)):
         yield i, gaussian_scene(int(s), 1000 + i)
 
 
-def cfg5_requests(rate: float = 2000.0, seconds: float = 60.0, encode_frac: float = 0.8):
+def serving_requests(rate: float = 2000.0, seconds: float = 60.0, encode_frac: float = 0.8):
     """Poisson arrival times, request kinds and sides for the serving workload.
 
     Returns arrays (t_arrival [s], is_encode [bool], side [px], seed).  Sides

@@ -23,7 +23,7 @@ def fic():
 
 def test_mixed_batch_512_images_sampled(fic, orc):
     import bench
-    sides = synth.cfg4_sides()
+    sides = synth.mixed_sides()
     imgs = bench.gen_images([("g", int(s), 1000 + i) for i, s in enumerate(sides)])
     p = fic.params("mns", 32, 4, 8.0)
     d = [torch.from_numpy(im).cuda() for im in imgs]

@@ -61,19 +61,19 @@ def _check_image(fic, orc, img, mode="mns", bmax=32, bmin=4, thr=8.0, iters=10, 
     return got
 
 
-def test_cfg1_scene_256(fic, orc):
+def test_scene_256(fic, orc):
     """256x256 scene seed 0, MNS 16->8->4, RMS 8, decode 10 iterations."""
-    _check_image(fic, orc, synth.cfg1_image(), "mns", 16, 4, 8.0, iters=10)
+    _check_image(fic, orc, synth.scene256_image(), "mns", 16, 4, 8.0, iters=10)
 
 
 @pytest.mark.parametrize("thr", [4.0, 8.0, 12.0, 16.0])
 @pytest.mark.parametrize("mode", ["mns", "nosearch"])
-def test_cfg2_scene_512(fic, orc, thr, mode):
+def test_scene_512(fic, orc, thr, mode):
     _check_image(fic, orc, synth.gaussian_scene(512, 1), mode, 32, 4, thr, iters=10)
 
 
 @pytest.mark.parametrize("seed", [101, 102])
-def test_cfg2_voronoi_512(fic, orc, seed):
+def test_voronoi_512(fic, orc, seed):
     _check_image(fic, orc, synth.voronoi(512, seed), "mns", 32, 4, 8.0, iters=8)
 
 
@@ -142,7 +142,7 @@ def test_batch_matches_single_and_oracle(fic, orc):
 def test_bench_workload_full_size(fic, orc):
     """The benchmark's launch: ten 512x512 images x four thresholds in one
     batch (40 encodes) and a batched 10-iteration decode, all bit-exact."""
-    imgs = [im for _, im in synth.cfg2_images()]
+    imgs = [im for _, im in synth.scenes512_images()]
     thrs = [4.0, 8.0, 12.0, 16.0]
     batch = [(im, t) for t in thrs for im in imgs]
     plist = [fic.params("mns", 32, 4, t) for _, t in batch]
@@ -275,7 +275,7 @@ def test_decode_single_launch_and_per_iteration_launches(fic, orc, bmax, bmin, s
 # Phase 2 with the other domain reading: quadrants of the parent's domain
 
 @pytest.mark.parametrize("img_fn,bmax,bmin,thr", [
-    (lambda: synth.cfg1_image(), 16, 4, 8.0),
+    (lambda: synth.scene256_image(), 16, 4, 8.0),
     (lambda: synth.gaussian_scene(512, 1), 32, 4, 6.0),
     (lambda: synth.gaussian_scene(256, 44), 32, 8, 10.0),
     (lambda: synth.voronoi(256, 101), 16, 4, 4.0),

@@ -348,8 +348,8 @@ def _check_encoding(orc, img, p):
 
 @pytest.mark.parametrize("thr", [8.0, 4.0])
 @pytest.mark.parametrize("p2d", [0, 1])
-def test_decisions_rederived_cfg1(orc, thr, p2d):
-    img = synth.cfg1_image()
+def test_decisions_rederived_scene256(orc, thr, p2d):
+    img = synth.scene256_image()
     p = orc.make_params("mns", 16, 4, thr, phase2_domain=p2d)
     leaves = _check_encoding(orc, img, p)
     assert (leaves["phase"] == 2).any() or thr == 4.0
@@ -430,7 +430,7 @@ def test_local_finds_planted_offset(orc):
 # Decoder
 
 def test_decoder_first_iterate_is_luminance(orc):
-    img = synth.cfg1_image()
+    img = synth.scene256_image()
     p = orc.make_params("mns", 16, 4, 8.0)
     leaves, _, _ = orc.encode(img, p)
     x1 = orc.decode(leaves, 256, 256, p, 1)
@@ -451,7 +451,7 @@ def test_decoder_first_iterate_is_luminance(orc):
 
 @pytest.mark.parametrize("p2d", [0, 1])
 def test_decoder_second_iterate_direct(orc, p2d):
-    img = synth.cfg1_image()
+    img = synth.scene256_image()
     p = orc.make_params("mns", 16, 4, 8.0, phase2_domain=p2d)
     leaves, _, _ = orc.encode(img, p)
     x1 = orc.decode(leaves, 256, 256, p, 1)
@@ -528,7 +528,7 @@ def test_decoder_converges(orc):
     """Within 64 iterations the iterates settle into a band of at most 1 LSB
     (integer rounding leaves a few pixels flickering between neighbouring
     values), and the attractor is close to the image."""
-    img = synth.cfg1_image()
+    img = synth.scene256_image()
     p = orc.make_params("mns", 16, 4, 8.0)
     leaves, _, _ = orc.encode(img, p)
     seq = [orc.decode(leaves, 256, 256, p, it) for it in range(1, 65)]
@@ -608,7 +608,7 @@ def test_bad_sizes_rejected(orc):
 def test_phase2_domain_readings_differ(orc):
     """The two readings of the phase-2 domain give different streams (both
     re-derived above); phase 1 and the split rule are shared."""
-    img = synth.cfg1_image()
+    img = synth.scene256_image()
     a, _, _ = orc.encode(img, orc.make_params("mns", 16, 4, 8.0, phase2_domain=0))
     b, _, _ = orc.encode(img, orc.make_params("mns", 16, 4, 8.0, phase2_domain=1))
     assert (a["phase"] == 2).any() and (b["phase"] == 2).any()
