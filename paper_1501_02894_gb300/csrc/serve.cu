@@ -203,7 +203,7 @@ struct fic_server {
     int64_t next_ticket = 1;
     bool stopping = false;
     std::thread worker;
-    CopyPool copies{3};
+    CopyPool copies{6};  // helpers: host copies of big images and results at high request rates
 
     // statistics
     int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batched_jobs = 0;
