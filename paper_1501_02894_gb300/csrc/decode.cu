@@ -310,12 +310,18 @@ __global__ void __launch_bounds__(kDecWarps * 32)
     __shared__ int s_base[kImgTable];
     __shared__ uint4 s_recs[kDecWarps][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the descriptors come from the host (uploaded when the plan was made)
+    if (count <= kImgTable)
+        for (int i = threadIdx.x; i < count; i += blockDim.x) s_base[i] = descs[i].strip_base;
+    // Programmatic dependent launch: the table above may be built while the
+    // previous kernel (the stream packer, or whatever wrote the records)
+    // finishes; nothing of the decode's workspace or of its inputs is read
+    // or written before that kernel has completed.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (bar && blockIdx.x == 0 && threadIdx.x == 0) {
         bar[0] = 0u;  // grid-barrier words of the single-launch iterations
         bar[1] = 0u;
     }
-    if (count <= kImgTable)
-        for (int i = threadIdx.x; i < count; i += blockDim.x) s_base[i] = descs[i].strip_base;
     __syncthreads();
     const int gwarps = gridDim.x * kDecWarps;
     for (int g = blockIdx.x * kDecWarps + warp; g < total_strips; g += gwarps)
@@ -795,15 +801,17 @@ static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, 
         if (e != cudaSuccess) return e;
         const int gs = sms * per;
         // the setup kernel also writes the first iterate (pixels when it is the only one)
-        decode_setup_kernel<BMAX, true><<<need < gs ? need : gs, kDecWarps * 32, 0, st>>>(
-            descs, count, total_strips, tables, tfw, tgw, iters == 1 ? 3 : 1, bar);
+        e = launch_pdl(decode_setup_kernel<BMAX, true>, need < gs ? need : gs, kDecWarps * 32, 0, st, descs, count,
+                       total_strips, tables, tfw, tgw, iters == 1 ? 3 : 1, bar);
+        if (e != cudaSuccess) return e;
     } else {
         cudaError_t e = kernel_slots(ks_setup_px, (const void *)decode_setup_kernel<BMAX, false>, kDecWarps * 32, 0,
                                      sms, per);
         if (e != cudaSuccess) return e;
         const int gs = sms * per;
-        decode_setup_kernel<BMAX, false><<<need < gs ? need : gs, kDecWarps * 32, 0, st>>>(descs, count, total_strips,
-                                                                                         tables, tfw, tgw, 0, nullptr);
+        e = launch_pdl(decode_setup_kernel<BMAX, false>, need < gs ? need : gs, kDecWarps * 32, 0, st, descs, count,
+                       total_strips, tables, tfw, tgw, 0, (uint32_t *)nullptr);
+        if (e != cudaSuccess) return e;
     }
     stage_mark(st, "decode_setup_kernel");
     cudaError_t e = cudaGetLastError();

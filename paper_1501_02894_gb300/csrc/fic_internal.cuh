@@ -93,6 +93,24 @@ inline cudaError_t kernel_slots(KernelSlots &ks, const void *fn, int threads, si
     return cudaSuccess;
 }
 
+// Launch `kernel` as a programmatic dependent of the previous kernel on the
+// stream (it must execute griddepcontrol.wait before touching anything that
+// kernel wrote).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Per-kernel timing of a plan run (fic_plan_run_timed): launchers call this
 // after every kernel launch; it records an event only while a timed run is
 // active on the calling thread.

@@ -32,6 +32,9 @@ __global__ void __launch_bounds__(kPackWarps * 32)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned FULL = 0xffffffffu;
     const int c = blockIdx.x;
+    // the decoder setup that may follow can be scheduled as this grid's CTAs
+    // retire (it waits for this grid's completion before reading its output)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (count <= kImgTable)
         for (int i = threadIdx.x; i < count; i += blockDim.x) s_cb[i] = descs[i].chunk_base;
     __syncthreads();
