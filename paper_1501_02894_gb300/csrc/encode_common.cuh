@@ -26,11 +26,15 @@ __device__ __forceinline__ int lum(int q, int ko1, uint32_t magic) {
 // settled by exact int64 comparisons against the grid midpoints; ties go to
 // the smaller |c|, then to c > 0.  A flat domain (nCdd = 0, hence nCdr = 0)
 // gives the smallest positive code.
+// FAST: the estimate's division by the fast intrinsic (measured faster in the
+// quadtree encoders, slower in the CUDA-core exhaustive search, whose hot
+// loop compiles differently around it); the result is exact either way.
+template <bool FAST = false>
 __device__ __forceinline__ int best_contrast(long long ncdr, long long ncdd, int s_bits) {
     const int K = 1 << s_bits, step = 256 >> s_bits;
     if (ncdd <= 0) return K >> 1;
-    // an estimate only (settled exactly below): the fast division suffices
-    float cs = __fdividef(512.f * (float)ncdr, (float)ncdd);
+    // an estimate only, settled exactly below
+    float cs = FAST ? __fdividef(512.f * (float)ncdr, (float)ncdd) : 512.f * (float)ncdr / (float)ncdd;
     float kf = (cs + 128.f) / (float)step - 0.5f;
     kf = fminf(fmaxf(kf, 0.f), (float)(K - 1));
     int k = __float2int_rn(kf);
@@ -85,7 +89,7 @@ __device__ __forceinline__ void fit_phase1(int sr, int srr, int sd, int sdd, int
     f.ncrr = ((long long)srr << lg2n) - (long long)sr * sr;
     f.ncdr = ((long long)sdr << lg2n) - (long long)sd * sr;
     f.ncdd = ((long long)sdd << lg2n) - (long long)sd * sd;
-    const int k = best_contrast(f.ncdr, f.ncdd, s_bits);
+    const int k = best_contrast<true>(f.ncdr, f.ncdd, s_bits);
     int bd;
     const int bq = best_luminance(sr, lg2n, ko1, magic, qscale, bd);
     f.k = k;

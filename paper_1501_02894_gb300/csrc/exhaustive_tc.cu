@@ -105,7 +105,7 @@ struct TcRow {
 __device__ __noinline__ TcRow tc_exact(TcRow b, int d, float acc, int sr, int4 ds, int s_bits) {
     const int ncdr = 64 * __float2int_rn(acc) - ds.x * sr;
     const uint32_t ncdd = (uint32_t)ds.y;
-    const int k = best_contrast((long long)ncdr, (long long)ncdd, s_bits);
+    const int k = best_contrast<true>((long long)ncdr, (long long)ncdd, s_bits);
     const long long c = contrast_code(k, s_bits);
     const long long g = c * c * (long long)ncdd - 1024LL * c * ncdr;
     if (exh_better(g, d, b.g, b.d)) {
