@@ -17,16 +17,12 @@
 //     leaf with one popcount) packed into one word: window column/row of its
 //     domain values, block side, contrast byte, luminance; plus a per-strip
 //     word.  It also writes the first iterate (from 128: the luminances).
-//   * decode_d4_iter_kernel (centred streams, once per later iteration, each
-//     launch a programmatic dependent of the previous kernel) iterates on
-//     2x2-sum images (below); decode_d4_loop_kernel runs all those
-//     iterations in one cooperative launch with grid barriers (a tuning
-//     option); decode_iter_kernel (other streams) stages the decimated
-//     window of the previous pixel iterate.  All read 16 domain values per
-//     half-patch, reduce Sd4 per transform with xor shuffles (one warp
-//     reduction when a single transform covers the strip), then per pixel
-//     one dp2a (select + multiply + offset), one shift and half of a
-//     saturating pack.
+//   * decode_d4_iter_kernel (centred streams, once per later iteration):
+//     iterates on 2x2-sum images (below); decode_iter_kernel (other streams):
+//     stages the decimated window of the previous pixel iterate.  Both read
+//     16 domain values per half-patch, reduce Sd4 per transform with xor
+//     shuffles, then per pixel one dp2a (select + multiply + offset), one
+//     shift and half of a saturating pack.
 // Domains that are not centred (local / exhaustive search, isometries) are
 // read from global memory instead of the staged window.
 #include "fic_internal.cuh"
