@@ -134,7 +134,7 @@ class CopyPool {
     }
 
   private:
-    static constexpr size_t kChunk = 1 << 20;
+    static constexpr size_t kChunk = 256 << 10;  // copies of 512 KiB and more are split
     struct Task {
         uint8_t *dst;
         const uint8_t *src;
