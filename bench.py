@@ -1030,11 +1030,20 @@ def run_serving(args):
         t_end = time.perf_counter() - t0
         return lat[:served], px_done, t_end, served
 
-    sampler = ClockSampler(gpu_uuid(torch, dev))
-    sampler.start()
-    lat_s, px_s, t_s, stats, q_s = serve_with_server()
-    clocks = sampler.stop()
-    lat_p, px_p, t_p, served_p = serve_plain()
+    # the client's own pauses would count as request latency: no cyclic
+    # garbage collection while a trace is replayed
+    import gc
+    gc.collect()
+    gc.disable()
+    try:
+        sampler = ClockSampler(gpu_uuid(torch, dev))
+        sampler.start()
+        lat_s, px_s, t_s, stats, q_s = serve_with_server()
+        clocks = sampler.stop()
+        gc.collect()
+        lat_p, px_p, t_p, served_p = serve_plain()
+    finally:
+        gc.enable()
 
     def pct(a, q):
         return round(float(np.percentile(a, q)), 3) if len(a) else None
