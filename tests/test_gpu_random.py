@@ -58,3 +58,33 @@ def test_random_configuration(orc, case):
     assert np.array_equal(got["split"], split) and got["fits"] == fits
     dec = fic.fic_decode(st, iters).cpu().numpy()
     assert np.array_equal(dec, orc.decode(leaves, W, H, op, iters))
+
+
+@pytest.mark.parametrize("b", range(8))
+def test_random_batches_equal_single_calls(b):
+    """A batch of images of random sizes (one bmax and mode, thresholds per
+    image) in one plan equals the images encoded and decoded one by one."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1501_02894_gb300 as fic
+    rng = np.random.default_rng(500 + b)
+    bmax = int(rng.choice([8, 16, 32]))
+    mode = str(rng.choice(["mns", "nosearch"]))
+    imgs, plist = [], []
+    for k in range(int(rng.integers(2, 10))):
+        W, H = bmax * int(rng.integers(2, 16)), bmax * int(rng.integers(2, 10))
+        W += (-W) % 16
+        H += (-H) % 16
+        imgs.append(synth.gaussian_scene(W, 6000 + 50 * b + k, H=H))
+        plist.append(fic.params(mode, bmax, 4, float(rng.uniform(2, 16))))
+    plan = fic.EncodePlan([torch.from_numpy(im).cuda() for im in imgs], plist)
+    plan.run()
+    dplan = fic.DecodePlan(plan.outs)
+    dplan.run(7)
+    torch.cuda.synchronize()
+    for im, p, st, out in zip(imgs, plist, plan.outs, dplan.outs):
+        ref = fic.fic_encode(torch.from_numpy(im).cuda(), p)
+        a, r = st.to_host(), ref.to_host()
+        assert np.array_equal(a["records"].view(np.uint8), r["records"].view(np.uint8))
+        assert np.array_equal(a["split"], r["split"]) and a["fits"] == r["fits"]
+        assert np.array_equal(out.cpu().numpy(), fic.fic_decode(ref, 7).cpu().numpy())
