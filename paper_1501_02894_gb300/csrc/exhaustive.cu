@@ -152,7 +152,34 @@ __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
         }
         __syncthreads();
         const int nj = min(kExhStage, E.nd - d0);
-        for (int j = 0; j < nj; ++j) {
+        int j = 0;
+        // four domains at a time: four independent dp2a chains, and one
+        // branch on the largest screen margin (the threshold only rises as
+        // the row's best improves, so no margin >= 0 means nothing to evaluate)
+        for (; j + 4 <= nj; j += 4) {
+            unsigned acc[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint4 p = reinterpret_cast<const uint4 *>(s_dp[j + u])[i];
+                    acc[u] = dp2a_lo(p.x, aw[2 * i], acc[u]);
+                    acc[u] = dp2a_hi(p.y, aw[2 * i], acc[u]);
+                    acc[u] = dp2a_lo(p.z, aw[2 * i + 1], acc[u]);
+                    acc[u] = dp2a_hi(p.w, aw[2 * i + 1], acc[u]);
+                }
+            }
+            float m = -__int_as_float(0x7f800000);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) m = fmaxf(m, exh_screen((float)acc[u], (float)sr, s_cs[j + u]) - best.thr);
+            if (live && m >= 0.f) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (exh_screen((float)acc[u], (float)sr, s_cs[j + u]) >= best.thr)
+                        exh_exact(best, d0 + j + u, (int)acc[u], sr, s_ds[j + u], E.s_bits);
+            }
+        }
+        for (; j < nj; ++j) {
             unsigned acc = 0;
             const uint4 *q = reinterpret_cast<const uint4 *>(s_dp[j]);
 #pragma unroll
