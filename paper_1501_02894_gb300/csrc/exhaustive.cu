@@ -154,8 +154,9 @@ __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
         const int nj = min(kExhStage, E.nd - d0);
         int j = 0;
         // four domains at a time: four independent dp2a chains, and one
-        // branch on the largest screen margin (the threshold only rises as
-        // the row's best improves, so no margin >= 0 means nothing to evaluate)
+        // branch on their largest screen value (the threshold only rises as
+        // the row's best improves, so a largest value below it means nothing
+        // to evaluate)
         for (; j + 4 <= nj; j += 4) {
             unsigned acc[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
@@ -171,8 +172,8 @@ __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
             }
             float m = -__int_as_float(0x7f800000);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) m = fmaxf(m, exh_screen((float)acc[u], (float)sr, s_cs[j + u]) - best.thr);
-            if (live && m >= 0.f) {
+            for (int u = 0; u < 4; ++u) m = fmaxf(m, exh_screen((float)acc[u], (float)sr, s_cs[j + u]));
+            if (live && m >= best.thr) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     if (exh_screen((float)acc[u], (float)sr, s_cs[j + u]) >= best.thr)

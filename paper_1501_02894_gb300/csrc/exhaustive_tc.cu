@@ -294,14 +294,14 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kTcCols + col), v);
                 const int dbase = (t0 + n) * kTcCols + col;
                 const float4 *cs = wc + acc * 64 + c0;
-                // the batch's largest screen margin first, without branches (the
+                // the batch's largest screen value first, without branches (the
                 // 32 screens schedule as independent chains); the threshold only
-                // rises as the row's best improves, so a batch with no margin >= 0
-                // holds no candidate to evaluate
+                // rises as the row's best improves, so a batch whose largest value
+                // is below it holds no candidate to evaluate
                 float m = -__int_as_float(0x7f800000);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) m = fmaxf(m, exh_screen(v[j], srf, cs[j]) - best.thr);
-                if (m >= 0.f) {
+                for (int j = 0; j < 32; ++j) m = fmaxf(m, exh_screen(v[j], srf, cs[j]));
+                if (m >= best.thr) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         if (exh_screen(v[j], srf, cs[j]) >= best.thr)
