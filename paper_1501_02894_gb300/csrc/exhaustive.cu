@@ -46,7 +46,7 @@ __global__ void exh_prep_domains(ExhDesc E) {
         const float k512 = ncdd > 0 ? 512.f / (float)ncdd : 0.f;
         E.dstat[d] = make_int4(sd, (int)(uint32_t)ncdd, __float_as_int(k512), 1);
         const float sw = ncdd > 0 ? sqrtf(262144.f / (float)ncdd) : 0.f;
-        E.dscr[d] = make_float4(-(float)sd, sw, 130.f * sw, 0.f);
+        E.dscr[d] = make_float4(-(float)sd * 0.015625f, 64.f * sw, 130.f * sw, 0.f);
     }
 }
 

@@ -26,7 +26,7 @@ struct ExhDesc {
     uint32_t *dpairs;         // [nd][32]   packed (d4, d4) pairs for dp2a
     __half *dfp16;            // [nd_pad][64] decimated domains, K-major, fp16
     int4 *dstat;              // [nd_pad]   Sd, nCdd (u32), 512/nCdd (float bits), valid
-    float4 *dscr;             // [nd_pad]   screening constants: -Sd, sqrt(512^2/nCdd), 130 * that, 0
+    float4 *dscr;             // [nd_pad]   screening constants: -Sd/64, 64 sqrt(512^2/nCdd), 130 sqrt(512^2/nCdd), 0
                               //            (NaN: padding)
     __half *afp16;            // [nr * 8][64] range rows permuted per isometry, fp16
     int4 *rstat;              // [nr]       Sr, Srr
@@ -60,14 +60,16 @@ __host__ __device__ inline void exh_iso_src(int t, int B, int u, int v, int &su,
 // c^2 nCdd - 1024 c nCdr is smallest at c* = 512 nCdr / nCdd, where it is
 // -L with L = 512^2 nCdr^2 / nCdd; the grid's best code can only do worse,
 // so a candidate with L < -g (g the row's best exact error) cannot win.  The
-// screen compares square roots: v = (|nCdr~| + 130) sqrt(512^2 / nCdd) with
-// nCdr~ = 64 Sdr - Sd Sr formed in float (at most 64 of absolute rounding
-// error: |nCdr| < 2^31, Sdr exact below 2^24), so sqrt(L) <= v (1 + 3e-7);
-// the row threshold sqrt(-g (1 - 1e-5) - 1) (1 - 1e-6) (or -1 while g >= 0)
-// covers those relative errors, and a candidate is evaluated exactly (int64)
-// only when v reaches it.  Padding domains carry NaN and never pass.
+// screen compares square roots: v = (64 |a| + 130) sqrt(512^2 / nCdd) with
+// a = Sdr - (Sd / 64) Sr, nCdr / 64 formed by one fused multiply-add (Sd / 64
+// and Sdr, below 2^24, are exact; |nCdr| < 2^31 bounds the single rounding
+// by 1, so 64 a is nCdr within 64), so sqrt(L) <= v (1 + 3e-7); the row
+// threshold sqrt(-g (1 - 1e-5) - 1) (1 - 1e-6) (or -1 while g >= 0) covers
+// those relative errors, and a candidate is evaluated exactly (int64) only
+// when v reaches it.  cs = (-Sd / 64, 64 sqrt(512^2 / nCdd), 130 sqrt(512^2 /
+// nCdd)); padding domains carry NaN and never pass.
 __device__ __forceinline__ float exh_screen(float sdr_f, float sr_f, float4 cs) {
-    const float a = fmaf(sdr_f, 64.f, cs.x * sr_f);
+    const float a = fmaf(cs.x, sr_f, sdr_f);
     return fmaf(fabsf(a), cs.y, cs.z);
 }
 
