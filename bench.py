@@ -98,7 +98,7 @@ def gen_images(specs, workers=None):
 def make_spec(name):
     if name == "one256":
         return Spec(name, "one256: 256x256 scene seed 0, MNS 16->8->4, RMS 8 + decode 10 it",
-                    [(synth.scene256_image(), "mns", 16, 4, 8.0)], 10)
+                    [(synth.scene256_image(), "mns", 16, 4, 8.0)], 10, autotune=True)
     if name == "batch40x512":
         imgs = [im for _, im in synth.scenes512_images()]
         return Spec(name, "batch40x512: 10 x 512x512 (8 scenes seeds 1-8 + 2 Voronoi 101/102) x RMS {4,8,12,16}, "
