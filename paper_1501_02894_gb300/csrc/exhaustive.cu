@@ -75,12 +75,14 @@ __global__ void exh_prep_ranges(ExhDesc E) {
 struct ExhRow {
     long long g;  // best exact s-part error
     float thr;    // screening threshold of g (exh_threshold)
+    float thra;   // threshold on |a| (exh_threshold_a)
     int d, k;
 };
 
 __device__ __forceinline__ void exh_row_init(ExhRow &b) {
     b.g = 0x7fffffffffffffffLL;
     b.thr = __int_as_float(0xff800000);  // -inf: everything passes
+    b.thra = -1.f;
     b.d = -1;
     b.k = 0;
 }
@@ -97,6 +99,7 @@ __device__ __forceinline__ void exh_exact(ExhRow &b, int d, int sdr, int sr, int
     if (exh_better(g, d, b.g, b.d)) {
         b.g = g;
         b.thr = exh_threshold(g);
+        b.thra = exh_threshold_a(g, s_bits);
         b.d = d;
         b.k = k;
     }
@@ -175,9 +178,11 @@ __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
             for (int u = 0; u < 4; ++u) m = fmaxf(m, exh_screen((float)acc[u], (float)sr, s_cs[j + u]));
             if (live && m >= best.thr) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (exh_screen((float)acc[u], (float)sr, s_cs[j + u]) >= best.thr)
+                for (int u = 0; u < 4; ++u) {
+                    float aa;
+                    if (exh_screen_abs((float)acc[u], (float)sr, s_cs[j + u], aa) >= best.thr && aa >= best.thra)
                         exh_exact(best, d0 + j + u, (int)acc[u], sr, s_ds[j + u], E.s_bits);
+                }
             }
         }
         for (; j < nj; ++j) {
@@ -191,7 +196,8 @@ __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
                 acc = dp2a_lo(p.z, aw[2 * i + 1], acc);
                 acc = dp2a_hi(p.w, aw[2 * i + 1], acc);
             }
-            if (live && exh_screen((float)acc, (float)sr, s_cs[j]) >= best.thr)
+            float aa;
+            if (live && exh_screen_abs((float)acc, (float)sr, s_cs[j], aa) >= best.thr && aa >= best.thra)
                 exh_exact(best, d0 + j, (int)acc, sr, s_ds[j], E.s_bits);
         }
     }

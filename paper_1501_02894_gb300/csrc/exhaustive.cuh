@@ -73,6 +73,27 @@ __device__ __forceinline__ float exh_screen(float sdr_f, float sr_f, float4 cs) 
     return fmaf(fabsf(a), cs.y, cs.z);
 }
 
+// The magnitude |a| of the screen's a = nCdr / 64 as well: the CUDA-core
+// engine's per-candidate pass uses both.
+__device__ __forceinline__ float exh_screen_abs(float sdr_f, float sr_f, float4 cs, float &abs_a) {
+    abs_a = fabsf(fmaf(cs.x, sr_f, sdr_f));
+    return fmaf(abs_a, cs.y, cs.z);
+}
+
+// Second necessary condition, from the contrast range: at a code |c| <= C =
+// 128 - 128 / 2^s_bits the score c^2 nCdd - 1024 c nCdr is at least
+// -1024 C |nCdr|, so a candidate that can reach g has |nCdr| / 64 >=
+// -g / (65536 C), and the screen's |a| (within 1 of |nCdr| / 64) is at least
+// that minus 1.  It rejects domains that correlate well with the range but
+// would need a contrast outside the codebook (the square-root screen ignores
+// the range of c).  The threshold -g (1 - 1e-5) / (65536 C) - 1 covers the
+// float roundings; -1 while g >= 0 (everything passes).
+__device__ __forceinline__ float exh_threshold_a(long long g, int s_bits) {
+    if (g >= 0) return -1.f;
+    const float C = (float)(128 - (128 >> s_bits));
+    return (float)(-g) * ((1.f - 1e-5f) / (65536.f * C)) - 1.f;
+}
+
 __device__ __forceinline__ float exh_threshold(long long g) {
     const float t = (float)(-g) * (1.f - 1e-5f) - 1.f;
     return t > 0.f ? sqrtf(t) * (1.f - 1e-6f) : -1.f;

@@ -10,7 +10,11 @@ when L >= -g.  The kernels decide "evaluate exactly" in float32:
     v  = fma(|a|, cs.y, cs.z)
     thr(g) = sqrt(-g (1 - 1e-5) - 1) (1 - 1e-6), or -1 when that is not positive
 
-and evaluate when v >= thr(g).  This test replays that arithmetic bit for bit
+and, in the CUDA-core engine's per-candidate pass, also |a| >= thra(g) = -g (1 - 1e-5) / (65536 C) - 1
+(or -1 while g >= 0), C = 128 - 128 / 2^s_bits the largest contrast code: at
+|c| <= C the score is at least -1024 C |nCdr|.  A candidate can reach g only if
+-g <= M, M the largest value of 1024 c nCdr - c^2 nCdd over real c in [-C, C]
+(M <= L).  Evaluate when both hold.  This test replays that arithmetic bit for bit
 (IEEE float32 round-to-nearest for every step, fused multiply-adds rounded once
 from the exact value) on blocks built to stress it -- the largest sums,
 near-flat domains, perfectly (anti)correlated pairs -- with g at the tightest
@@ -49,13 +53,30 @@ def fma_f32(a, b, c) -> np.float32:
     return round_f32(Fraction(float(a)) * Fraction(float(b)) + Fraction(float(c)))
 
 
-def screen_value(sdr: int, sd: int, sr: int, ncdd: int) -> np.float32:
+def screen_value(sdr: int, sd: int, sr: int, ncdd: int, with_a=False):
     sw = np.sqrt(F32(262144.0) / F32(ncdd)) if ncdd > 0 else F32(0.0)
     cx = F32(-F32(sd)) * F32(0.015625)
     cy = F32(64.0) * sw
     cz = F32(130.0) * sw
-    a = fma_f32(cx, F32(sr), F32(sdr))
-    return fma_f32(abs(a), cy, cz)
+    a = abs(fma_f32(cx, F32(sr), F32(sdr)))
+    v = fma_f32(a, cy, cz)
+    return (v, a) if with_a else v
+
+
+def threshold_a(g: int, s_bits: int) -> np.float32:
+    if g >= 0:
+        return F32(-1.0)
+    c = F32(128 - (128 >> s_bits))
+    k = (F32(1.0) - F32(1e-5)) / (F32(65536.0) * c)
+    return F32(F32(-g) * k) - F32(1.0)
+
+
+def largest_gain(ncdr: int, ncdd: int, s_bits: int) -> Fraction:
+    """max over real c in [-C, C] of 1024 c nCdr - c^2 nCdd."""
+    C = 128 - (128 >> s_bits)
+    if ncdd > 0 and abs(Fraction(512 * ncdr, ncdd)) <= C:
+        return Fraction(262144 * ncdr * ncdr, ncdd)
+    return Fraction(1024 * C * abs(ncdr) - C * C * ncdd)
 
 
 def threshold(g: int) -> np.float32:
@@ -111,6 +132,39 @@ def test_screen_passes_every_candidate_that_can_win():
                 assert v >= threshold(g), (sdr, sd, sr, ncdd, g)
                 checked += 1
     assert checked > 2000
+
+
+def test_both_screens_pass_every_candidate_that_can_win():
+    rng = np.random.default_rng(1501)
+    checked = 0
+    for s_bits in (1, 3, 5, 7):
+        for d, r in cases(rng):
+            sdr, sd, sr, ncdd, ncdr = block_stats(d, r)
+            v, a = screen_value(sdr, sd, sr, ncdd, with_a=True)
+            M = largest_gain(ncdr, ncdd, s_bits)
+            tight = -math.floor(M)
+            for g in {tight, tight + 1, tight // 2, -1, 0, 5}:
+                if Fraction(-g) <= M:
+                    assert v >= threshold(g) and a >= threshold_a(g, s_bits), (s_bits, sdr, sd, sr, ncdd, g)
+                    checked += 1
+    assert checked > 8000
+
+
+def test_contrast_range_test_rejects_domains_needing_large_contrast():
+    """Near-flat domains that correlate with a busy range pass the square-root
+    screen (L does not depend on the domain's spread) but need |c| > C."""
+    rng = np.random.default_rng(11)
+    caught = 0
+    for _ in range(100):
+        r = rng.integers(0, 256, 64)
+        d = np.full(64, 500) + (r > 127)  # follows r, spread 1
+        sdr, sd, sr, ncdd, ncdr = block_stats(d, r)
+        L = Fraction(262144 * ncdr * ncdr, ncdd)
+        M = largest_gain(ncdr, ncdd, 5)
+        g = -math.floor((L + M) / 2)  # a best this domain cannot reach at |c| <= C
+        v, a = screen_value(sdr, sd, sr, ncdd, with_a=True)
+        caught += bool(v >= threshold(g) and a < threshold_a(g, 5))
+    assert caught == 100
 
 
 def test_screen_rejects_clear_losers():
