@@ -179,8 +179,8 @@ __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
             if (live && m >= best.thr) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    float aa;
-                    if (exh_screen_abs((float)acc[u], (float)sr, s_cs[j + u], aa) >= best.thr && aa >= best.thra)
+                    float abs_a;
+                    if (exh_screen_abs((float)acc[u], (float)sr, s_cs[j + u], abs_a) >= best.thr && abs_a >= best.thra)
                         exh_exact(best, d0 + j + u, (int)acc[u], sr, s_ds[j + u], E.s_bits);
                 }
             }
@@ -196,8 +196,8 @@ __global__ void __launch_bounds__(kExhWarps * 32) exh_cuda_kernel(ExhDesc E) {
                 acc = dp2a_lo(p.z, aw[2 * i + 1], acc);
                 acc = dp2a_hi(p.w, aw[2 * i + 1], acc);
             }
-            float aa;
-            if (live && exh_screen_abs((float)acc, (float)sr, s_cs[j], aa) >= best.thr && aa >= best.thra)
+            float abs_a;
+            if (live && exh_screen_abs((float)acc, (float)sr, s_cs[j], abs_a) >= best.thr && abs_a >= best.thra)
                 exh_exact(best, d0 + j, (int)acc, sr, s_ds[j], E.s_bits);
         }
     }
