@@ -338,9 +338,9 @@ def run_reference(args):
         "impl": "reference", "metric": metric, "value": round(value, 3), "unit": unit,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": desc, "sample": f"{step_s:.0f} s of oracle work per step"},
+        "config": {"workload": desc, "sample": f"{step_s:g} s of oracle work per step"},
         "cpu_baseline": {"value": round(value, 3), "unit": unit, "cores": threads, "kind": "oracle",
-                         "sample": f"items of the workload, {step_s:.0f} s per step on {threads} threads"},
+                         "sample": f"items of the workload, {step_s:g} s per step on {threads} threads"},
         "e2e": {"value": round(value, 3), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
