@@ -1,6 +1,8 @@
 """Exhaustive search (Section 1; flat 8x8 ranges, domains on a grid, eight
 isometries) on the GPU: the tensor-core path (tcgen05) and the CUDA-core
 path against the oracle and against each other, bit-exact."""
+import os
+
 import numpy as np
 import pytest
 
@@ -62,19 +64,81 @@ def test_exhaustive_finds_planted(fic, orc, engine):
         assert (int(r["dx"]), int(r["dy"]), int(r["iso"])) == (dx, dy, iso)
 
 
-@pytest.mark.parametrize("N,sample", [(512, 48), (1024, 16)])
-def test_exhaustive_full_size_engines_agree_and_sampled_oracle(fic, orc, N, sample):
-    img = synth.gaussian_scene(N, 1 if N == 512 else 9)
-    _, a = _encode(fic, img, "tensor")
+def _search_threaded(orc, img, op, idx, N):
+    """The oracle's phase-1 search (Section 1: every grid domain, every
+    isometry) of the 8x8 ranges with raster indices `idx`, spread over host
+    threads (ctypes releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    xs, ys = (idx % (N // 8)) * 8, (idx // (N // 8)) * 8
+    nt = max(1, os.cpu_count() or 1)
+    parts = np.array_split(np.arange(len(idx)), 8 * nt)
+
+    def one(sl):
+        return sl, orc.search_ranges(img, op, xs[sl], ys[sl], np.full(len(sl), 8))
+
+    out = {k: np.zeros(len(idx), dtype=np.int64) for k in ("k", "q", "dx", "dy", "iso")}
+    with ThreadPoolExecutor(max_workers=nt) as ex:
+        for sl, w in ex.map(one, [q for q in parts if len(q)]):
+            for k in out:
+                out[k][sl] = w[k]
+    return xs, ys, out
+
+
+def _leaves(orc, xs, ys, w):
+    """Oracle leaves of a flat 8x8 partition (one level, phase 1)."""
+    lv = np.zeros(len(xs), dtype=orc.LEAF_DTYPE)
+    lv["x"], lv["y"], lv["level"], lv["phase"] = xs, ys, 1, 1
+    for k in ("k", "q", "dx", "dy", "iso"):
+        lv[k] = w[k]
+    return lv
+
+
+def test_exhaustive_512_every_range_and_decode_vs_oracle(fic, orc):
+    """512x512 scene, 8 isometries, domain step 4: every one of the 4096
+    records of the tensor-core engine equals the oracle's search, the
+    CUDA-core engine's stream is identical, and the 6-iteration decode of the
+    stream equals the oracle's decode of its own leaves."""
+    N = 512
+    img = synth.gaussian_scene(N, 1)
+    st, a = _encode(fic, img, "tensor")
     _, b = _encode(fic, img, "cuda")
     assert np.array_equal(a["records"].view(np.uint8), b["records"].view(np.uint8))
     assert a["fits"] == b["fits"] == (N // 8) ** 2 * ((N - 16) // 4 + 1) ** 2 * 8
-    rng = np.random.default_rng(N)
-    idx = np.sort(rng.choice((N // 8) ** 2, size=sample, replace=False))
-    xs, ys = (idx % (N // 8)) * 8, (idx // (N // 8)) * 8
     op = orc.make_params("exhaustive", 8, 8, 8.0)
-    want = orc.search_ranges(img, op, xs, ys, np.full(sample, 8))
-    rec = a["records"][idx]
-    for i in range(sample):
-        assert (int(rec[i]["k"]), int(rec[i]["q"]), int(rec[i]["dx"]), int(rec[i]["dy"]), int(rec[i]["iso"])) == (
-            int(want["k"][i]), int(want["q"][i]), int(want["dx"][i]), int(want["dy"][i]), int(want["iso"][i])), i
+    idx = np.arange((N // 8) ** 2)
+    xs, ys, w = _search_threaded(orc, img, op, idx, N)
+    want = _leaves(orc, xs, ys, w)
+    gb, wb = a["records"].view(np.uint8).reshape(-1, 16), want.view(np.uint8).reshape(-1, 16)
+    assert gb.shape == wb.shape
+    bad = np.nonzero(np.any(gb != wb, axis=1))[0]
+    assert bad.size == 0, f"{bad.size} of {len(idx)} records differ, first {a['records'][bad[0]]} vs {want[bad[0]]}"
+    assert np.array_equal(a["split"], np.zeros((N // 8) ** 2, dtype=np.uint32))
+    dec = fic.fic_decode(st, 6).cpu().numpy()
+    assert np.array_equal(dec, orc.decode(want, N, N, op, 6))
+
+
+def test_exhaustive_1024_rows_and_random_ranges_vs_oracle(fic, orc):
+    """1024x1024 scene: 1024 of the 16384 ranges against the oracle -- four
+    whole range rows (top, bottom and two inner) and 512 random ranges --
+    both engines identical everywhere, and the 6-iteration decode of the GPU
+    stream equals the oracle's decode of the same records."""
+    N = 1024
+    img = synth.gaussian_scene(N, 9)
+    st, a = _encode(fic, img, "tensor")
+    _, b = _encode(fic, img, "cuda")
+    assert np.array_equal(a["records"].view(np.uint8), b["records"].view(np.uint8))
+    assert a["fits"] == b["fits"] == (N // 8) ** 2 * ((N - 16) // 4 + 1) ** 2 * 8
+    per = N // 8
+    rows = np.concatenate([np.arange(r * per, (r + 1) * per) for r in (0, 41, 86, per - 1)])
+    rng = np.random.default_rng(N)
+    rest = np.setdiff1d(np.arange(per * per), rows)
+    idx = np.sort(np.concatenate([rows, rng.choice(rest, size=512, replace=False)]))
+    op = orc.make_params("exhaustive", 8, 8, 8.0)
+    xs, ys, w = _search_threaded(orc, img, op, idx, N)
+    want = _leaves(orc, xs, ys, w)
+    got = a["records"][idx]
+    gb, wb = got.view(np.uint8).reshape(-1, 16), want.view(np.uint8).reshape(-1, 16)
+    bad = np.nonzero(np.any(gb != wb, axis=1))[0]
+    assert bad.size == 0, f"{bad.size} of {len(idx)} records differ, first {got[bad[0]]} vs {want[bad[0]]}"
+    dec = fic.fic_decode(st, 6).cpu().numpy()
+    assert np.array_equal(dec, orc.decode(a["records"], N, N, op, 6))
