@@ -285,8 +285,13 @@ FIC_API int fic_plan_autotune(fic_plan *plan, int iters, int reps, void *stream,
  *   - Every GPU that loads the library holds the array (about 256 KiB) until
  *     the process exits.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, once per device, with that device current); make
- *     that first call before any stream capture.
+ *     (cudaGetSymbolAddress, once per device, with that device current).
+ *   - It must not be called while `stream` is being captured into a CUDA
+ *     graph: it stages the image descriptor and tensor map from its own host
+ *     memory with cudaMemcpyAsync, which a graph could not replay, so it
+ *     returns FIC_EBADPARAM before enqueuing anything.  These copies are from
+ *     pageable memory, so the call may wait for them on the host.
+ *   - Modes FIC_NOSEARCH and FIC_MNS only (FIC_EBADPARAM otherwise).
  *   - All calls share the one array: calls whose work overlaps on the GPU
  *     (e.g. on two streams without ordering) race and corrupt each other's
  *     streams.  Each call clears the parts that must start at zero.  */

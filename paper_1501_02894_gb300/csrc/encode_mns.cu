@@ -686,6 +686,14 @@ extern "C" int fic_encode_noalloc(const uint8_t *d_img, int width, int height, c
     const int spr = (tw + tops - 1) / tops;
     const long long nstrips = (long long)spr * th;
     if (nstrips > FIC_NOALLOC_MAX_STRIPS) return FIC_EBADSIZE;  // larger than the static scratch
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    {
+        // the descriptor is staged from this call's own host memory, which a
+        // captured graph could not replay: refuse to be captured
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FIC_ECUDA;
+        if (cs != cudaStreamCaptureStatusNone) return FIC_EBADPARAM;
+    }
     NoAllocScratch *scr = nullptr;
     rc = noalloc_scratch_for_current_device(&scr);
     if (rc) return rc;
@@ -720,6 +728,7 @@ extern "C" int fic_encode_noalloc(const uint8_t *d_img, int width, int height, c
     d.o_bits = p->o_bits;
     d.local_radius = p->local_radius;
     d.local_step = p->local_step;
+    d.bmax = bmax;
     {
         const int bw = bmax == 32 ? WinBox<32>::W : (bmax == 16 ? WinBox<16>::W : WinBox<8>::W);
         d.boxw = bw < width ? bw : width;
@@ -733,7 +742,6 @@ extern "C" int fic_encode_noalloc(const uint8_t *d_img, int width, int height, c
     out->params = *p;
     out->ntop = tw * th;
 
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // The descriptor is staged from host memory; the status words, the ticket
     // and the stream's info block are cleared by the init kernel of the launch.
     if (cudaMemcpyAsync(&scr->map, &map, sizeof(map), cudaMemcpyHostToDevice, st) != cudaSuccess) return FIC_ECUDA;
