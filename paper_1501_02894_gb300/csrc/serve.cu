@@ -483,6 +483,17 @@ void worker_main(fic_server *S) {
             if (!prepare_job(S, J)) {  // fragmentation: retry when memory frees
                 std::lock_guard<std::mutex> g(S->mu);
                 S->dev_accounted -= J->footprint;
+                if (S->inflight.empty() && S->admitted.empty()) {
+                    // both arenas are wholly free and the job still cannot be
+                    // placed: no later release can help, so it fails now
+                    J->res.status = FIC_ENOMEM;
+                    J->res.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - J->t_submit).count();
+                    J->done = true;
+                    S->completed += 1;
+                    S->cv_done.notify_all();
+                    progress = true;
+                    continue;
+                }
                 S->queue.push_front(J);
                 break;
             }
@@ -616,10 +627,12 @@ void worker_main(fic_server *S) {
         std::unique_lock<std::mutex> lk(S->mu);
         if (S->stopping && S->queue.empty() && S->admitted.empty() && S->inflight.empty()) break;
         if (!progress) {
-            if (S->inflight.empty() && S->admitted.empty() && S->queue.empty())
-                S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
-            else if (S->queue.empty() || !S->inflight.empty())
+            // batches in flight are polled every 20 us; with none, only a
+            // submit or the shutdown (both signal cv_work) can change anything
+            if (!S->inflight.empty() || !S->admitted.empty())
                 S->cv_work.wait_for(lk, std::chrono::microseconds(20));
+            else
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
         }
     }
 }
