@@ -455,6 +455,11 @@ int encode_plan_create_staged(const uint8_t *const *d_imgs, const int *widths, c
     pl->total_chunks = chunks;
     pl->d_dec = nullptr;
     {
+        bool own_domains = true;  // every image's phase-2 sub-blocks use their own centred domains
+        for (int i = 0; i < count; ++i) own_domains = own_domains && !params[i].phase2_domain;
+        pl->etune.kernel32 = (bmax == 32 && own_domains) ? 1 : 0;
+    }
+    {
         fic_record *slots = reinterpret_cast<fic_record *>(w + lay.slots);
         uint2 *stats = reinterpret_cast<uint2 *>(w + lay.stats);
         for (int i = 0; i < count; ++i) {

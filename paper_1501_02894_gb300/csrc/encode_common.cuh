@@ -37,7 +37,15 @@ __device__ __forceinline__ int best_contrast(long long ncdr, long long ncdd, int
     float cs = FAST ? __fdividef(512.f * (float)ncdr, (float)ncdd) : 512.f * (float)ncdr / (float)ncdd;
     float kf = (cs + 128.f) / (float)step - 0.5f;
     kf = fminf(fmaxf(kf, 0.f), (float)(K - 1));
-    int k = __float2int_rn(kf);
+    const float kr = rintf(kf);
+    int k = (int)kr;
+    // Far from every grid midpoint (k +- 1/2) the estimate is the answer.  Its
+    // error, for a c* within the grid (|c*| <= 128 + step / 2; beyond it the
+    // clamp decides), is at most |c*| (2^-24 + 2^-24 + 2^-22) from the two
+    // roundings to float and the approximate division, plus 2^-24 (|c*| + 128)
+    // from the sum, divided by the step (>= 2): below 3e-5, far inside the
+    // 1e-3 band around a midpoint that goes to the exact comparisons below.
+    if (fabsf(kf - kr) < 0.499f) return k;
     const long long a = 512LL * ncdr;
 #pragma unroll 1
     for (int it = 0; it < K && k < K - 1; ++it) {
@@ -57,24 +65,23 @@ __device__ __forceinline__ int best_contrast(long long ncdr, long long ncdd, int
 }
 
 // The luminance code whose level is nearest the block mean Sr / n (ties to
-// the smaller code); *dist = |Sr - n L(q)|.  The float estimate is within
-// one code of the answer, which the exact integer check settles.
+// the smaller code); *dist = |Sr - n L(q)|.  The float estimate q0 is within
+// one code of the answer; the levels increase with q, so the answer is q0 or
+// its neighbour on the side of the block mean, settled by the exact distance.
 __device__ __forceinline__ int best_luminance(int sr, int lg2n, int ko1, uint32_t magic, float qscale, int &dist) {
     int q0 = __float2int_rn((float)sr * qscale * __int_as_float((127 - lg2n) << 23));
     q0 = clampi(q0, 0, ko1);
-    int bq = q0, bd = 0x7fffffff;
-#pragma unroll
-    for (int dq = -1; dq <= 1; ++dq) {
-        const int q = q0 + dq;
-        if (q < 0 || q > ko1) continue;
-        const int d = abs(sr - (lum(q, ko1, magic) << lg2n));
-        if (d < bd) {
-            bd = d;
-            bq = q;
-        }
-    }
-    dist = bd;
-    return bq;
+    const int d0 = sr - (lum(q0, ko1, magic) << lg2n);
+    // the answer is q0 or its neighbour on the side of the block mean
+    const bool up = d0 >= 0;
+    const int q1 = up ? q0 + 1 : q0 - 1;
+    const bool ok1 = up ? q1 <= ko1 : q1 >= 0;
+    const int d1 = ok1 ? abs(sr - (lum(q1, ko1, magic) << lg2n)) : 0x7fffffff;
+    const int a0 = abs(d0);
+    // ties: the smaller code
+    const bool take1 = up ? d1 < a0 : d1 <= a0;
+    dist = take1 ? d1 : a0;
+    return take1 ? q1 : q0;
 }
 
 // Phase-1 fit (Section 3: the best contrast factor for the one domain, the

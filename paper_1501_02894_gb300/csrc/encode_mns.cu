@@ -591,6 +591,8 @@ cudaError_t launch_mns_encode(int bmax, const EncDesc *d_descs, int count, int t
 
 cudaError_t launch_pack(const EncDesc *d_descs, int count, int total_chunks, uint32_t *pack_status,
                         uint32_t *ticket, cudaStream_t st);
+cudaError_t launch_mns32_slots(const EncDesc *d_descs, int count, int total_strips, int total_chunks,
+                               uint32_t *pack_status, uint32_t *ticket, const EncTune &tune, cudaStream_t st);
 
 // Slot variant: encode into per-strip slots, then compact with pack_kernel.
 // `tune` picks warps per CTA, CTAs per SM and the strip schedule; every
@@ -606,6 +608,11 @@ cudaError_t launch_mns_encode_slots(int bmax, const EncDesc *d_descs, int count,
         // (status, ticket and counters are contiguous in the workspace)
         e = cudaMemsetAsync(pack_status, 0, (2 * (size_t)total_chunks + 1) * sizeof(uint32_t), st);
         if (e != cudaSuccess) return e;
+    }
+    if (bmax == 32 && tune.kernel32) {
+        e = launch_mns32_slots(d_descs, count, total_strips, total_chunks, pack_status, tk, tune, st);
+        if (e != cudaSuccess || fused) return e;
+        return launch_pack(d_descs, count, total_chunks, pack_status, tk, st);
     }
 #define FIC_SLOTS_LAUNCH(B)                                                                                       \
     e = w4 ? launch_t<B, true, 4>(d_descs, count, total_strips, pack_status, tk, total_chunks, k, dyn, fused, st)   \

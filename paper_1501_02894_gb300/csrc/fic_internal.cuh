@@ -124,6 +124,8 @@ struct EncTune {
     int dynamic = 0;      // 1: strips from an atomic counter, 0: static grid stride
     int fused_pack = 0;   // 1: the warp finishing a chunk packs it; 0: a separate pack kernel
                           // (measured faster: the per-strip release fence costs more than the launch)
+    int kernel32 = 0;     // set by the plan: 1 = mns32_kernel (bmax 32, sub-blocks on their own
+                          // centred domains), 0 = the general mns_encode_kernel
 };
 struct DecTune {
     int ctas_per_sm = 0;    // resident CTAs per SM of the iteration kernel; 0 = the occupancy limit

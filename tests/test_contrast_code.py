@@ -97,3 +97,43 @@ def test_nearest_code_is_the_oracles_smallest_score(orc, s_bits):
         g = [c * c * ncdd - 1024 * c * ncdr for c in codes]
         best = min(range(K), key=lambda k: (g[k], abs(codes[k]), -codes[k]))
         assert best == nearest_by_definition(ncdr, ncdd, s_bits)
+
+
+def screened(ncdr, ncdd, s_bits, ulps):
+    """The kernels' float screen with its quotient moved by `ulps` units in
+    the last place (the approximate division is within 2 ulp of the exact
+    quotient of the rounded operands): the code it returns, or None when it
+    hands the block to the integer steps."""
+    K, step = 1 << s_bits, 256 >> s_bits
+    num = np.float32(512.0) * np.float32(ncdr)
+    q = np.float32(num / np.float32(ncdd))
+    for _ in range(abs(ulps)):
+        q = np.nextafter(q, np.float32(np.inf) if ulps > 0 else np.float32(-np.inf), dtype=np.float32)
+    kf = np.float32(np.float32(q + np.float32(128.0)) / np.float32(step)) - np.float32(0.5)
+    kf = np.float32(min(max(kf, np.float32(0.0)), np.float32(K - 1)))
+    kr = np.float32(np.rint(kf))
+    return int(kr) if abs(np.float32(kf - kr)) < np.float32(0.499) else None
+
+
+@pytest.mark.parametrize("s_bits", range(1, 8))
+def test_float_screen_never_returns_a_wrong_code(s_bits):
+    """Whenever the screen returns a code without the integer steps, it is
+    the nearest code, with the division off by up to 2 ulp either way; blocks
+    on or next to a midpoint go to the integer steps."""
+    rng = np.random.default_rng(200 + s_bits)
+    K, step = 1 << s_bits, 256 >> s_bits
+    cases = list(blocks(rng, s_bits))
+    for k in range(K - 1):  # c* a hair either side of every midpoint
+        m = step * (k + 1) - 128
+        for eps in (-3, -1, 1, 3):
+            t = int(rng.integers(1 << 20, 1 << 30))
+            cases.append((m * t + eps, 512 * t))
+    decided = 0
+    for ncdr, ncdd in cases:
+        want = nearest_by_definition(ncdr, ncdd, s_bits)
+        for u in (-2, 0, 2):
+            got = screened(ncdr, ncdd, s_bits, u)
+            if got is not None:
+                decided += 1
+                assert got == want, (s_bits, ncdr, ncdd, u, got, want)
+    assert decided > len(cases) // 2  # the screen decides most blocks by itself

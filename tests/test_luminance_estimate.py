@@ -4,9 +4,10 @@ The offset o of a block is coded as the level L(q) = floor((510 q + K) / (2 K))
 (K = 2^o_bits - 1) nearest the block mean Sr / n, ties to the smaller code
 (Section 3, the quantised offset).  The kernels estimate the code in float32,
 q0 = round_half_even(float(Sr) * float(K / 255) * 2^-lg2n), clamp it to
-[0, K], and keep the best of q0 - 1, q0, q0 + 1 by the exact integer distance
+[0, K], and compare q0 with its one neighbour on the side of the block mean
+(q0 + 1 when Sr >= n L(q0), else q0 - 1) by the exact integer distance
 |Sr - n L(q)|.  That is right only if the estimate is never two or more codes
-from the answer.  This test replays the float steps bit for bit (numpy float32
+from the answer and the levels increase strictly with q.  This test replays the float steps bit for bit (numpy float32
 is IEEE round-to-nearest) for every Sr of every block size 2^lg2n (1 to 4096
 pixels) and every code width, and compares code and distance with a search
 over all codes."""
@@ -37,16 +38,15 @@ def kernel_estimate(sr, lg2n, o_bits, lev):
     qscale = F32(k) / F32(255.0)
     x = (sr.astype(F32) * qscale) * F32(2.0 ** -lg2n)
     q0 = np.clip(np.rint(x).astype(np.int64), 0, k)
-    best_q = np.full(sr.shape, -1, np.int64)
-    best_d = np.full(sr.shape, np.iinfo(np.int64).max, np.int64)
-    for dq in (-1, 0, 1):
-        q = q0 + dq
-        ok = (q >= 0) & (q <= k)
-        d = np.where(ok, np.abs(sr - (lev[np.clip(q, 0, k)] << lg2n)), np.iinfo(np.int64).max)
-        take = d < best_d
-        best_q = np.where(take, q, best_q)
-        best_d = np.where(take, d, best_d)
-    return best_q, best_d
+    d0 = sr - (lev[q0] << lg2n)
+    up = d0 >= 0
+    q1 = np.where(up, q0 + 1, q0 - 1)
+    ok1 = np.where(up, q1 <= k, q1 >= 0)
+    big = np.iinfo(np.int64).max
+    d1 = np.where(ok1, np.abs(sr - (lev[np.clip(q1, 0, k)] << lg2n)), big)
+    a0 = np.abs(d0)
+    take1 = np.where(up, d1 < a0, d1 <= a0)
+    return np.where(take1, q1, q0), np.where(take1, d1, a0)
 
 
 def test_levels_are_increasing_and_span_the_range():
