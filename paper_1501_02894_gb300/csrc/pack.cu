@@ -4,31 +4,30 @@
 //
 // The encoder writes the leaves of strip s to slot s (at most 64 records)
 // and the strip's record count.  Here one CTA takes 32 consecutive strips of
-// one image: warp 0 scans their counts and looks back over the image's
-// earlier chunks (their counts are already final, so the look-back resolves
-// in a few rounds), turns the encoder's per-strip tile offsets into stream
-// offsets and adds the fit counts to the stream's info block; meanwhile the
-// other seven warps load the 32 slots' records into registers (coalesced
-// 16-byte loads), and store them at their stream offsets once warp 0 has
-// them.  The info block of each stream (record count, fits, device error
-// bits) is written here, by the image's last chunk.
+// one image.  Every count is final when this kernel runs, so a chunk needs
+// no other chunk's result: the CTA sums the counts of all of the image's
+// earlier strips itself (each thread a strided share, then one block
+// reduction) -- no look-back, no wait on another CTA.  Meanwhile its copy
+// warps load the 32 slots' records into registers (coalesced 16-byte
+// loads); warp 0 scans the chunk's counts, fixes the tile offsets, and the
+// copy warps store the records at their stream offsets.  The image's last
+// chunk also writes the stream's info block (record count, fits, device
+// error bits), summing the fits of all of the image's strips in the same
+// strided pass.
 #include "fic_internal.cuh"
 
 namespace fic {
 
 constexpr int kPackWarps = 8;
-constexpr uint32_t kPAgg = 1u << 30, kPIncl = 2u << 30, kPVal = (1u << 30) - 1;
 constexpr int kSlotRecs = 64;
 
-// One CTA per chunk of 32 strips, in block order (lower chunks of an image
-// are scheduled first, so a look-back only waits on chunks already running;
-// the wait is bounded in any case).
 __global__ void __launch_bounds__(kPackWarps * 32)
-    pack_kernel(const EncDesc *__restrict__ descs, int count, int total_chunks, uint32_t *__restrict__ pstatus,
-                uint32_t *__restrict__ ticket) {
+    pack_kernel(const EncDesc *__restrict__ descs, int count, int total_chunks, uint32_t *__restrict__ ticket) {
     __shared__ int s_cb[kImgTable];
-    __shared__ int s_ok;
     __shared__ uint32_t s_off[32];
+    __shared__ uint32_t s_part[kPackWarps];
+    __shared__ unsigned long long s_fits[kPackWarps];
+    __shared__ uint32_t s_err[kPackWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned FULL = 0xffffffffu;
     const int c = blockIdx.x;
@@ -38,7 +37,7 @@ __global__ void __launch_bounds__(kPackWarps * 32)
     if (count <= kImgTable)
         for (int i = threadIdx.x; i < count; i += blockDim.x) s_cb[i] = descs[i].chunk_base;
     __syncthreads();
-    // the chunk's image (every warp: the copy warps prefetch below)
+    // the chunk's image
     int lo = 0;
     {
         int hi = count - 1;
@@ -56,13 +55,14 @@ __global__ void __launch_bounds__(kPackWarps * 32)
     // the encoder's strip counter (dynamic schedule) is free again: reset it
     // for the next launch
     if (ticket && c == 0 && threadIdx.x == 0) *ticket = 0u;
-    // warps 1..7 load their slots' records while warp 0 resolves the offsets
+    const EncDesc &D = descs[lo];
+    const int cl = c - D.chunk_base;
+    const bool last = cl == D.nchunks - 1;
+    // copy warps: their slots' records into registers
     constexpr int kPer = (32 + kPackWarps - 2) / (kPackWarps - 1);  // slots per copy warp (5)
     uint4 pre[kPer][2];
     uint32_t pre_n[kPer];
     if (warp > 0) {
-        const EncDesc &D = descs[lo];
-        const int cl = c - D.chunk_base;
 #pragma unroll
         for (int t = 0; t < kPer; ++t) {
             const int j = (warp - 1) + (kPackWarps - 1) * t;
@@ -75,13 +75,35 @@ __global__ void __launch_bounds__(kPackWarps * 32)
                                                 : make_uint4(0u, 0u, 0u, 0u);
         }
     }
+    // records of the image's earlier strips (and, in the last chunk, the fits
+    // and error flags of all of its strips)
+    uint32_t part = 0, err = 0;
+    unsigned long long fs = 0;
+    {
+        const int before = cl * 32, end = last ? D.nstrips : before;
+        for (int i = threadIdx.x; i < end; i += kPackWarps * 32) {
+            const uint2 v = D.stats[i];
+            if (i < before) part += v.x;
+            fs += v.y & 0x7fffffffu;
+            err |= v.y >> 31;
+        }
+    }
+    part = __reduce_add_sync(FULL, part);
+    err = __reduce_or_sync(FULL, err);
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) fs += __shfl_xor_sync(FULL, fs, m);
+    if (lane == 0) {
+        s_part[warp] = part;
+        s_fits[warp] = fs;
+        s_err[warp] = err;
+    }
+    __syncthreads();
     if (warp == 0) {
-        const EncDesc &D = descs[lo];
-        const int cl = c - D.chunk_base;
+        uint32_t prefix = lane < kPackWarps ? s_part[lane] : 0u;
+        prefix = __reduce_add_sync(FULL, prefix);
         const int s = cl * 32 + lane;
         const bool in = s < D.nstrips;
-        const uint2 st = in ? D.stats[s] : make_uint2(0u, 0u);
-        const uint32_t cnt = st.x;
+        const uint32_t cnt = in ? D.stats[s].x : 0u;
         uint32_t incl = cnt;
 #pragma unroll
         for (int m = 1; m < 32; m <<= 1) {
@@ -89,77 +111,41 @@ __global__ void __launch_bounds__(kPackWarps * 32)
             if (lane >= m) incl += o;
         }
         const uint32_t tot = __shfl_sync(FULL, incl, 31);
-        // look-back over the image's earlier chunks (their counts are final)
-        uint32_t prefix = 0;
-        int ok = 1;
-        if (cl == 0) {
-            if (lane == 0) st_volatile(pstatus + c, kPIncl | tot);
-        } else {
-            if (lane == 0) st_volatile(pstatus + c, kPAgg | tot);
-            int p = c - 1;
-            for (;;) {
-                const int idx = p - lane;
-                const bool inimg = idx >= D.chunk_base;
-                uint32_t v = inimg ? ld_volatile(pstatus + idx) : kPIncl;
-                unsigned it = 0;
-                while (!__all_sync(FULL, v != 0u) && ++it < kSpinLimit) {
-                    __nanosleep(32);
-                    if (v == 0u) v = ld_volatile(pstatus + idx);
-                }
-                if (!__all_sync(FULL, v != 0u)) {
-                    ok = 0;
-                    break;
-                }
-                const uint32_t inc = __ballot_sync(FULL, (v & ~kPVal) == kPIncl);
-                const int first = inc ? __ffs(inc) - 1 : 32;
-                prefix += __reduce_add_sync(FULL, (lane <= first) ? (v & kPVal) : 0u);
-                if (inc) break;
-                p -= 32;
-            }
-            if (lane == 0 && ok) st_volatile(pstatus + c, kPIncl | (prefix + tot));
-        }
         const uint32_t excl = prefix + incl - cnt;
         s_off[lane] = excl;
-        if (lane == 0) s_ok = ok;
-        if (ok && in) {
-            // tile offsets: the encoder stored offsets inside the strip
+        if (in) {
+            // tile offsets: the encoder stored each block's offset inside its
+            // strip (0 when a strip is one block)
             const int tops = 1024 / (D.bmax * D.bmax);
             const int row = s / D.spr, sc = s - row * D.spr;
             const int top0 = row * D.tw + sc * tops;
-            const int nvalid = min(tops, D.tw - sc * tops);
-            for (int t = 0; t < nvalid; ++t) D.tile_off[top0 + t] += excl;
-        }
-        if (cl == D.nchunks - 1) {
-            // last chunk of the image: totals, fits and error bits of all its strips
-            unsigned long long fsum = 0;
-            uint32_t err = ok ? 0u : FIC_DEVERR_TIMEOUT;
-            for (int t = lane; t < D.nstrips; t += 32) {
-                const uint2 v = D.stats[t];
-                fsum += v.y & 0x7fffffffu;
-                err |= (v.y >> 31) ? FIC_DEVERR_TIMEOUT : 0u;
+            if (tops == 1) {
+                D.tile_off[top0] = excl;
+            } else {
+                const int nvalid = min(tops, D.tw - sc * tops);
+                for (int t = 0; t < nvalid; ++t) D.tile_off[top0 + t] += excl;
             }
+        }
+        if (last) {
+            unsigned long long fsum = lane < kPackWarps ? s_fits[lane] : 0ull;
 #pragma unroll
             for (int m = 16; m >= 1; m >>= 1) fsum += __shfl_xor_sync(FULL, fsum, m);
-            err = __reduce_or_sync(FULL, err);
-            if (ok && prefix + tot > (uint32_t)D.capacity) err |= FIC_DEVERR_CAPACITY;
+            uint32_t e = __reduce_or_sync(FULL, lane < kPackWarps ? s_err[lane] : 0u) ? FIC_DEVERR_TIMEOUT : 0u;
+            if (prefix + tot > (uint32_t)D.capacity) e |= FIC_DEVERR_CAPACITY;
             if (lane == 0) {
+                // the info block is written here only (it may hold anything before)
                 D.info[FIC_INFO_FITS_LO] = (uint32_t)fsum;
                 D.info[FIC_INFO_FITS_HI] = (uint32_t)(fsum >> 32);
-                D.info[FIC_INFO_ERROR] = err;
-                if (ok) {
-                    D.tile_off[D.tw * D.th] = prefix + tot;
-                    D.info[FIC_INFO_RECORDS] = prefix + tot;
-                }
+                D.info[FIC_INFO_ERROR] = e;
+                D.tile_off[D.tw * D.th] = prefix + tot;
+                D.info[FIC_INFO_RECORDS] = prefix + tot;
             }
-        } else if (!ok && lane == 0) {
-            raise_error(D.info, FIC_DEVERR_TIMEOUT);
         }
     }
     __syncthreads();
-    if (!s_ok || warp == 0) return;
+    if (warp == 0) return;
     // store the prefetched records at their stream offsets (records past
     // the capacity are dropped; the image's last chunk reports it)
-    const EncDesc &D = descs[lo];
 #pragma unroll
     for (int t = 0; t < kPer; ++t) {
         const int j = (warp - 1) + (kPackWarps - 1) * t;
@@ -186,7 +172,8 @@ cudaError_t launch_pack(const EncDesc *d_descs, int count, int total_chunks, uin
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, pack_kernel, d_descs, count, total_chunks, pack_status, ticket);
+    (void)pack_status;  // the look-back words are used by fused packing only
+    cudaError_t e = cudaLaunchKernelEx(&cfg, pack_kernel, d_descs, count, total_chunks, ticket);
     stage_mark(st, "pack_kernel");
     return e != cudaSuccess ? e : cudaGetLastError();
 }
