@@ -65,6 +65,8 @@ extern "C" {
 typedef struct fic_params {
     int32_t mode;         /* FIC_NOSEARCH .. FIC_EXHAUSTIVE */
     int32_t bmax, bmin;   /* range sides, powers of two, 4 <= bmin <= bmax <= 32, L <= 4;
+                             FIC_NOSEARCH / FIC_MNS also bmin = 2 (bmax 8 or 16: the
+                             paper's 16 -> 2 quadtree of Sections 3.3-3.4);
                              FIC_EXHAUSTIVE: a flat partition, bmax = bmin = 8 */
     double thr_rms[4];    /* RMS error threshold E_j per level j=1..4 (Section 3);
                              compared as SSE < round(256 T^2)/256 * n */
@@ -291,7 +293,8 @@ FIC_API int fic_plan_autotune(fic_plan *plan, int iters, int reps, void *stream,
  *     memory with cudaMemcpyAsync, which a graph could not replay, so it
  *     returns FIC_EBADPARAM before enqueuing anything.  These copies are from
  *     pageable memory, so the call may wait for them on the host.
- *   - Modes FIC_NOSEARCH and FIC_MNS only (FIC_EBADPARAM otherwise).
+ *   - Modes FIC_NOSEARCH and FIC_MNS with bmin >= 4 only (FIC_EBADPARAM
+ *     otherwise).
  *   - All calls share the one array: calls whose work overlaps on the GPU
  *     (e.g. on two streams without ordering) race and corrupt each other's
  *     streams.  Each call clears the parts that must start at zero.  */

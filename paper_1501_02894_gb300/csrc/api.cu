@@ -75,6 +75,8 @@ cudaError_t launch_local_encode(int bmax, const EncDesc *d_descs, int count, int
                                 uint32_t *pack_status, cudaStream_t st);
 cudaError_t launch_decode(int bmax, const DecDesc *d_descs, int count, int total_strips, void *tables, int iters,
                           bool d4, const DecTune &tune, cudaStream_t st);
+cudaError_t launch_decode_leaves(const DecDesc *d_descs, const DecDesc *hdec, int count, int max_recs, int iters,
+                                 cudaStream_t st);
 int decode_d4_box(int bmax);
 size_t decode_table_bytes_per_strip();
 int mns_strip_width(int bmax);
@@ -107,7 +109,9 @@ int check_params(const fic_params *p) {
          (p->local_step & 1)))
         return FIC_EBADPARAM;
     if (!(p->bmax == 8 || p->bmax == 16 || p->bmax == 32)) return FIC_EBADPARAM;
-    if (!is_pow2(p->bmin) || p->bmin < 4 || p->bmin > p->bmax) return FIC_EBADPARAM;
+    // 2 x 2 leaves (the paper's 16 -> 2 quadtree) for the centred-domain modes
+    const int min_b = (p->mode == FIC_NOSEARCH || p->mode == FIC_MNS) ? 2 : 4;
+    if (!is_pow2(p->bmin) || p->bmin < min_b || p->bmin > p->bmax) return FIC_EBADPARAM;
     if (levels_of(p) > 4) return FIC_EBADPARAM;
     if (p->s_bits < 1 || p->s_bits > 7 || p->o_bits < 1 || p->o_bits > 8) return FIC_EBADPARAM;
     if (p->phase2_domain != 0 && p->phase2_domain != 1) return FIC_EBADPARAM;
@@ -132,7 +136,7 @@ int check_stream(int W, int H, const fic_params *p) {
     if (!p) return FIC_EBADPARAM;
     if (p->mode < FIC_NOSEARCH || p->mode > FIC_EXHAUSTIVE) return FIC_EBADPARAM;
     if (!(p->bmax == 8 || p->bmax == 16 || p->bmax == 32)) return FIC_EBADPARAM;
-    if (!is_pow2(p->bmin) || p->bmin < 4 || p->bmin > p->bmax) return FIC_EBADPARAM;
+    if (!is_pow2(p->bmin) || p->bmin < 2 || p->bmin > p->bmax) return FIC_EBADPARAM;
     if (levels_of(p) > 4) return FIC_EBADPARAM;
     if (p->mode == FIC_EXHAUSTIVE && (p->bmin != p->bmax || p->isometries < 1 || p->isometries > 8 || p->dom_step < 1))
         return FIC_EBADPARAM;
@@ -181,6 +185,8 @@ struct fic_plan {
     EncTune etune;  // launch mapping (fic_plan_set_tuning / fic_plan_autotune)
     DecTune dtune;
     bool d4 = false;  // decode: iterate on 2x2-sum images (every stream centred)
+    bool leaves = false;  // decode: a stream with 2 x 2 leaves (transform-per-thread iteration)
+    int max_recs = 0;     // decode: the largest record capacity of the batch
 };
 
 // Exhaustive search: per image, decimated domains (packed and fp16), domain
@@ -328,20 +334,24 @@ struct EncLayout {
     size_t maps, descs, stats, pstatus, slots, total;
 };
 
-static EncLayout enc_layout(int count, size_t strips, size_t chunks) {
+static EncLayout enc_layout(int count, size_t strips, size_t chunks, size_t slot_records) {
     EncLayout L;
     L.maps = 0;
     L.descs = L.maps + align_up(sizeof(TmaMap) * (size_t)count);
     L.stats = L.descs + align_up(sizeof(EncDesc) * (size_t)count);
     L.pstatus = L.stats + align_up(8 * strips);
     L.slots = L.pstatus + align_up(4 * (2 * chunks + 1));  // status, strip counter, chunk counters
-    L.total = L.slots + align_up(sizeof(fic_record) * 64 * strips);
+    L.total = L.slots + align_up(sizeof(fic_record) * slot_records);
     return L;
 }
 
+// Records one strip of 1024 pixels can emit: a 4 x 4 leaf each 16 pixels,
+// a 2 x 2 leaf each 4.
+static int slot_records_of(const fic_params *p) { return p->bmin < 4 ? 256 : 64; }
+
 size_t fic_encode_workspace_bytes(int count, const int *widths, const int *heights, const fic_params *params) {
     if (count <= 0 || !widths || !heights || !params) return 0;
-    size_t strips = 0, chunks = 0, exh = 0;
+    size_t strips = 0, chunks = 0, exh = 0, slot_recs = 0;
     for (int i = 0; i < count; ++i) {
         if (fic_validate(widths[i], heights[i], &params[i])) return 0;
         if (params[i].mode == FIC_EXHAUSTIVE) {
@@ -351,8 +361,9 @@ size_t fic_encode_workspace_bytes(int count, const int *widths, const int *heigh
         const size_t n = (size_t)nstrips_of(widths[i], heights[i], params[i].bmax);
         strips += n;
         chunks += (n + 31) / 32;
+        slot_recs += n * (size_t)slot_records_of(&params[i]);
     }
-    return enc_layout(count, strips, chunks).total + exh;
+    return enc_layout(count, strips, chunks, slot_recs).total + exh;
 }
 
 }  // extern "C"
@@ -383,6 +394,9 @@ int encode_plan_create_staged(const uint8_t *const *d_imgs, const int *widths, c
     std::vector<TmaMap> maps((size_t)count);
     const TmaMap *d_maps = static_cast<const TmaMap *>(d_workspace);
     int strips = 0, chunks = 0;
+    size_t slot_recs = 0;
+    std::vector<size_t> slot_base((size_t)count);
+    bool min2 = false;  // a stream with 2 x 2 leaves
     for (int i = 0; i < count; ++i) {
         const fic_params *p = &params[i];
         int rc = fic_validate(widths[i], heights[i], p);
@@ -433,10 +447,14 @@ int encode_plan_create_staged(const uint8_t *const *d_imgs, const int *widths, c
         if (rc) return rc;
         d.chunk_base = chunks;
         d.nchunks = (d.nstrips + 31) / 32;
+        d.slot_recs = slot_records_of(p);
+        slot_base[(size_t)i] = slot_recs;
+        slot_recs += (size_t)d.nstrips * (size_t)d.slot_recs;
+        min2 = min2 || p->bmin < 4;
         strips += d.nstrips;
         chunks += d.nchunks;
     }
-    const EncLayout lay = enc_layout(count, (size_t)strips, (size_t)chunks);
+    const EncLayout lay = enc_layout(count, (size_t)strips, (size_t)chunks, slot_recs);
     const size_t need = lay.total;
     if (ws_bytes < need || (reinterpret_cast<uintptr_t>(d_workspace) & (kAlign - 1))) return FIC_ENOMEM;
     fic_plan *pl = new (std::nothrow) fic_plan();
@@ -458,12 +476,13 @@ int encode_plan_create_staged(const uint8_t *const *d_imgs, const int *widths, c
         bool own_domains = true;  // every image's phase-2 sub-blocks use their own centred domains
         for (int i = 0; i < count; ++i) own_domains = own_domains && !params[i].phase2_domain;
         pl->etune.kernel32 = (bmax == 32 && own_domains) ? 1 : 0;
+        pl->etune.min2 = min2 ? 1 : 0;
     }
     {
         fic_record *slots = reinterpret_cast<fic_record *>(w + lay.slots);
         uint2 *stats = reinterpret_cast<uint2 *>(w + lay.stats);
         for (int i = 0; i < count; ++i) {
-            h[(size_t)i].slots = slots + (size_t)h[(size_t)i].strip_base * 64;
+            h[(size_t)i].slots = slots + slot_base[(size_t)i];
             h[(size_t)i].stats = stats + h[(size_t)i].strip_base;
         }
     }
@@ -719,10 +738,16 @@ int decode_plan_create_staged(const fic_stream *sts, int count, uint8_t *const *
     std::vector<TmaMap> maps(2 * (size_t)count);
     // 2x2-sum iteration when every stream uses centred domains and is wide
     // enough for the window box
-    bool d4 = true;
-    for (int i = 0; i < count; ++i)
+    bool d4 = true, leaves = false;
+    int max_recs = 0;
+    for (int i = 0; i < count; ++i) {
         d4 = d4 && (sts[i].params.mode == FIC_NOSEARCH || sts[i].params.mode == FIC_MNS) &&
              sts[i].width / 2 >= decode_d4_box(bmax);
+        leaves = leaves || sts[i].params.bmin < 4;
+        if (sts[i].params.bmin > 0)
+            max_recs = std::max(max_recs, (sts[i].width / sts[i].params.bmin) * (sts[i].height / sts[i].params.bmin));
+    }
+    if (leaves) d4 = false;
     int strips = 0;
     for (int i = 0; i < count; ++i) {
         const fic_stream *s = &sts[i];
@@ -778,6 +803,8 @@ int decode_plan_create_staged(const fic_stream *sts, int count, uint8_t *const *
     pl->count = count;
     pl->bmax = bmax;
     pl->d4 = d4;
+    pl->leaves = leaves;
+    pl->max_recs = max_recs;
     pl->total_strips = strips;
     pl->dec_tables = scratch;  // after the per-image iterate buffers
     pl->ws = d_workspace;
@@ -824,6 +851,8 @@ int fic_decode_plan_run(const fic_plan *pl, int iters, void *stream) {
         }
         return FIC_OK;
     }
+    if (pl->leaves)
+        return cuda_rc(launch_decode_leaves(pl->d_dec, pl->hdec.data(), pl->count, pl->max_recs, iters, st));
     return cuda_rc(launch_decode(pl->bmax, pl->d_dec, pl->count, pl->total_strips, pl->dec_tables, iters, pl->d4,
                                  pl->dtune, st));
 }

@@ -884,6 +884,107 @@ static cudaError_t dlaunch_t(const DecDesc *descs, int count, int total_strips, 
     return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// Transform-per-thread iteration, for streams whose leaves go down to 2 x 2
+// pixels (the paper's 16 -> 2 quadtree; the strip kernels above assume every
+// 4 x 4 half-patch is covered by one transform).  One thread applies one
+// stored transform (a phase-2 leaf: its four sub-block transforms, eq. (1))
+// to the previous iterate: Sd4 over its decimated domain, then every pixel
+// p = clamp(floor((512 n O + c (n d4 - Sd4) + 256 n) / (512 n))), the same
+// fixed-point rule as the strip kernels.  Leaves tile the image, so every
+// pixel of the next iterate is written.  Transforms whose range or domain
+// would leave the image are skipped (a stream from the encoder has none).
+__device__ __forceinline__ int d4_at(const uint8_t *x, int W, int px, int py) {
+    const uint8_t *p = x + (size_t)py * W + px;
+    return (int)p[0] + (int)p[1] + (int)p[W] + (int)p[W + 1];
+}
+
+__device__ void apply_leaf_transform(const uint8_t *__restrict__ x, uint8_t *__restrict__ y, int W, int H, int rx,
+                                     int ry, int B, int dx, int dy, int iso, int c, int O) {
+    if (rx < 0 || ry < 0 || rx + B > W || ry + B > H || dx < 0 || dy < 0 || dx + 2 * B > W || dy + 2 * B > H) return;
+    const int lgB = 31 - __clz(B);
+    const long long n = (long long)B * B;
+    long long sd = 0;
+    for (int v = 0; v < B; ++v)
+        for (int u = 0; u < B; ++u) sd += d4_at(x, W, dx + 2 * u, dy + 2 * v);
+    const long long base = 512 * n * O - (long long)c * sd + 256 * n;
+    for (int v = 0; v < B; ++v) {
+        for (int u = 0; u < B; ++u) {
+            int su, sv;
+            iso_src(iso, B, u, v, su, sv);
+            const long long num = base + (long long)c * n * d4_at(x, W, dx + 2 * su, dy + 2 * sv);
+            long long pix = num >> (9 + 2 * lgB);  // 512 n is a power of two: floor division
+            pix = pix < 0 ? 0 : (pix > 255 ? 255 : pix);
+            y[(size_t)(ry + v) * W + rx + u] = (uint8_t)pix;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    decode_leaf_kernel(const DecDesc *__restrict__ descs, int src) {
+    const DecDesc &D = descs[blockIdx.y];
+    const int nrec = (int)D.tile_off[D.tw * D.th];
+    const uint8_t *x = D.buf[src];
+    uint8_t *y = D.buf[src ^ 1];
+    const int bmax = D.W / D.tw, ko1 = (1 << D.o_bits) - 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrec; i += gridDim.x * blockDim.x) {
+        const uint4 r = *reinterpret_cast<const uint4 *>(D.rec + i);
+        const int rx = (int)(r.x & 0xffffu), ry = (int)(r.x >> 16);
+        const int level = (int)(r.y & 0xffu), phase = (int)((r.y >> 8) & 0xffu);
+        const int k = (int)((r.y >> 16) & 0xffu), q = (int)(r.y >> 24);
+        const int iso = (int)(r.z >> 24);
+        const int dx = (int)(r.w & 0xffffu), dy = (int)(r.w >> 16);
+        if (level < 1 || level > D.L) continue;
+        const int B = bmax >> (level - 1);
+        const int O = (int)__umulhi((uint32_t)(510 * q + ko1), c_lum_magic[D.o_bits]);  // L(q)
+        if (phase == 1) {
+            apply_leaf_transform(x, y, D.W, D.H, rx, ry, B, dx, dy, iso, contrast_code(k, D.s_bits), O);
+        } else {
+            const int h = B / 2;
+            const int d0 = (int)(int8_t)(r.z & 0xffu), d1 = (int)(int8_t)((r.z >> 8) & 0xffu);
+            const int d2 = (int)(int8_t)((r.z >> 16) & 0xffu);
+            const int Ok[4] = {O + d0, O + d1, O + d2, O - (d0 + d1 + d2)};  // eq. (1)
+            for (int sb = 0; sb < 4; ++sb) {
+                const int sx = rx + (sb & 1) * h, sy = ry + (sb >> 1) * h;
+                int sdx, sdy;
+                if (D.phase2_domain) {
+                    sdx = centred_origin(rx, B, D.W) + (sb & 1) * B;
+                    sdy = centred_origin(ry, B, D.H) + (sb >> 1) * B;
+                } else {
+                    sdx = centred_origin(sx, h, D.W);
+                    sdy = centred_origin(sy, h, D.H);
+                }
+                apply_leaf_transform(x, y, D.W, D.H, sx, sy, h, sdx, sdy, 0, phase2_code(level, (k >> sb) & 1),
+                                     Ok[sb]);
+            }
+        }
+    }
+}
+
+// `hdec`: the host copy of the descriptors (the iterate buffers of the
+// memset); `max_recs`: the largest record capacity of the batch.
+cudaError_t launch_decode_leaves(const DecDesc *d_descs, const DecDesc *hdec, int count, int max_recs, int iters,
+                                 cudaStream_t st) {
+    if (iters < 1 || count < 1 || count > 65535) return cudaErrorInvalidValue;
+    // iteration t writes buffer (iters - 1 - t) & 1: the last one writes buf[0]
+    const int first_src = ((iters - 1) & 1) ^ 1;
+    for (int i = 0; i < count; ++i) {
+        const cudaError_t e =
+            cudaMemsetAsync(hdec[i].buf[first_src], 128, (size_t)hdec[i].W * (size_t)hdec[i].H, st);
+        if (e != cudaSuccess) return e;
+    }
+    int gx = (max_recs + 255) / 256;
+    gx = gx < 1 ? 1 : (gx > 4096 ? 4096 : gx);
+    for (int t = 0; t < iters; ++t) {
+        const int src = ((iters - 1 - t) & 1) ^ 1;
+        decode_leaf_kernel<<<dim3(gx, count), 256, 0, st>>>(d_descs, src);
+        stage_mark(st, "decode_leaf_kernel");
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_decode(int bmax, const DecDesc *d_descs, int count, int total_strips, void *tables, int iters,
                           bool d4, const DecTune &tune, cudaStream_t st) {
     switch (bmax) {

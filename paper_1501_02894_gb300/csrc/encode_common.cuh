@@ -220,6 +220,13 @@ __device__ __forceinline__ void half_moments(const uint32_t *d4e, int c, int rr,
     sdr = (int)a_dr;
 }
 
+// 2x2 sums of two rows of four pixels: (p0+p1+q0+q1) | (p2+p3+q2+q3) << 16.
+__device__ __forceinline__ uint32_t pair2x2(uint32_t a, uint32_t b) {
+    const uint32_t lo = __dp4a(a, 0x00000101u, __dp4a(b, 0x00000101u, 0u));
+    const uint32_t hi = __dp4a(a, 0x01010000u, __dp4a(b, 0x01010000u, 0u));
+    return __byte_perm(lo, hi, 0x5410);
+}
+
 // Phase-1 summary of a block that the level loop carries forward.
 struct Code {
     int k, q;

@@ -58,7 +58,11 @@ constexpr uint32_t kAgg = 1u << 30, kIncl = 2u << 30, kValMask = (1u << 30) - 1;
 //   word per strip of scratch).
 // NW warps per CTA: 8 (registers capped at 80 for 3 CTAs = 24 warps per SM)
 // or 4 (up to 128 registers, no spills, 4 CTAs = 16 warps per SM).
-template <int BMAX, bool SLOTS, int NW>
+// MIN2 (slot variant only): the quadtree goes down to 2 x 2 blocks (bmin 2);
+//   their domains (4 x 4 pixels, odd origins inside the image) are read from
+//   the raw window, which is then kept until the strip is done, and the up to
+//   256 leaves of a strip are staged in shared memory by canonical position.
+template <int BMAX, bool SLOTS, int NW, bool MIN2 = false>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
     mns_encode_kernel(const EncDesc *__restrict__ descs, int count, int total_strips,
                       uint32_t *__restrict__ status, uint32_t *__restrict__ ticket, int total_chunks, int dyn,
@@ -74,8 +78,14 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // TMA destinations need 128-byte alignment in the shared window
     uint8_t *const smem_a = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
-    uint8_t *raw = smem_a + warp * (RAWB + G::WORDS * 4);
+    // staged leaves + their position mask (8 words, padded: every warp's
+    // window must start 128-byte aligned for its TMA copies)
+    constexpr int STAGE = MIN2 ? 256 * 16 + 128 : 0;
+    static_assert((RAWB + G::WORDS * 4 + STAGE) % 128 == 0, "per-warp shared memory keeps TMA alignment");
+    uint8_t *raw = smem_a + warp * (RAWB + G::WORDS * 4 + STAGE);
     uint32_t *d4e = reinterpret_cast<uint32_t *>(raw + RAWB);
+    uint4 *lrec = reinterpret_cast<uint4 *>(raw + RAWB + G::WORDS * 4);
+    uint32_t *lmask = reinterpret_cast<uint32_t *>(lrec + (MIN2 ? 256 : 0));
     uint64_t *bar = &s_bar[warp];
     const int pr = lane / PC, pc = lane % PC;
     const unsigned FULL = 0xffffffffu;
@@ -175,9 +185,11 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
             rw[i] = valid ? *reinterpret_cast<const uint2 *>(raw + (sy0 + 4 * pr + i - ry0) * pitch + sx0 + 8 * pc - ax0)
                           : make_uint2(0u, 0u);
         stage_window_smem<BMAX, UPR, NP>(raw, pitch, (ax1 - ax0) >> 4, d4e, lane);
+        if (MIN2 && lane < 8) lmask[lane] = 0u;
         __syncwarp();
-        // the window buffer is free: fetch the next strip's window now
-        if (lane == 0) {
+        // the window buffer is free (MIN2: once the 2 x 2 blocks are done):
+        // fetch the next strip's window now
+        if (!MIN2 && lane == 0) {
             if (g_next < total_strips) issue_window(g_next);
         }
         int g_after = g_next + gstep;
@@ -393,6 +405,108 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
                         cur4[h].pass = ch[h].pass;
                     }
                 }
+            } else if (MIN2 && j < L) {
+                // B == 4 above the last level: each half is a 4 x 4 block of
+                // level j with four 2 x 2 children at level j + 1 = L, fitted
+                // against their own centred domains (Section 3; phase 2 of the
+                // 4 x 4 block, Sections 3.1-3.2, tests them as its sub-blocks)
+                const long long thr_p2 = D.t2q[j - 1] << 14;  // n = 4: t2q n^2 1024
+                const int dmax = (j == 1) ? 15 : 31;
+                const int c0 = phase2_code(j, 0), c1 = phase2_code(j, 1);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int xh = sx0 + 8 * pc + 4 * h, yh = sy0 + 4 * pr;
+                    const int tx = 8 * pc + 4 * h - lane_top * BMAX, ty = 4 * pr;
+                    const int posh = lane_top * cpt + (int)morton3(tx >> 1, ty >> 1);
+                    const int dxh = centred_origin(xh, 4, W), dyh = centred_origin(yh, 4, H);
+                    if (act) fits += 1;
+                    if (act && cur4[h].pass)
+                        make_leaf(leaf[h], xh, yh, j, 1, cur4[h].k, cur4[h].q, 0, 0, 0, dxh, dyh, posh);
+                    const bool need_h = act && !cur4[h].pass;
+                    if (!__any_sync(FULL, need_h)) continue;
+                    if (ph2 && need_h) fits += 4;
+                    const int Oi = lum(cur4[h].q, ko1, magic);
+                    int csr[4], csrr[4], dl[4];
+                    bool inr = true;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int bi = k & 1, bj = k >> 1;
+                        const uint32_t t = h ? rw[2 * bj].y : rw[2 * bj].x;
+                        const uint32_t u = h ? rw[2 * bj + 1].y : rw[2 * bj + 1].x;
+                        const uint32_t m1 = bi ? 0x01010000u : 0x00000101u, mb = bi ? 0xffff0000u : 0x0000ffffu;
+                        csr[k] = (int)__dp4a(t, m1, __dp4a(u, m1, 0u));
+                        csrr[k] = (int)__dp4a(t, t & mb, __dp4a(u, u & mb, 0u));
+                        // round half up of (mean_k - O_i), n = 4
+                        dl[k] = (2 * (csr[k] - (Oi << 2)) + 4) >> 3;
+                        inr = inr && dl[k] <= dmax && dl[k] >= -dmax;
+                    }
+                    const int O3 = Oi - (dl[0] + dl[1] + dl[2]);  // eq. (1)
+                    bool allok = true;
+                    int sb = 0;
+                    uint4 cw[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int bi = k & 1, bj = k >> 1;
+                        const int xc = xh + 2 * bi, yc = yh + 2 * bj;
+                        const int dxc = centred_origin(xc, 2, W), dyc = centred_origin(yc, 2, H);
+                        const uint32_t t = h ? rw[2 * bj].y : rw[2 * bj].x;
+                        const uint32_t u = h ? rw[2 * bj + 1].y : rw[2 * bj + 1].x;
+                        // moments of the child against a 4 x 4 domain read from
+                        // the raw window (any column parity)
+                        auto dom = [&](int ddx, int ddy, Fit &f) {
+                            const int o = ddx - ax0;
+                            const uint8_t *rp = raw + (ddy - ry0) * pitch + (o & ~3);
+                            uint32_t rr[4];
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                const uint32_t w0 = *reinterpret_cast<const uint32_t *>(rp + r * pitch);
+                                const uint32_t w1 = *reinterpret_cast<const uint32_t *>(rp + r * pitch + 4);
+                                rr[r] = __funnelshift_r(w0, w1, 8 * (o & 3));
+                            }
+                            const uint32_t top = pair2x2(rr[0], rr[1]), bot = pair2x2(rr[2], rr[3]);
+                            const int sdr = bi ? (int)dp2a_hi(top, t, dp2a_hi(bot, u, 0u))
+                                               : (int)dp2a_lo(top, t, dp2a_lo(bot, u, 0u));
+                            const uint32_t pk = top + bot;
+                            const int sd = (int)((pk & 0xffffu) + (pk >> 16));
+                            unsigned ql = 0, qh = 0;
+                            acc_sq(top, ql, qh);
+                            acc_sq(bot, ql, qh);
+                            const int sdd = (int)(ql + (qh << 8));
+                            f.sr = csr[k];
+                            f.ncrr = ((long long)csrr[k] << 2) - (long long)csr[k] * csr[k];
+                            f.ncdr = ((long long)sdr << 2) - (long long)sd * csr[k];
+                            f.ncdd = ((long long)sdd << 2) - (long long)sd * sd;
+                        };
+                        Fit f;
+                        dom(dxc, dyc, f);
+                        const int kc = best_contrast<true>(f.ncdr, f.ncdd, s_bits);
+                        int bd;
+                        const int qc = best_luminance(csr[k], 2, ko1, magic, qscale, bd);
+                        // the phase-2 sub-block fit: against its own centred domain
+                        // or, with the other reading, quadrant k of the parent's
+                        if (D.phase2_domain) dom(dxh + 4 * bi, dyh + 4 * bj, f);
+                        int bit;
+                        const bool ok = fit_phase2_sub(f, 2, k == 3 ? O3 : Oi + dl[k], c0, c1, thr_p2, bit);
+                        allok = allok && ok;
+                        sb |= bit << k;
+                        cw[k] = make_uint4((uint32_t)xc | ((uint32_t)yc << 16),
+                                           (uint32_t)(j + 1) | (1u << 8) | ((uint32_t)kc << 16) | ((uint32_t)qc << 24),
+                                           0u, (uint32_t)dxc | ((uint32_t)dyc << 16));
+                    }
+                    const bool p2 = ph2 && need_h && inr && allok;
+                    if (p2) make_leaf(leaf[h], xh, yh, j, 2, sb, cur4[h].q, dl[0], dl[1], dl[2], dxh, dyh, posh);
+                    if (need_h && !p2) {
+                        splitbits |= 1u << (((1u << (2 * (j - 1))) - 1) / 3 + morton3(tx >> 2, ty >> 2));
+                        fits += 4;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int pos = lane_top * cpt + (int)morton3((tx >> 1) + (k & 1), (ty >> 1) + (k >> 1));
+                            lrec[pos] = cw[k];
+                            atomicOr(lmask + (pos >> 5), 1u << (pos & 31));
+                        }
+                    }
+                }
+                break;
             } else {
                 // B == 4: last level, forced acceptance (two leaves per lane)
 #pragma unroll
@@ -409,6 +523,52 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 4)
             }
         }
 
+        if (MIN2 && SLOTS) {
+            // the raw window is free now: fetch the next strip's
+            __syncwarp();
+            if (lane == 0 && g_next < total_strips) issue_window(g_next);
+            // the lanes' own leaves join the staged ones; then each lane
+            // stores the leaves at positions lane, lane + 32, ... at their
+            // canonical ranks
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (leaf[h].pos < 0) continue;
+                lrec[leaf[h].pos] = make_uint4(leaf[h].w0, leaf[h].w1, leaf[h].w2, leaf[h].w3);
+                atomicOr(lmask + (leaf[h].pos >> 5), 1u << (leaf[h].pos & 31));
+            }
+            __syncwarp();
+            uint32_t mw[8], before[8];
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                mw[w] = lmask[w];
+                before[w] = run;
+                run += (uint32_t)__popc(mw[w]);
+            }
+            fic_record *slot = D.slots + (size_t)s * D.slot_recs;
+            const uint32_t below = (1u << lane) - 1u;
+#pragma unroll
+            for (int w = 0; w < 8; ++w)
+                if ((mw[w] >> lane) & 1u)
+                    *reinterpret_cast<uint4 *>(slot + before[w] + (uint32_t)__popc(mw[w] & below)) = lrec[32 * w + lane];
+            const unsigned ftot = __reduce_add_sync(FULL, fits);
+            splitbits = group_or<PC>(splitbits, BMAX / 8, BMAX / 4);
+            if (valid && (8 * pc) % BMAX == 0 && pr == 0) {
+                const int p0 = lane_top * cpt;  // first position of the lane's top-level block
+                uint32_t first = 0;
+#pragma unroll
+                for (int w = 0; w < 8; ++w)
+                    first += (32 * w + 32 <= p0) ? (uint32_t)__popc(mw[w])
+                           : (32 * w < p0 ? (uint32_t)__popc(mw[w] & ((1u << (p0 & 31)) - 1u)) : 0u);
+                D.split[top0 + lane_top] = splitbits;
+                D.tile_off[top0 + lane_top] = first;
+            }
+            if (lane == 0) D.stats[s] = make_uint2(run, ftot & 0x7fffffffu);
+            __syncwarp();
+            g = ticketed ? __shfl_sync(FULL, g_next, 0) : g_next;
+            g_next = g_after;
+            continue;
+        }
         // ---- canonical ranks, look-back, stores
         unsigned long long mine = 0;
         if (leaf[0].pos >= 0) mine |= 1ull << leaf[0].pos;
@@ -528,37 +688,38 @@ __global__ void encode_init_kernel(const EncDesc *__restrict__ descs, int count,
     if (i == 0) *ticket = 0u;
 }
 
-size_t mns_smem_bytes(int bmax, int nw) {
-    const size_t per = bmax == 32 ? WinBox<32>::W * WinBox<32>::H + Geom<32>::WORDS * 4
-                     : bmax == 16 ? WinBox<16>::W * WinBox<16>::H + Geom<16>::WORDS * 4
-                                  : WinBox<8>::W * WinBox<8>::H + Geom<8>::WORDS * 4;
+size_t mns_smem_bytes(int bmax, int nw, bool min2) {
+    const size_t per = (bmax == 32 ? WinBox<32>::W * WinBox<32>::H + Geom<32>::WORDS * 4
+                        : bmax == 16 ? WinBox<16>::W * WinBox<16>::H + Geom<16>::WORDS * 4
+                                     : WinBox<8>::W * WinBox<8>::H + Geom<8>::WORDS * 4) +
+                       (min2 ? 256 * 16 + 128 : 0);
     return (size_t)nw * per + 128;  // + alignment slack
 }
 
 int mns_strip_width(int bmax) { return 1024 / bmax; }
 
 // Resident CTAs per SM of one instantiation (its occupancy limit, per device).
-template <int BMAX, bool SLOTS, int NW>
+template <int BMAX, bool SLOTS, int NW, bool MIN2>
 static int mns_occupancy(int &sms) {
     static KernelSlots ks;
     int per = 0;
-    if (kernel_slots(ks, (const void *)mns_encode_kernel<BMAX, SLOTS, NW>, NW * 32, mns_smem_bytes(BMAX, NW), sms,
-                     per) != cudaSuccess)
+    if (kernel_slots(ks, (const void *)mns_encode_kernel<BMAX, SLOTS, NW, MIN2>, NW * 32,
+                     mns_smem_bytes(BMAX, NW, MIN2), sms, per) != cudaSuccess)
         return 0;
     return per;
 }
 
-template <int BMAX, bool SLOTS, int NW>
+template <int BMAX, bool SLOTS, int NW, bool MIN2 = false>
 static cudaError_t launch_t(const EncDesc *descs, int count, int total_strips, uint32_t *status,
                             uint32_t *ticket, int total_chunks, int ctas_per_sm, int dyn, int fused,
                             cudaStream_t st) {
     int sms = 0;
-    const int per = mns_occupancy<BMAX, SLOTS, NW>(sms);
+    const int per = mns_occupancy<BMAX, SLOTS, NW, MIN2>(sms);
     if (per == 0) return cudaErrorInvalidValue;
     const int k = ctas_per_sm > 0 && ctas_per_sm < per ? ctas_per_sm : per;
     const int need = (total_strips + NW - 1) / NW;
     const int grid = need < sms * k ? need : sms * k;
-    mns_encode_kernel<BMAX, SLOTS, NW><<<grid, NW * 32, mns_smem_bytes(BMAX, NW), st>>>(
+    mns_encode_kernel<BMAX, SLOTS, NW, MIN2><<<grid, NW * 32, mns_smem_bytes(BMAX, NW, MIN2), st>>>(
         descs, count, total_strips, status, ticket, total_chunks, dyn, fused);
     stage_mark(st, "mns_encode_kernel");
     return cudaGetLastError();
@@ -600,7 +761,9 @@ cudaError_t launch_mns32_slots(const EncDesc *d_descs, int count, int total_stri
 cudaError_t launch_mns_encode_slots(int bmax, const EncDesc *d_descs, int count, int total_strips, int total_chunks,
                                     uint32_t *pack_status, uint32_t *ticket, const EncTune &tune, cudaStream_t st) {
     cudaError_t e;
-    const int k = tune.ctas_per_sm, dyn = tune.dynamic ? 1 : 0, fused = tune.fused_pack ? 1 : 0;
+    const int k = tune.ctas_per_sm, dyn = tune.dynamic ? 1 : 0;
+    // fused packing copies at most 64 records per strip: not with 2 x 2 leaves
+    const int fused = tune.fused_pack && !tune.min2 ? 1 : 0;
     uint32_t *tk = dyn ? ticket : nullptr;
     const bool w4 = tune.warps == 4;
     if (fused) {
@@ -614,14 +777,23 @@ cudaError_t launch_mns_encode_slots(int bmax, const EncDesc *d_descs, int count,
         if (e != cudaSuccess || fused) return e;
         return launch_pack(d_descs, count, total_chunks, pack_status, tk, st);
     }
-#define FIC_SLOTS_LAUNCH(B)                                                                                       \
-    e = w4 ? launch_t<B, true, 4>(d_descs, count, total_strips, pack_status, tk, total_chunks, k, dyn, fused, st)   \
-           : launch_t<B, true, kWarps>(d_descs, count, total_strips, pack_status, tk, total_chunks, k, dyn, fused, st)
-    switch (bmax) {
-    case 32: FIC_SLOTS_LAUNCH(32); break;
-    case 16: FIC_SLOTS_LAUNCH(16); break;
-    case 8: FIC_SLOTS_LAUNCH(8); break;
-    default: return cudaErrorInvalidValue;
+#define FIC_SLOTS_LAUNCH(B, M2)                                                                                    \
+    e = w4 ? launch_t<B, true, 4, M2>(d_descs, count, total_strips, pack_status, tk, total_chunks, k, dyn, fused, st) \
+           : launch_t<B, true, kWarps, M2>(d_descs, count, total_strips, pack_status, tk, total_chunks, k, dyn, fused, \
+                                            st)
+    if (tune.min2) {
+        switch (bmax) {
+        case 16: FIC_SLOTS_LAUNCH(16, true); break;
+        case 8: FIC_SLOTS_LAUNCH(8, true); break;
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (bmax) {
+        case 32: FIC_SLOTS_LAUNCH(32, false); break;
+        case 16: FIC_SLOTS_LAUNCH(16, false); break;
+        case 8: FIC_SLOTS_LAUNCH(8, false); break;
+        default: return cudaErrorInvalidValue;
+        }
     }
 #undef FIC_SLOTS_LAUNCH
     if (e != cudaSuccess || fused) return e;
@@ -682,6 +854,7 @@ extern "C" int fic_encode_noalloc(const uint8_t *d_img, int width, int height, c
     int rc = fic_validate(width, height, p);
     if (rc) return rc;
     if (p->mode != FIC_NOSEARCH && p->mode != FIC_MNS) return FIC_EBADPARAM;  // centred-domain modes only
+    if (p->bmin < 4) return FIC_EBADPARAM;  // leaves of 4 x 4 pixels or more
     if (!d_img || (reinterpret_cast<uintptr_t>(d_img) & 15) || !out) return FIC_EBADPARAM;
     if (!out->records || !out->tile_offsets || !out->split || !out->info || out->capacity <= 0)
         return FIC_EBADPARAM;
@@ -736,6 +909,7 @@ extern "C" int fic_encode_noalloc(const uint8_t *d_img, int width, int height, c
     d.local_radius = p->local_radius;
     d.local_step = p->local_step;
     d.bmax = bmax;
+    d.slot_recs = 64;
     {
         const int bw = bmax == 32 ? WinBox<32>::W : (bmax == 16 ? WinBox<16>::W : WinBox<8>::W);
         d.boxw = bw < width ? bw : width;

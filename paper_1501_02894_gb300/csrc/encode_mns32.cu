@@ -38,15 +38,9 @@ constexpr int kRawBytes = 64 * 64;  // the TMA window: the level-1 domain
 constexpr int kNP = 16;             // words (2x2-sum pairs) per decimated row
 constexpr int kWords = 32 * kNP;
 constexpr int kPerWarp = kRawBytes + kWords * 4;
+static_assert(kPerWarp % 128 == 0, "every warp's TMA window starts 128-byte aligned");
 constexpr int kSlotRecs = 64;
 }  // namespace m32
-
-// 2x2 sums of two rows of four pixels: (p0+p1+q0+q1) | (p2+p3+q2+q3) << 16.
-__device__ __forceinline__ uint32_t pair2x2(uint32_t a, uint32_t b) {
-    const uint32_t lo = __dp4a(a, 0x00000101u, __dp4a(b, 0x00000101u, 0u));
-    const uint32_t hi = __dp4a(a, 0x01010000u, __dp4a(b, 0x01010000u, 0u));
-    return __byte_perm(lo, hi, 0x5410);
-}
 
 // Moments of a lane's 8 x 4 patch against the 8 x 4 decimated domain values
 // at column c (even), row rr of the decimated window.  W64: c is a multiple

@@ -38,7 +38,8 @@ struct EncDesc {
     const TmaMap *map;   // 2-D tensor map of the image (box: the strip's domain window)
     int32_t boxw;        // box width in pixels (= row pitch of the staged window)
     int32_t bmax;
-    fic_record *slots;   // slot variant: 64 records per strip (workspace)
+    fic_record *slots;   // slot variant: slot_recs records per strip (workspace)
+    int32_t slot_recs;   // records a strip can emit: 64, or 256 when bmin is 2
     uint2 *stats;        // slot variant: per strip (record count, fits)
     int32_t chunk_base;  // slot variant: first 32-strip chunk of the image (pack kernel)
     int32_t nchunks;
@@ -124,8 +125,9 @@ struct EncTune {
     int dynamic = 0;      // 1: strips from an atomic counter, 0: static grid stride
     int fused_pack = 0;   // 1: the warp finishing a chunk packs it; 0: a separate pack kernel
                           // (measured faster: the per-strip release fence costs more than the launch)
-    int kernel32 = 0;     // set by the plan: 1 = mns32_kernel (bmax 32, sub-blocks on their own
-                          // centred domains), 0 = the general mns_encode_kernel
+    int kernel32 = 0;     // set by the plan: 1 = mns_encode32_kernel (bmax 32, sub-blocks on their
+                          // own centred domains), 0 = the general mns_encode_kernel
+    int min2 = 0;         // set by the plan: a stream of the batch has 2 x 2 leaves
 };
 struct DecTune {
     int ctas_per_sm = 0;    // resident CTAs per SM of the iteration kernel; 0 = the occupancy limit

@@ -19,7 +19,6 @@
 namespace fic {
 
 constexpr int kPackWarps = 8;
-constexpr int kSlotRecs = 64;
 
 __global__ void __launch_bounds__(kPackWarps * 32)
     pack_kernel(const EncDesc *__restrict__ descs, int count, int total_chunks, uint32_t *__restrict__ ticket) {
@@ -69,7 +68,7 @@ __global__ void __launch_bounds__(kPackWarps * 32)
             const int sidx = cl * 32 + j;
             const uint32_t n = (j < 32 && sidx < D.nstrips) ? D.stats[sidx].x : 0u;
             pre_n[t] = n;
-            const fic_record *src = D.slots + (size_t)sidx * kSlotRecs;
+            const fic_record *src = D.slots + (size_t)sidx * D.slot_recs;
             pre[t][0] = (uint32_t)lane < n ? *reinterpret_cast<const uint4 *>(src + lane) : make_uint4(0u, 0u, 0u, 0u);
             pre[t][1] = (uint32_t)lane + 32u < n ? *reinterpret_cast<const uint4 *>(src + lane + 32)
                                                 : make_uint4(0u, 0u, 0u, 0u);
@@ -155,6 +154,13 @@ __global__ void __launch_bounds__(kPackWarps * 32)
             *reinterpret_cast<uint4 *>(D.rec + off + lane) = pre[t][0];
         if ((uint32_t)lane + 32u < n && off + lane + 32 < (uint32_t)D.capacity)
             *reinterpret_cast<uint4 *>(D.rec + off + lane + 32) = pre[t][1];
+        // slots of 2 x 2 leaves hold up to 256 records: the rest directly
+        if (n > 64u) {
+            const fic_record *src = D.slots + (size_t)(cl * 32 + j) * D.slot_recs;
+            for (uint32_t k = 64u + (uint32_t)lane; k < n; k += 32u)
+                if (off + k < (uint32_t)D.capacity)
+                    *reinterpret_cast<uint4 *>(D.rec + off + k) = *reinterpret_cast<const uint4 *>(src + k);
+        }
     }
 }
 

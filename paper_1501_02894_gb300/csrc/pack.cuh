@@ -102,7 +102,7 @@ __device__ __forceinline__ bool pack_chunk_warp(const EncDesc &D, int cl, uint32
     // copy the 32 slots: lane-strided over each slot's records
     for (int j = 0; j < 32 && cl * 32 + j < D.nstrips; ++j) {
         const uint32_t n = __shfl_sync(FULL, cnt, j), off = __shfl_sync(FULL, excl, j);
-        const fic_record *src = D.slots + (size_t)(cl * 32 + j) * 64;
+        const fic_record *src = D.slots + (size_t)(cl * 32 + j) * D.slot_recs;
         for (uint32_t k = lane; k < n; k += 32) {
             if (off + k < (uint32_t)D.capacity) *reinterpret_cast<uint4 *>(D.rec + off + k) = ld_cg4(src + k);
         }

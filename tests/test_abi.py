@@ -40,7 +40,10 @@ def test_host_only_calls(libfic):
     assert fic.validate(512, 512, p) == 0
     assert fic.validate(500, 512, p) == -1            # not a multiple of bmax
     assert fic.validate(32, 64, p) == -1              # smaller than 2*bmax
-    assert fic.validate(512, 512, fic.params("mns", 32, 2, 8.0)) == -2   # bmin below 4
+    assert fic.validate(512, 512, fic.params("mns", 32, 2, 8.0)) == -2   # five levels (32 -> 2)
+    assert fic.validate(512, 512, fic.params("mns", 16, 2, 8.0, s_bits=3, o_bits=8)) == 0  # the paper's 16 -> 2
+    assert fic.validate(256, 256, fic.params("nosearch", 8, 2, 8.0)) == 0
+    assert fic.validate(512, 512, fic.params("local", 16, 2, 8.0)) == -2  # 2 x 2 leaves: centred modes only
     assert fic.validate(512, 512, fic.params("mns", 64, 4, 8.0)) == -2   # bmax above 32
     assert fic.validate(512, 512, fic.params("mns", 32, 4, -1.0)) == -2
     ntop, cap = ctypes.c_int32(), ctypes.c_int32()
