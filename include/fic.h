@@ -333,6 +333,21 @@ FIC_API int fic_serialize(const fic_stream *st, int technique2, uint32_t *d_word
  * for it). */
 FIC_API int fic_parse(const uint32_t *d_words, int64_t nwords, const uint64_t *d_tile_bits, int technique2,
                       fic_stream *out, void *d_workspace, size_t workspace_bytes, void *stream);
+/* The same for `count` streams at once (Sections 3.3-3.4): three kernel
+ * launches for every 48 streams instead of three per stream.  Stream i uses
+ * d_words[i] (nwords[i] words, at least fic_bitstream_max_words; zeroed by
+ * the writer) and d_tile_bits[i]; one workspace of
+ * fic_bitstream_batch_workspace_bytes holds every stream's scans.  Results
+ * are those of fic_serialize / fic_parse on each stream.  Errors as there;
+ * the first bad argument of any stream fails the whole call before anything
+ * is enqueued for the streams after it. */
+FIC_API size_t fic_bitstream_batch_workspace_bytes(const fic_stream *sts, int count);
+FIC_API int fic_serialize_batch(const fic_stream *sts, int count, int technique2, uint32_t *const *d_words,
+                                const int64_t *nwords, uint64_t *const *d_tile_bits, void *d_workspace,
+                                size_t workspace_bytes, void *stream);
+FIC_API int fic_parse_batch(const uint32_t *const *d_words, const int64_t *nwords, const uint64_t *const *d_tile_bits,
+                            int technique2, fic_stream *outs, int count, void *d_workspace, size_t workspace_bytes,
+                            void *stream);
 
 /* ---- Resolution-independent decoding (Section 1) ----
  * The stored transforms describe the image at no particular resolution.

@@ -24,8 +24,10 @@ from .fic import (  # noqa: F401
     offset_histogram,
     params,
     parse,
+    parse_batch,
     rescale,
     serialize,
+    serialize_batch,
     stream_sizes,
     validate,
 )

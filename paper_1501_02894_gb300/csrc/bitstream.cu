@@ -18,11 +18,14 @@
 // block independently.
 //
 // Writer: a warp per top-level block sizes its leaves (warp sum), a scan
-// over the blocks gives the index, and the warp then writes every leaf's
-// fields at its bit offset with atomicOr (fields may straddle words and
-// blocks may share a word).  Reader: a thread per block parses it twice --
-// once to count its leaves (scanned into tile offsets), once to write the
-// records, split masks and the record count.
+// over each stream's blocks gives the index (and zeroes its words), and the
+// warp then writes every leaf's fields at its bit offset with atomicOr
+// (fields may straddle words and blocks may share a word).  Reader: a thread
+// per block parses it twice -- once to count its leaves (scanned into tile
+// offsets), once to write the records, split masks and the record count.
+// Every kernel covers a whole batch of streams (up to kBitBatch per launch,
+// their descriptors passed by value as the kernel's parameter), so writing
+// or reading any number of streams takes three launches per kBitBatch.
 #include "fic_internal.cuh"
 
 namespace fic {
@@ -140,64 +143,63 @@ __device__ __forceinline__ uint32_t get_bits(const uint32_t *w, unsigned long lo
     return (uint32_t)(both >> sh) & (nb == 32 ? 0xffffffffu : ((1u << nb) - 1u));
 }
 
-// ---- writer
+// ---- batches
 
-__global__ void tile_size_kernel(BitLayout b, const fic_record *__restrict__ rec, const uint32_t *__restrict__ toff,
-                                 int ntop, unsigned long long *__restrict__ sizes) {
-    const int lane = threadIdx.x & 31;
-    const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (t >= ntop) return;
-    const uint32_t beg = toff[t], end = toff[t + 1];
-    unsigned long long s = 0;
-    for (uint32_t i = beg + lane; i < end; i += 32) s += (unsigned)leaf_bits(b, *reinterpret_cast<const uint4 *>(rec + i));
-    for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-    if (lane == 0) sizes[t] = s;
-}
+constexpr int kBitBatch = 48;  // streams per launch (descriptors travel as the kernel parameter)
 
-__global__ void write_kernel(BitLayout b, const fic_record *__restrict__ rec, const uint32_t *__restrict__ toff,
-                             int ntop, const unsigned long long *__restrict__ tile_bits, uint32_t *__restrict__ words) {
-    const int lane = threadIdx.x & 31;
-    const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (t >= ntop) return;
-    const uint32_t beg = toff[t], end = toff[t + 1];
-    unsigned long long base = tile_bits[t];
-    for (uint32_t i0 = beg; i0 < end; i0 += 32) {
-        const uint32_t i = i0 + lane;
-        const bool has = i < end;
-        uint4 r = make_uint4(0u, 0u, 0u, 0u);
-        uint32_t v[9];
-        int n[9];
-        int f = 0, s = 0;
-        if (has) {
-            r = *reinterpret_cast<const uint4 *>(rec + i);
-            f = leaf_fields(b, r, v, n);
-            for (int j = 0; j < f; ++j) s += n[j];
-        }
-        // exclusive prefix of the leaf sizes over the lanes
-        int incl = s;
-        for (int m = 1; m < 32; m <<= 1) {
-            const int o = __shfl_up_sync(0xffffffffu, incl, m);
-            if (lane >= m) incl += o;
-        }
-        unsigned long long pos = base + (unsigned)(incl - s);
-        for (int j = 0; j < f; ++j) {
-            put_bits(words, pos, v[j], n[j]);
-            pos += (unsigned)n[j];
-        }
-        base += (unsigned)__shfl_sync(0xffffffffu, incl, 31);
+// One stream of a batch.
+struct BitDesc {
+    BitLayout b;
+    int ntop;
+    const fic_record *rec;        // serialize: the stream's records and tile offsets
+    const uint32_t *toff;
+    uint32_t *words;              // serialize: output words (nwords, zeroed here)
+    const uint32_t *words_in;     // parse: input words
+    long long nwords;
+    unsigned long long *tile_bits;     // serialize: output index; parse: input index (read only)
+    unsigned long long *sizes;         // workspace: per block bits (serialize) or leaf counts (parse)
+    unsigned long long *first;         // workspace (parse): exclusive scan of the counts
+    fic_record *out_rec;          // parse outputs
+    uint32_t *out_toff, *out_split, *out_info;
+};
+
+struct BitBatch {
+    int count;
+    int tops_base[kBitBatch + 1];  // first global block index of each stream
+    BitDesc d[kBitBatch];
+};
+
+// The stream of global block g and its local index.
+__device__ __forceinline__ int batch_stream(const BitBatch &B, int g) {
+    int lo = 0, hi = B.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.tops_base[mid] <= g) lo = mid;
+        else hi = mid - 1;
     }
+    return lo;
 }
 
-// Exclusive scan of n uint64 values into out[0..n] (out[n] = total) by one
-// CTA: each thread sums a contiguous slice, the CTA scans the slice sums,
-// and each thread writes its slice.
-__global__ void scan_kernel(const unsigned long long *__restrict__ in, int n, unsigned long long *__restrict__ out) {
+// Exclusive scan of one stream's n uint64 values into out[0..n] (out[n] =
+// total) by one CTA: each thread sums a contiguous slice, the CTA scans the
+// slice sums, and each thread writes its slice.  Returns (to every thread)
+// whether any value had its top bit set (a block that does not parse).
+__device__ bool cta_scan(const unsigned long long *__restrict__ in, int n, unsigned long long *__restrict__ out) {
     __shared__ unsigned long long s_part[1024];
+    __shared__ int s_bad;
     const int t = threadIdx.x, nt = blockDim.x;
+    if (t == 0) s_bad = 0;
+    __syncthreads();
     const int per = (n + nt - 1) / nt;
     const int lo = min(n, t * per), hi = min(n, lo + per);
     unsigned long long s = 0;
-    for (int i = lo; i < hi; ++i) s += in[i];
+    bool bad = false;
+    for (int i = lo; i < hi; ++i) {
+        const unsigned long long v = in[i];
+        bad = bad || (v >> 63);
+        s += v;
+    }
+    if (bad) s_bad = 1;
     s_part[t] = s;
     __syncthreads();
     for (int off = 1; off < nt; off <<= 1) {
@@ -212,6 +214,68 @@ __global__ void scan_kernel(const unsigned long long *__restrict__ in, int n, un
         acc += in[i];
     }
     if (t == nt - 1) out[n] = s_part[t];
+    __syncthreads();
+    return s_bad != 0;
+}
+
+// ---- writer
+
+__global__ void tile_size_kernel(const __grid_constant__ BitBatch B) {
+    const int lane = threadIdx.x & 31;
+    const int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (g >= B.tops_base[B.count]) return;
+    const BitDesc &D = B.d[batch_stream(B, g)];
+    const int t = g - B.tops_base[batch_stream(B, g)];
+    const uint32_t beg = D.toff[t], end = D.toff[t + 1];
+    unsigned long long s = 0;
+    for (uint32_t i = beg + lane; i < end; i += 32)
+        s += (unsigned)leaf_bits(D.b, *reinterpret_cast<const uint4 *>(D.rec + i));
+    for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if (lane == 0) D.sizes[t] = s;
+}
+
+// One CTA per stream: the index, and the stream's words zeroed.
+__global__ void __launch_bounds__(1024) ser_scan_kernel(const __grid_constant__ BitBatch B) {
+    const BitDesc &D = B.d[blockIdx.x];
+    for (long long i = threadIdx.x; i < D.nwords; i += blockDim.x) D.words[i] = 0u;
+    cta_scan(D.sizes, D.ntop, D.tile_bits);
+}
+
+__global__ void write_kernel(const __grid_constant__ BitBatch B) {
+    const int lane = threadIdx.x & 31;
+    const int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (g >= B.tops_base[B.count]) return;
+    const int si = batch_stream(B, g);
+    const BitDesc &D = B.d[si];
+    const int t = g - B.tops_base[si];
+    const BitLayout &b = D.b;
+    const uint32_t beg = D.toff[t], end = D.toff[t + 1];
+    unsigned long long base = D.tile_bits[t];
+    for (uint32_t i0 = beg; i0 < end; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        const bool has = i < end;
+        uint4 r = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t v[9];
+        int n[9];
+        int f = 0, s = 0;
+        if (has) {
+            r = *reinterpret_cast<const uint4 *>(D.rec + i);
+            f = leaf_fields(b, r, v, n);
+            for (int j = 0; j < f; ++j) s += n[j];
+        }
+        // exclusive prefix of the leaf sizes over the lanes
+        int incl = s;
+        for (int m = 1; m < 32; m <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, m);
+            if (lane >= m) incl += o;
+        }
+        unsigned long long pos = base + (unsigned)(incl - s);
+        for (int j = 0; j < f; ++j) {
+            put_bits(D.words, pos, v[j], n[j]);
+            pos += (unsigned)n[j];
+        }
+        base += (unsigned)__shfl_sync(0xffffffffu, incl, 31);
+    }
 }
 
 // ---- reader
@@ -301,39 +365,47 @@ __device__ int parse_tile(const BitLayout &b, const uint32_t *words, long long n
     return count;
 }
 
-__global__ void parse_count_kernel(BitLayout b, const uint32_t *__restrict__ words, long long nwords,
-                                   const unsigned long long *__restrict__ tile_bits, int ntop,
-                                   unsigned long long *__restrict__ counts, uint32_t *__restrict__ info) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntop; t += gridDim.x * blockDim.x) {
-        const unsigned long long beg = tile_bits[t], end = tile_bits[t + 1];
-        int n = -1;
-        if (end >= beg && end <= (unsigned long long)nwords * 32ull)
-            n = parse_tile<false>(b, words, nwords, beg, end, t, nullptr, nullptr);
-        if (n < 0) {
-            atomicOr(info + FIC_INFO_ERROR, FIC_DEVERR_FORMAT);
-            n = 0;
-        }
-        counts[t] = (unsigned long long)n;
+__global__ void parse_count_kernel(const __grid_constant__ BitBatch B) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= B.tops_base[B.count]) return;
+    const int si = batch_stream(B, g);
+    const BitDesc &D = B.d[si];
+    const int t = g - B.tops_base[si];
+    const unsigned long long beg = D.tile_bits[t], end = D.tile_bits[t + 1];
+    int n = -1;
+    if (end >= beg && end <= (unsigned long long)D.nwords * 32ull)
+        n = parse_tile<false>(D.b, D.words_in, D.nwords, beg, end, t, nullptr, nullptr);
+    // a block that does not parse is marked by the top bit (the scan finds it)
+    D.sizes[t] = n < 0 ? (1ull << 63) : (unsigned long long)n;
+}
+
+// One CTA per stream: tile offsets of the records, the info block.
+__global__ void __launch_bounds__(1024) parse_scan_kernel(const __grid_constant__ BitBatch B) {
+    const BitDesc &D = B.d[blockIdx.x];
+    const bool bad = cta_scan(D.sizes, D.ntop, D.first);
+    if (threadIdx.x == 0) {
+        const uint32_t total = bad ? 0u : (uint32_t)D.first[D.ntop];
+        D.out_info[FIC_INFO_RECORDS] = total;
+        D.out_info[FIC_INFO_ERROR] = bad ? FIC_DEVERR_FORMAT : 0u;
+        D.out_info[FIC_INFO_FITS_LO] = 0u;
+        D.out_info[FIC_INFO_FITS_HI] = 0u;
+        for (int w = FIC_INFO_FITS_HI + 1; w < FIC_INFO_WORDS; ++w) D.out_info[w] = 0u;
+        D.out_toff[D.ntop] = total;
     }
 }
 
-__global__ void parse_write_kernel(BitLayout b, const uint32_t *__restrict__ words, long long nwords,
-                                   const unsigned long long *__restrict__ tile_bits, int ntop,
-                                   const unsigned long long *__restrict__ first, fic_record *__restrict__ rec,
-                                   uint32_t *__restrict__ toff, uint32_t *__restrict__ split,
-                                   uint32_t *__restrict__ info) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntop; t += gridDim.x * blockDim.x) {
-        toff[t] = (uint32_t)first[t];
-        split[t] = 0u;
-        if (info[FIC_INFO_ERROR] & FIC_DEVERR_FORMAT) continue;
-        parse_tile<true>(b, words, nwords, tile_bits[t], tile_bits[t + 1], t, rec + first[t], split);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        toff[ntop] = (uint32_t)first[ntop];
-        info[FIC_INFO_RECORDS] = (uint32_t)first[ntop];
-        info[FIC_INFO_FITS_LO] = 0u;
-        info[FIC_INFO_FITS_HI] = 0u;
-    }
+__global__ void parse_write_kernel(const __grid_constant__ BitBatch B) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= B.tops_base[B.count]) return;
+    const int si = batch_stream(B, g);
+    const BitDesc &D = B.d[si];
+    const int t = g - B.tops_base[si];
+    const bool bad = D.out_info[FIC_INFO_ERROR] & FIC_DEVERR_FORMAT;
+    D.out_toff[t] = bad ? 0u : (uint32_t)D.first[t];
+    D.out_split[t] = 0u;
+    if (bad) return;
+    parse_tile<true>(D.b, D.words_in, D.nwords, D.tile_bits[t], D.tile_bits[t + 1], t, D.out_rec + D.first[t],
+                     D.out_split);
 }
 
 }  // namespace
@@ -356,6 +428,121 @@ size_t fic_bitstream_workspace_bytes(int width, int height, const fic_params *p)
     return 8 * ((size_t)ntop + 1) * 2;
 }
 
+// Launch the three kernels of a writer (parse = false) or reader batch.
+static int run_batch(BitBatch &B, bool parse, cudaStream_t s) {
+    B.tops_base[0] = 0;
+    for (int i = 0; i < B.count; ++i) B.tops_base[i + 1] = B.tops_base[i] + B.d[i].ntop;
+    const int tops = B.tops_base[B.count];
+    if (B.count == 0) return FIC_OK;
+    if (!parse) {
+        const int warps_per_cta = 8;
+        const int grid = (tops + warps_per_cta - 1) / warps_per_cta;
+        tile_size_kernel<<<grid, warps_per_cta * 32, 0, s>>>(B);
+        ser_scan_kernel<<<B.count, 1024, 0, s>>>(B);
+        write_kernel<<<grid, warps_per_cta * 32, 0, s>>>(B);
+    } else {
+        const int threads = 128, grid = (tops + threads - 1) / threads;
+        parse_count_kernel<<<grid, threads, 0, s>>>(B);
+        parse_scan_kernel<<<B.count, 1024, 0, s>>>(B);
+        parse_write_kernel<<<grid, threads, 0, s>>>(B);
+    }
+    return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+}
+
+// Each stream's scans at a 256-byte aligned offset; the last one needs only
+// its own size (so a batch of one needs fic_bitstream_workspace_bytes).
+size_t fic_bitstream_batch_workspace_bytes(const fic_stream *sts, int count) {
+    if (!sts || count <= 0) return 0;
+    size_t n = 0;
+    for (int i = 0; i < count; ++i) {
+        const size_t one = fic_bitstream_workspace_bytes(sts[i].width, sts[i].height, &sts[i].params);
+        if (one == 0) return 0;
+        n += i == count - 1 ? one : (one + 255) & ~(size_t)255;
+    }
+    return n;
+}
+
+int fic_serialize_batch(const fic_stream *sts, int count, int technique2, uint32_t *const *d_words,
+                        const int64_t *nwords, uint64_t *const *d_tile_bits, void *d_workspace, size_t ws_bytes,
+                        void *stream) {
+    if (!sts || count <= 0 || !d_words || !nwords || !d_tile_bits || !d_workspace) return FIC_EBADPARAM;
+    if (ws_bytes < fic_bitstream_batch_workspace_bytes(sts, count)) return FIC_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t *ws = static_cast<uint8_t *>(d_workspace);
+    BitBatch B;
+    B.count = 0;
+    for (int i = 0; i < count; ++i) {
+        const fic_stream *st = &sts[i];
+        if (!st->records || !st->tile_offsets || !d_words[i] || !d_tile_bits[i]) return FIC_EBADPARAM;
+        const int rc = fic_validate_stream(st->width, st->height, &st->params);
+        if (rc) return rc;
+        if (nwords[i] < fic_bitstream_max_words(st->width, st->height, &st->params)) return FIC_ENOMEM;
+        BitDesc &D = B.d[B.count++];
+        D.b = make_layout(st->width, st->height, st->params, technique2);
+        D.ntop = st->ntop;
+        D.rec = st->records;
+        D.toff = st->tile_offsets;
+        D.words = d_words[i];
+        D.words_in = nullptr;
+        D.nwords = nwords[i];
+        D.tile_bits = reinterpret_cast<unsigned long long *>(d_tile_bits[i]);
+        D.sizes = reinterpret_cast<unsigned long long *>(ws);
+        D.first = nullptr;
+        D.out_rec = nullptr;
+        D.out_toff = D.out_split = D.out_info = nullptr;
+        ws += (fic_bitstream_workspace_bytes(st->width, st->height, &st->params) + 255) & ~(size_t)255;
+        if (B.count == kBitBatch || i == count - 1) {
+            const int rc2 = run_batch(B, false, s);
+            if (rc2) return rc2;
+            B.count = 0;
+        }
+    }
+    return FIC_OK;
+}
+
+int fic_parse_batch(const uint32_t *const *d_words, const int64_t *nwords, const uint64_t *const *d_tile_bits,
+                    int technique2, fic_stream *outs, int count, void *d_workspace, size_t ws_bytes, void *stream) {
+    if (!outs || count <= 0 || !d_words || !nwords || !d_tile_bits || !d_workspace) return FIC_EBADPARAM;
+    if (ws_bytes < fic_bitstream_batch_workspace_bytes(outs, count)) return FIC_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t *ws = static_cast<uint8_t *>(d_workspace);
+    BitBatch B;
+    B.count = 0;
+    for (int i = 0; i < count; ++i) {
+        fic_stream *out = &outs[i];
+        if (!out->records || !out->tile_offsets || !out->split || !out->info || !d_words[i] || !d_tile_bits[i] ||
+            nwords[i] <= 0)
+            return FIC_EBADPARAM;
+        const int rc = fic_validate_stream(out->width, out->height, &out->params);
+        if (rc) return rc;
+        int32_t ntop = 0, cap = 0;
+        fic_stream_sizes(out->width, out->height, &out->params, &ntop, &cap);
+        if (out->ntop != ntop || out->capacity < cap) return FIC_ECAPACITY;
+        BitDesc &D = B.d[B.count++];
+        D.b = make_layout(out->width, out->height, out->params, technique2);
+        D.ntop = ntop;
+        D.rec = nullptr;
+        D.toff = nullptr;
+        D.words = nullptr;
+        D.words_in = d_words[i];
+        D.nwords = nwords[i];
+        D.tile_bits = const_cast<unsigned long long *>(reinterpret_cast<const unsigned long long *>(d_tile_bits[i]));
+        D.sizes = reinterpret_cast<unsigned long long *>(ws);
+        D.first = D.sizes + ntop + 1;
+        D.out_rec = out->records;
+        D.out_toff = out->tile_offsets;
+        D.out_split = out->split;
+        D.out_info = out->info;
+        ws += (fic_bitstream_workspace_bytes(out->width, out->height, &out->params) + 255) & ~(size_t)255;
+        if (B.count == kBitBatch || i == count - 1) {
+            const int rc2 = run_batch(B, true, s);
+            if (rc2) return rc2;
+            B.count = 0;
+        }
+    }
+    return FIC_OK;
+}
+
 int fic_serialize(const fic_stream *st, int technique2, uint32_t *d_words, int64_t nwords, uint64_t *d_tile_bits,
                   void *d_workspace, size_t ws_bytes, void *stream) {
     if (!st || !d_words || !d_tile_bits || !d_workspace || !st->records || !st->tile_offsets) return FIC_EBADPARAM;
@@ -364,19 +551,7 @@ int fic_serialize(const fic_stream *st, int technique2, uint32_t *d_words, int64
     if (nwords < fic_bitstream_max_words(st->width, st->height, &st->params) ||
         ws_bytes < fic_bitstream_workspace_bytes(st->width, st->height, &st->params))
         return FIC_ENOMEM;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const BitLayout b = make_layout(st->width, st->height, st->params, technique2);
-    const int ntop = st->ntop;
-    unsigned long long *sizes = static_cast<unsigned long long *>(d_workspace);
-    if (cudaMemsetAsync(d_words, 0, (size_t)nwords * 4, s) != cudaSuccess) return FIC_ECUDA;
-    const int warps_per_cta = 8;
-    const int grid = (ntop + warps_per_cta - 1) / warps_per_cta;
-    tile_size_kernel<<<grid, warps_per_cta * 32, 0, s>>>(b, st->records, st->tile_offsets, ntop, sizes);
-    scan_kernel<<<1, 1024, 0, s>>>(sizes, ntop, reinterpret_cast<unsigned long long *>(d_tile_bits));
-    write_kernel<<<grid, warps_per_cta * 32, 0, s>>>(b, st->records, st->tile_offsets, ntop,
-                                                     reinterpret_cast<const unsigned long long *>(d_tile_bits),
-                                                     d_words);
-    return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+    return fic_serialize_batch(st, 1, technique2, &d_words, &nwords, &d_tile_bits, d_workspace, ws_bytes, stream);
 }
 
 int fic_parse(const uint32_t *d_words, int64_t nwords, const uint64_t *d_tile_bits, int technique2, fic_stream *out,
@@ -390,20 +565,7 @@ int fic_parse(const uint32_t *d_words, int64_t nwords, const uint64_t *d_tile_bi
     fic_stream_sizes(out->width, out->height, &out->params, &ntop, &cap);
     if (out->ntop != ntop || out->capacity < cap) return FIC_ECAPACITY;
     if (ws_bytes < fic_bitstream_workspace_bytes(out->width, out->height, &out->params)) return FIC_ENOMEM;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const BitLayout b = make_layout(out->width, out->height, out->params, technique2);
-    unsigned long long *counts = static_cast<unsigned long long *>(d_workspace);
-    unsigned long long *first = counts + ntop + 1;
-    if (cudaMemsetAsync(out->info, 0, FIC_INFO_WORDS * 4, s) != cudaSuccess) return FIC_ECUDA;
-    const int threads = 128;
-    int grid = (ntop + threads - 1) / threads;
-    grid = grid < 1 ? 1 : grid;
-    const unsigned long long *tb = reinterpret_cast<const unsigned long long *>(d_tile_bits);
-    parse_count_kernel<<<grid, threads, 0, s>>>(b, d_words, nwords, tb, ntop, counts, out->info);
-    scan_kernel<<<1, 1024, 0, s>>>(counts, ntop, first);
-    parse_write_kernel<<<grid, threads, 0, s>>>(b, d_words, nwords, tb, ntop, first, out->records, out->tile_offsets,
-                                                out->split, out->info);
-    return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
+    return fic_parse_batch(&d_words, &nwords, &d_tile_bits, technique2, out, 1, d_workspace, ws_bytes, stream);
 }
 
 }  // extern "C"

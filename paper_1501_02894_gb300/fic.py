@@ -166,6 +166,12 @@ def lib():
         L.fic_bitstream_workspace_bytes.restype = ctypes.c_size_t
         L.fic_serialize.argtypes = [P(StreamC), ctypes.c_int, vp, ctypes.c_int64, vp, vp, ctypes.c_size_t, vp]
         L.fic_parse.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int, P(StreamC), vp, ctypes.c_size_t, vp]
+        L.fic_bitstream_batch_workspace_bytes.argtypes = [P(StreamC), ctypes.c_int]
+        L.fic_bitstream_batch_workspace_bytes.restype = ctypes.c_size_t
+        L.fic_serialize_batch.argtypes = [P(StreamC), ctypes.c_int, ctypes.c_int, P(vp), P(ctypes.c_int64), P(vp), vp,
+                                          ctypes.c_size_t, vp]
+        L.fic_parse_batch.argtypes = [P(vp), P(ctypes.c_int64), P(vp), ctypes.c_int, P(StreamC), ctypes.c_int, vp,
+                                      ctypes.c_size_t, vp]
         L.fic_strerror.argtypes = [ctypes.c_int]
         L.fic_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -481,6 +487,53 @@ def parse(words: torch.Tensor, index: torch.Tensor, width: int, height: int, p: 
     _check(L.fic_parse(_ptr(words), words.numel(), _ptr(index), 1 if technique2 else 0, ctypes.byref(st.c), _ptr(ws),
                        ws_n, _stream_handle(stream)), "fic_parse")
     return st
+
+
+def serialize_batch(sts, technique2: bool = True, stream=None):
+    """Bitstreams of several streams in one batched call: [(words, index)]
+    as serialize() gives them, stream by stream."""
+    L = lib()
+    n = len(sts)
+    if n == 0:
+        raise FicError(-2, "serialize_batch: no streams")
+    dev = sts[0].records.device
+    outs, wp, ip, nws = [], [], [], []
+    for st in sts:
+        nw = int(L.fic_bitstream_max_words(st.width, st.height, ctypes.byref(st.params)))
+        words = torch.empty(nw, dtype=torch.int32, device=dev)
+        index = torch.empty(st.ntop + 1, dtype=torch.int64, device=dev)
+        outs.append((words, index))
+        wp.append(words.data_ptr())
+        ip.append(index.data_ptr())
+        nws.append(nw)
+    Sa = (StreamC * n)(*[st.c for st in sts])
+    ws_n = int(L.fic_bitstream_batch_workspace_bytes(Sa, n))
+    ws = torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
+    _check(L.fic_serialize_batch(Sa, n, 1 if technique2 else 0, (ctypes.c_void_p * n)(*wp), (ctypes.c_int64 * n)(*nws),
+                                 (ctypes.c_void_p * n)(*ip), _ptr(ws), ws_n, _stream_handle(stream)),
+           "fic_serialize_batch")
+    return outs
+
+
+def parse_batch(items, technique2: bool = True, stream=None):
+    """Read several bitstreams back in one batched call.  `items`: (words,
+    index, width, height, params) per stream; returns new Streams."""
+    L = lib()
+    n = len(items)
+    if n == 0:
+        raise FicError(-2, "parse_batch: no streams")
+    dev = items[0][0].device
+    outs = [Stream(W, H, p, dev) for (_, _, W, H, p) in items]
+    Sa = (StreamC * n)(*[o.c for o in outs])
+    ws_n = int(L.fic_bitstream_batch_workspace_bytes(Sa, n))
+    ws = torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
+    _check(L.fic_parse_batch((ctypes.c_void_p * n)(*[w.data_ptr() for (w, _, _, _, _) in items]),
+                             (ctypes.c_int64 * n)(*[w.numel() for (w, _, _, _, _) in items]),
+                             (ctypes.c_void_p * n)(*[ix.data_ptr() for (_, ix, _, _, _) in items]),
+                             1 if technique2 else 0, Sa, n, _ptr(ws), ws_n, _stream_handle(stream)), "fic_parse_batch")
+    for o, c in zip(outs, Sa):
+        o.c = c  # the call filled the C structs
+    return outs
 
 
 def rescale(st: Stream, shift: int, stream=None) -> Stream:

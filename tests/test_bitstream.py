@@ -137,3 +137,31 @@ def test_device_parse_rejects_malformed(fic, orc):
     with pytest.raises(fic.FicError) as e:
         back.info_host()
     assert e.value.code == -2
+
+
+@pytest.mark.gpu
+def test_device_batch_equals_per_stream_and_oracle(fic, orc):
+    """Every case's stream written and read back in one batched call (the
+    case list mixes modes, quadtrees, codebooks and sizes): words, index and
+    records equal the oracle's, and the per-stream calls' results."""
+    import torch
+    sts, want = [], []
+    for (mode, bmax, bmin, thr, N, kw) in CASES:
+        img = synth.gaussian_scene(N, 5)
+        op = orc.make_params(mode, bmax, bmin, thr, **kw)
+        leaves, split, _ = orc.encode(img, op)
+        want.append((leaves, split, orc.serialize(leaves, N, N, op, True)))
+        sts.append(fic.fic_encode(torch.from_numpy(img).cuda(), fic.params(mode, bmax, bmin, thr, **kw)))
+    got = fic.serialize_batch(sts, True)
+    back = fic.parse_batch([(w, ix, st.width, st.height, st.params) for (w, ix), st in zip(got, sts)], True)
+    torch.cuda.synchronize()
+    for (words, index), st, b, (leaves, split, (ww, wi, nbits)) in zip(got, sts, back, want):
+        assert np.array_equal(index.cpu().numpy().view(np.uint64), wi)
+        w = words.cpu().numpy().view(np.uint32)
+        nw = (nbits + 31) // 32
+        assert np.array_equal(w[:nw], ww) and not w[nw:].any()
+        one_w, one_ix = fic.serialize(st, True)
+        assert torch.equal(one_w, words) and torch.equal(one_ix, index)
+        h = b.to_host()
+        assert np.array_equal(h["records"].view(np.uint8), leaves.view(np.uint8))
+        assert np.array_equal(h["split"], split)
