@@ -365,18 +365,45 @@ __device__ int parse_tile(const BitLayout &b, const uint32_t *words, long long n
     return count;
 }
 
-__global__ void parse_count_kernel(const __grid_constant__ BitBatch B) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+// The reader's passes parse a block bit by bit, one dependent load per
+// field: the warp that owns a block first copies the block's words into
+// shared memory (coalesced), and its lane 0 parses from there.
+constexpr int kParseWarps = 4;
+constexpr int kBlockWords = 320;  // words staged per block (larger blocks read global memory)
+
+// Stage the words holding bits [beg, end) of a block; returns the first
+// staged word, or -1 when the block does not fit the buffer.
+__device__ __forceinline__ long long stage_block_words(const BitDesc &D, unsigned long long beg, unsigned long long end,
+                                                       uint32_t *sw, int lane, int &nstaged) {
+    const long long w0 = (long long)(beg >> 5);
+    const long long w1 = min(D.nwords, (long long)((end + 63) >> 5));  // + the word a field may reach into
+    nstaged = (int)(w1 - w0);
+    if (nstaged > kBlockWords || nstaged < 0) return -1;
+    for (int i = lane; i < nstaged; i += 32) sw[i] = D.words_in[w0 + i];
+    __syncwarp();
+    return w0;
+}
+
+__global__ void __launch_bounds__(kParseWarps * 32) parse_count_kernel(const __grid_constant__ BitBatch B) {
+    __shared__ uint32_t s_words[kParseWarps][kBlockWords];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = blockIdx.x * kParseWarps + warp;
     if (g >= B.tops_base[B.count]) return;
     const int si = batch_stream(B, g);
     const BitDesc &D = B.d[si];
     const int t = g - B.tops_base[si];
     const unsigned long long beg = D.tile_bits[t], end = D.tile_bits[t + 1];
     int n = -1;
-    if (end >= beg && end <= (unsigned long long)D.nwords * 32ull)
-        n = parse_tile<false>(D.b, D.words_in, D.nwords, beg, end, t, nullptr, nullptr);
+    if (end >= beg && end <= (unsigned long long)D.nwords * 32ull) {
+        int nst = 0;
+        const long long w0 = stage_block_words(D, beg, end, s_words[warp], lane, nst);
+        if (lane == 0)
+            n = w0 >= 0 ? parse_tile<false>(D.b, s_words[warp], nst, beg - 32ull * (unsigned long long)w0,
+                                             end - 32ull * (unsigned long long)w0, t, nullptr, nullptr)
+                        : parse_tile<false>(D.b, D.words_in, D.nwords, beg, end, t, nullptr, nullptr);
+    }
     // a block that does not parse is marked by the top bit (the scan finds it)
-    D.sizes[t] = n < 0 ? (1ull << 63) : (unsigned long long)n;
+    if (lane == 0) D.sizes[t] = n < 0 ? (1ull << 63) : (unsigned long long)n;
 }
 
 // One CTA per stream: tile offsets of the records, the info block.
@@ -394,18 +421,29 @@ __global__ void __launch_bounds__(1024) parse_scan_kernel(const __grid_constant_
     }
 }
 
-__global__ void parse_write_kernel(const __grid_constant__ BitBatch B) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kParseWarps * 32) parse_write_kernel(const __grid_constant__ BitBatch B) {
+    __shared__ uint32_t s_words[kParseWarps][kBlockWords];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = blockIdx.x * kParseWarps + warp;
     if (g >= B.tops_base[B.count]) return;
     const int si = batch_stream(B, g);
     const BitDesc &D = B.d[si];
     const int t = g - B.tops_base[si];
     const bool bad = D.out_info[FIC_INFO_ERROR] & FIC_DEVERR_FORMAT;
-    D.out_toff[t] = bad ? 0u : (uint32_t)D.first[t];
-    D.out_split[t] = 0u;
+    if (lane == 0) {
+        D.out_toff[t] = bad ? 0u : (uint32_t)D.first[t];
+        D.out_split[t] = 0u;
+    }
     if (bad) return;
-    parse_tile<true>(D.b, D.words_in, D.nwords, D.tile_bits[t], D.tile_bits[t + 1], t, D.out_rec + D.first[t],
-                     D.out_split);
+    const unsigned long long beg = D.tile_bits[t], end = D.tile_bits[t + 1];
+    int nst = 0;
+    const long long w0 = stage_block_words(D, beg, end, s_words[warp], lane, nst);
+    if (lane != 0) return;
+    if (w0 >= 0)
+        parse_tile<true>(D.b, s_words[warp], nst, beg - 32ull * (unsigned long long)w0,
+                         end - 32ull * (unsigned long long)w0, t, D.out_rec + D.first[t], D.out_split);
+    else
+        parse_tile<true>(D.b, D.words_in, D.nwords, beg, end, t, D.out_rec + D.first[t], D.out_split);
 }
 
 }  // namespace
@@ -441,10 +479,10 @@ static int run_batch(BitBatch &B, bool parse, cudaStream_t s) {
         ser_scan_kernel<<<B.count, 1024, 0, s>>>(B);
         write_kernel<<<grid, warps_per_cta * 32, 0, s>>>(B);
     } else {
-        const int threads = 128, grid = (tops + threads - 1) / threads;
-        parse_count_kernel<<<grid, threads, 0, s>>>(B);
+        const int grid = (tops + kParseWarps - 1) / kParseWarps;
+        parse_count_kernel<<<grid, kParseWarps * 32, 0, s>>>(B);
         parse_scan_kernel<<<B.count, 1024, 0, s>>>(B);
-        parse_write_kernel<<<grid, threads, 0, s>>>(B);
+        parse_write_kernel<<<grid, kParseWarps * 32, 0, s>>>(B);
     }
     return cudaGetLastError() == cudaSuccess ? FIC_OK : FIC_ECUDA;
 }

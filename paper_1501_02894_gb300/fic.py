@@ -489,44 +489,52 @@ def parse(words: torch.Tensor, index: torch.Tensor, width: int, height: int, p: 
     return st
 
 
-def serialize_batch(sts, technique2: bool = True, stream=None):
+def serialize_batch(sts, technique2: bool = True, stream=None, outs=None, workspace=None):
     """Bitstreams of several streams in one batched call: [(words, index)]
-    as serialize() gives them, stream by stream."""
+    as serialize() gives them, stream by stream.  `outs` (a previous
+    result) and `workspace` may be passed to reuse their buffers."""
     L = lib()
     n = len(sts)
     if n == 0:
         raise FicError(-2, "serialize_batch: no streams")
     dev = sts[0].records.device
-    outs, wp, ip, nws = [], [], [], []
-    for st in sts:
-        nw = int(L.fic_bitstream_max_words(st.width, st.height, ctypes.byref(st.params)))
-        words = torch.empty(nw, dtype=torch.int32, device=dev)
-        index = torch.empty(st.ntop + 1, dtype=torch.int64, device=dev)
-        outs.append((words, index))
-        wp.append(words.data_ptr())
-        ip.append(index.data_ptr())
-        nws.append(nw)
+    if outs is None:
+        outs = []
+        for st in sts:
+            nw = int(L.fic_bitstream_max_words(st.width, st.height, ctypes.byref(st.params)))
+            outs.append((torch.empty(nw, dtype=torch.int32, device=dev),
+                         torch.empty(st.ntop + 1, dtype=torch.int64, device=dev)))
+    wp = [w.data_ptr() for w, _ in outs]
+    ip = [ix.data_ptr() for _, ix in outs]
+    nws = [w.numel() for w, _ in outs]
     Sa = (StreamC * n)(*[st.c for st in sts])
     ws_n = int(L.fic_bitstream_batch_workspace_bytes(Sa, n))
-    ws = torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
+    ws = workspace if workspace is not None else torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
+    if ws.numel() < ws_n:
+        raise FicError(-3, "serialize_batch: workspace too small")
     _check(L.fic_serialize_batch(Sa, n, 1 if technique2 else 0, (ctypes.c_void_p * n)(*wp), (ctypes.c_int64 * n)(*nws),
                                  (ctypes.c_void_p * n)(*ip), _ptr(ws), ws_n, _stream_handle(stream)),
            "fic_serialize_batch")
     return outs
 
 
-def parse_batch(items, technique2: bool = True, stream=None):
+def parse_batch(items, technique2: bool = True, stream=None, outs=None, workspace=None):
     """Read several bitstreams back in one batched call.  `items`: (words,
-    index, width, height, params) per stream; returns new Streams."""
+    index, width, height, params) per stream; returns Streams (new ones, or
+    the given `outs`, whose geometry must match).  `workspace` may be
+    passed to reuse it."""
     L = lib()
     n = len(items)
     if n == 0:
         raise FicError(-2, "parse_batch: no streams")
     dev = items[0][0].device
-    outs = [Stream(W, H, p, dev) for (_, _, W, H, p) in items]
+    if outs is None:
+        outs = [Stream(W, H, p, dev) for (_, _, W, H, p) in items]
     Sa = (StreamC * n)(*[o.c for o in outs])
     ws_n = int(L.fic_bitstream_batch_workspace_bytes(Sa, n))
-    ws = torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
+    ws = workspace if workspace is not None else torch.empty(max(ws_n, 1), dtype=torch.uint8, device=dev)
+    if ws.numel() < ws_n:
+        raise FicError(-3, "parse_batch: workspace too small")
     _check(L.fic_parse_batch((ctypes.c_void_p * n)(*[w.data_ptr() for (w, _, _, _, _) in items]),
                              (ctypes.c_int64 * n)(*[w.numel() for (w, _, _, _, _) in items]),
                              (ctypes.c_void_p * n)(*[ix.data_ptr() for (_, ix, _, _, _) in items]),
