@@ -365,9 +365,115 @@ __device__ int parse_tile(const BitLayout &b, const uint32_t *words, long long n
     return count;
 }
 
-// The reader's passes parse a block bit by bit, one dependent load per
-// field: the warp that owns a block first copies the block's words into
-// shared memory (coalesced), and its lane 0 parses from there.
+// The leaf boundaries of a block follow from the leaves' headers alone (the
+// level id, when stored, and the phase bit fix a leaf's size), so the reader
+// splits parsing in two: lane 0 walks the headers -- the only serial part --
+// recording where each leaf's fields start, and then every lane decodes
+// leaves of its own.  A block has at most 64 leaves ((bmax / bmin)^2).
+struct LeafPos {
+    uint32_t pos;   // first bit of the leaf's fields after its header (relative to the staged words)
+    uint16_t c;     // its first bmin cell (Morton index inside the top-level block)
+    uint8_t level, phase;
+};
+constexpr int kTileLeaves = 64;
+
+// Walk the headers of a block; returns its leaf count, or -1 for a block that
+// does not tile (or, with `out`, holds more than `cap` leaves).
+__device__ int walk_tile(const BitLayout &b, const uint32_t *words, long long nwords, unsigned long long pos,
+                         unsigned long long end, LeafPos *out, int cap) {
+    const int cells = b.bmax / b.bmin;
+    int c = 0, count = 0;
+    while (c < cells * cells) {
+        int level;
+        if (b.technique2 && b.L > 1 && (c & 3) != 0) {
+            level = b.L;
+        } else {
+            level = (int)get_bits(words, pos, b.lbits, nwords) + 1;
+            pos += (unsigned)b.lbits;
+        }
+        if (level > b.L) return -1;
+        const int B = b.bmax >> (level - 1);
+        const int span = (B / b.bmin) * (B / b.bmin);
+        if (c % span) return -1;
+        int phase = 1;
+        if (b.phase_bit && level < b.L) {
+            phase = get_bits(words, pos, 1, nwords) ? 2 : 1;
+            pos += 1;
+        }
+        if (out) {
+            if (count >= cap) return -1;
+            out[count].pos = (uint32_t)pos;
+            out[count].c = (uint16_t)c;
+            out[count].level = (uint8_t)level;
+            out[count].phase = (uint8_t)phase;
+        }
+        if (phase == 1) {
+            pos += (unsigned)(b.s_bits + b.o_bits);
+            if (b.mode == FIC_LOCAL) {
+                if ((int)get_bits(words, pos, b.local_bits, nwords) >= b.per * b.per) return -1;
+                pos += (unsigned)b.local_bits;
+            } else if (b.mode == FIC_EXHAUSTIVE) {
+                pos += (unsigned)(b.dom_bits + b.iso_bits);
+            }
+        } else {
+            pos += (unsigned)(b.o_bits + 3 * (level == 1 ? 5 : 6) + 4);
+        }
+        if (pos > end) return -1;
+        ++count;
+        c += span;
+    }
+    return pos == end ? count : -1;
+}
+
+// The record of one walked leaf of top-level block t.
+__device__ uint4 decode_leaf(const BitLayout &b, const uint32_t *words, long long nwords, const LeafPos &lp, int t) {
+    const int tw = b.W / b.bmax;
+    const int tx = (t % tw) * b.bmax, ty = (t / tw) * b.bmax;
+    const int c = lp.c, level = lp.level, phase = lp.phase;
+    int cx = 0, cy = 0;
+    for (int k = 0; k < 3; ++k) {
+        cx |= ((c >> (2 * k)) & 1) << k;
+        cy |= ((c >> (2 * k + 1)) & 1) << k;
+    }
+    const int B = b.bmax >> (level - 1);
+    const int x = tx + cx * b.bmin, y = ty + cy * b.bmin;
+    unsigned long long pos = lp.pos;
+    uint32_t k = 0, q = 0, dz = 0, iso = 0;
+    int dx = centred_origin(x, B, b.W), dy = centred_origin(y, B, b.H);
+    if (phase == 1) {
+        k = get_bits(words, pos, b.s_bits, nwords);
+        pos += (unsigned)b.s_bits;
+        q = get_bits(words, pos, b.o_bits, nwords);
+        pos += (unsigned)b.o_bits;
+        if (b.mode == FIC_LOCAL) {
+            const int idx = (int)get_bits(words, pos, b.local_bits, nwords);
+            dx += (idx % b.per - b.rstep) * b.step;
+            dy += (idx / b.per - b.rstep) * b.step;
+        } else if (b.mode == FIC_EXHAUSTIVE) {
+            const int idx = (int)get_bits(words, pos, b.dom_bits, nwords);
+            pos += (unsigned)b.dom_bits;
+            dx = (idx % b.ndx) * b.step;
+            dy = (idx / b.ndx) * b.step;
+            iso = get_bits(words, pos, b.iso_bits, nwords);
+        }
+    } else {
+        const int M = level == 1 ? 5 : 6;
+        q = get_bits(words, pos, b.o_bits, nwords);
+        pos += (unsigned)b.o_bits;
+        for (int i = 0; i < 3; ++i) {
+            int d = (int)get_bits(words, pos, M, nwords);
+            pos += (unsigned)M;
+            if (d >= (1 << (M - 1))) d -= 1 << M;
+            dz |= ((uint32_t)d & 0xffu) << (8 * i);
+        }
+        k = get_bits(words, pos, 4, nwords);
+    }
+    return make_uint4((uint32_t)x | ((uint32_t)y << 16), (uint32_t)level | ((uint32_t)phase << 8) | (k << 16) | (q << 24),
+                      dz | (iso << 24), (uint32_t)dx | ((uint32_t)dy << 16));
+}
+
+// The reader's passes read a block bit by bit: the warp that owns a block
+// first copies the block's words into shared memory (coalesced).
 constexpr int kParseWarps = 4;
 constexpr int kBlockWords = 320;  // words staged per block (larger blocks read global memory)
 
@@ -398,8 +504,8 @@ __global__ void __launch_bounds__(kParseWarps * 32) parse_count_kernel(const __g
         int nst = 0;
         const long long w0 = stage_block_words(D, beg, end, s_words[warp], lane, nst);
         if (lane == 0)
-            n = w0 >= 0 ? parse_tile<false>(D.b, s_words[warp], nst, beg - 32ull * (unsigned long long)w0,
-                                             end - 32ull * (unsigned long long)w0, t, nullptr, nullptr)
+            n = w0 >= 0 ? walk_tile(D.b, s_words[warp], nst, beg - 32ull * (unsigned long long)w0,
+                                    end - 32ull * (unsigned long long)w0, nullptr, 0)
                         : parse_tile<false>(D.b, D.words_in, D.nwords, beg, end, t, nullptr, nullptr);
     }
     // a block that does not parse is marked by the top bit (the scan finds it)
@@ -438,12 +544,28 @@ __global__ void __launch_bounds__(kParseWarps * 32) parse_write_kernel(const __g
     const unsigned long long beg = D.tile_bits[t], end = D.tile_bits[t + 1];
     int nst = 0;
     const long long w0 = stage_block_words(D, beg, end, s_words[warp], lane, nst);
-    if (lane != 0) return;
-    if (w0 >= 0)
-        parse_tile<true>(D.b, s_words[warp], nst, beg - 32ull * (unsigned long long)w0,
-                         end - 32ull * (unsigned long long)w0, t, D.out_rec + D.first[t], D.out_split);
-    else
-        parse_tile<true>(D.b, D.words_in, D.nwords, beg, end, t, D.out_rec + D.first[t], D.out_split);
+    if (w0 < 0) {
+        if (lane == 0) parse_tile<true>(D.b, D.words_in, D.nwords, beg, end, t, D.out_rec + D.first[t], D.out_split);
+        return;
+    }
+    // lane 0 walks the headers, then the lanes decode the leaves
+    __shared__ LeafPos s_leaf[kParseWarps][kTileLeaves];
+    int n = 0;
+    if (lane == 0)
+        n = walk_tile(D.b, s_words[warp], nst, beg - 32ull * (unsigned long long)w0,
+                      end - 32ull * (unsigned long long)w0, s_leaf[warp], kTileLeaves);
+    n = __shfl_sync(0xffffffffu, n, 0);  // the count pass found the same blocks well formed
+    __syncwarp();
+    uint32_t mask = 0;
+    fic_record *out = D.out_rec + D.first[t];
+    for (int i = lane; i < n; i += 32) {
+        const LeafPos lp = s_leaf[warp][i];
+        *reinterpret_cast<uint4 *>(out + i) = decode_leaf(D.b, s_words[warp], nst, lp, t);
+        for (int a = 1; a < lp.level; ++a)
+            mask |= 1u << (((1u << (2 * (a - 1))) - 1) / 3 + (uint32_t)(lp.c >> (2 * (D.b.L - a))));
+    }
+    mask = __reduce_or_sync(0xffffffffu, mask);
+    if (lane == 0) D.out_split[t] = mask;
 }
 
 }  // namespace
