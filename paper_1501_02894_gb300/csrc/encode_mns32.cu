@@ -146,10 +146,12 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 5)
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_base[kImgTable];
     __shared__ __align__(8) uint64_t s_bar[NW];
+    __shared__ int s_take;  // dynamic schedule: the CTA's strips handed out so far
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned FULL = 0xffffffffu;
     uint8_t *const smem_a = smem + ((128u - (smem_u32(smem) & 127u)) & 127u);
     uint8_t *const raw = smem_a + warp * kPerWarp;
+    if (threadIdx.x == 0) s_take = 0;
     uint32_t *const d4e = reinterpret_cast<uint32_t *>(raw + kRawBytes);
     uint64_t *const bar = &s_bar[warp];
     const int pr = lane >> 2, pc = lane & 3;
@@ -175,26 +177,33 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 5)
             tma_load_2d(raw, descs[t.img].map, t.rx0, t.ry0, bar);
         }
     };
+    // Schedule.  Static: warp w takes strips w, w + gstep, ...  With `dyn`
+    // the CTA owns strips blockIdx.x, blockIdx.x + gridDim.x, ... (spread
+    // over the batch) and its warps take them one by one from a shared-memory
+    // counter, one strip ahead: a warp whose strips were accepted at level 1
+    // takes more of them, and the CTA's warps finish together.  (A global
+    // ticket counter was slower: thousands of warps contend for one word.)
     const int gstep = gridDim.x * NW;
-    int g0, g1;
+    int g0, g_next, tk = 0;  // tk (lane 0): the CTA-local index of the strip after the next one
     if (dyn) {
-        int a = 0, b = 0;
         if (lane == 0) {
-            a = (int)atomicAdd(ticket, 1u);
-            b = (int)atomicAdd(ticket, 1u);
+            g0 = blockIdx.x + gridDim.x * atomicAdd(&s_take, 1);
+            tk = atomicAdd(&s_take, 1);
         }
-        g0 = __shfl_sync(FULL, a, 0);
-        g1 = __shfl_sync(FULL, b, 0);
+        g0 = __shfl_sync(FULL, g0, 0);
     } else {
         g0 = blockIdx.x * NW + warp;
-        g1 = g0 + gstep;
     }
+    g_next = g0 + gstep;
     Strip32 cur = strip32_of(s_base, descs, count, g0, total_strips);
     issue(cur);
-    int g_next = g1;
     uint32_t phase = 0;
 
     while (cur.g < total_strips) {
+        if (dyn) {
+            g_next = blockIdx.x + gridDim.x * __shfl_sync(FULL, tk, 0);
+            if (lane == 0) tk = atomicAdd(&s_take, 1);
+        }
         const EncDesc &D = descs[cur.img];
         const int W = D.W, H = D.H;
         const int sx0 = cur.sx0, sy0 = cur.sy0, rx0 = cur.rx0, ry0 = cur.ry0;
@@ -208,12 +217,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : 5)
         const int ox = sx0 - rx0, oy = sy0 - ry0;  // range block inside the window
         // the strip after this one: its window is fetched once this one's is consumed
         const Strip32 nxt = strip32_of(s_base, descs, count, g_next, total_strips);
-        int g_after = g_next + gstep;
-        if (dyn) {
-            int a = 0;
-            if (lane == 0) a = (int)atomicAdd(ticket, 1u);
-            g_after = __shfl_sync(FULL, a, 0);
-        }
+        const int g_after = g_next + gstep;  // static schedule
 
         const bool arrived = mbar_wait(bar, phase, kMbarLimit);
         phase ^= 1u;
