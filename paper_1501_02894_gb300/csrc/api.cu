@@ -189,10 +189,11 @@ struct fic_plan {
     int max_recs = 0;     // decode: the largest record capacity of the batch
 };
 
-// Exhaustive search: per image, decimated domains (packed and fp16), domain
-// and range statistics, permuted range rows and per-row results.
+// Exhaustive search: per image, decimated domains (packed) and the tensor
+// path's screen operand, domain and range statistics, permuted range rows
+// (fp16 and bytes) and per-row results.
 struct ExhLayout {
-    size_t dpairs, dfp16, dstat, dscr, afp16, rstat, row_g, row_dk, total;
+    size_t dpairs, dsc, dstat, dscr, afp16, rbytes, rstat, row_g, row_dk, total;
 };
 
 static ExhLayout exh_layout(int W, int H, const fic_params *p, int *nd_out, int *nd_pad_out, int *ndx_out,
@@ -202,11 +203,12 @@ static ExhLayout exh_layout(int W, int H, const fic_params *p, int *nd_out, int 
     const size_t nr = (size_t)(W / kExhB) * (H / kExhB);
     ExhLayout L;
     L.dpairs = 0;
-    L.dfp16 = L.dpairs + align_up((size_t)nd * 128);
-    L.dstat = L.dfp16 + align_up((size_t)nd_pad * 128);
+    L.dsc = L.dpairs + align_up((size_t)nd * 128);
+    L.dstat = L.dsc + align_up((size_t)nd_pad * 128);
     L.dscr = L.dstat + align_up((size_t)nd_pad * 16);
     L.afp16 = L.dscr + align_up((size_t)nd_pad * 16);
-    L.rstat = L.afp16 + align_up(nr * 8 * 128);
+    L.rbytes = L.afp16 + align_up(nr * 8 * 128);
+    L.rstat = L.rbytes + align_up(nr * 8 * 64);
     L.row_g = L.rstat + align_up(nr * 16);
     L.row_dk = L.row_g + align_up(nr * 8 * 8 * kExhMaxSeg);
     L.total = L.row_dk + align_up(nr * 8 * 8 * kExhMaxSeg);
@@ -265,11 +267,12 @@ static int exh_plan_create(const uint8_t *const *d_imgs, const int *widths, cons
         E.s_bits = p->s_bits;
         E.o_bits = p->o_bits;
         E.dpairs = reinterpret_cast<uint32_t *>(w + off + L.dpairs);
-        E.dfp16 = reinterpret_cast<__half *>(w + off + L.dfp16);
+        E.dsc = reinterpret_cast<__half *>(w + off + L.dsc);
         E.dstat = reinterpret_cast<int4 *>(w + off + L.dstat);
         E.dscr = reinterpret_cast<float4 *>(w + off + L.dscr);
         E.nseg = 1;
         E.afp16 = reinterpret_cast<__half *>(w + off + L.afp16);
+        E.rbytes = w + off + L.rbytes;
         E.rstat = reinterpret_cast<int4 *>(w + off + L.rstat);
         E.row_g = reinterpret_cast<long long *>(w + off + L.row_g);
         E.row_dk = reinterpret_cast<int2 *>(w + off + L.row_dk);

@@ -5,44 +5,74 @@
 //
 // Sum r*d4 of all (range, isometry) x domain pairs is a dense contraction
 // over the 64 decimated values of a block, so it is computed either on the
-// tensor cores (exhaustive_tc.cu: tcgen05, fp16 operands, fp32 accumulators,
-// exact because every partial sum is an integer below 2^24) or here on the
-// CUDA cores (dp2a on packed operands).  Both feed the same screening
-// epilogue: a float lower bound of each candidate's best contrast error
-// skips it unless it may beat the row's best, which is then settled in exact
-// int64 arithmetic.  The isometry is applied on the range side: row
+// CUDA cores here (dp2a on packed operands), or replaced on the tensor cores
+// (exhaustive_tc.cu: tcgen05, fp16 operands, fp32 accumulators) by a
+// contraction that yields each candidate's screen value directly.  Either
+// way a float bound of each candidate's best contrast error skips it unless
+// it may beat the row's best, which is then settled in exact int64
+// arithmetic.  The isometry is applied on the range side: row
 // (range, t) holds the range pixel r(u, v) at the position of the domain
 // element it meets under isometry t.
 #include "exhaustive.cuh"
 
 namespace fic {
 
-// Decimated domains: packed pairs for dp2a, fp16 K-major rows for the tensor
-// cores, and per-domain statistics (Sd, nCdd, 512 / nCdd).
-__global__ void exh_prep_domains(ExhDesc E) {
-    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < E.nd_pad; d += gridDim.x * blockDim.x) {
-        if (d >= E.nd) {
-            for (int i = 0; i < kExhK; ++i) E.dfp16[(size_t)d * kExhK + i] = __ushort_as_half(0);
+// Decimated domains: packed pairs for dp2a, per-domain statistics (Sd,
+// nCdd, 512 / nCdd), the CUDA-core engine's screening constants, and the
+// tensor path's screen operand: x_k = 64 d4_k - Sd (sum x_k = 0, sum x_k^2 =
+// 64 nCdd) scaled by 1024 / sqrt(nCdd), so that sum_k r_k w_k = 1024 nCdr /
+// sqrt(nCdd) = 2 sqrt(L) in magnitude (L: exhaustive.cuh); |w_k| <= 8192.
+// Eight threads per domain, one per row of its 8 x 8 decimated block; the
+// grid covers nd_pad domains exactly.
+__global__ void __launch_bounds__(256) exh_prep_domains(ExhDesc E) {
+    const unsigned FULL = 0xffffffffu;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = gt >> 3, v = gt & 7;
+    const bool real = d < E.nd;
+    int vals[kExhB];
+    int sd = 0, sdd = 0;  // sum d4^2 <= 64 * 1020^2 < 2^31
+    if (real) {
+        const int dy = (d / E.ndx) * E.step, dx = (d % E.ndx) * E.step;
+        const uint8_t *p = E.img + (size_t)(dy + 2 * v) * E.W + dx;
+#pragma unroll
+        for (int u = 0; u < kExhB; ++u) {
+            vals[u] = (int)p[2 * u] + p[2 * u + 1] + p[E.W + 2 * u] + p[E.W + 2 * u + 1];
+            sd += vals[u];
+            sdd += vals[u] * vals[u];
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < kExhB; ++u) vals[u] = 0;
+    }
+#pragma unroll
+    for (int m = 1; m < 8; m <<= 1) {
+        sd += __shfl_xor_sync(FULL, sd, m);
+        sdd += __shfl_xor_sync(FULL, sdd, m);
+    }
+    if (d >= E.nd_pad) return;
+    uint4 *wrow = reinterpret_cast<uint4 *>(E.dsc + (size_t)d * kExhK + v * kExhB);
+    if (!real) {
+        *wrow = make_uint4(0u, 0u, 0u, 0u);
+        if (v == 0) {
             E.dstat[d] = make_int4(0, 0, 0, 0);
             E.dscr[d] = make_float4(0.f, __int_as_float(0x7fc00000), __int_as_float(0x7fc00000), 0.f);  // NaN
-            continue;
         }
-        const int dy = (d / E.ndx) * E.step, dx = (d % E.ndx) * E.step;
-        int sd = 0;
-        long long sdd = 0;
-        for (int v = 0; v < kExhB; ++v) {
-            const uint8_t *p = E.img + (size_t)(dy + 2 * v) * E.W + dx;
-            int vals[kExhB];
-            for (int u = 0; u < kExhB; ++u) {
-                vals[u] = (int)p[2 * u] + p[2 * u + 1] + p[E.W + 2 * u] + p[E.W + 2 * u + 1];
-                sd += vals[u];
-                sdd += (long long)vals[u] * vals[u];
-                E.dfp16[(size_t)d * kExhK + v * kExhB + u] = __int2half_rn(vals[u]);
-            }
-            for (int u = 0; u < kExhB; u += 2)
-                E.dpairs[(size_t)d * 32 + (v * kExhB + u) / 2] = (uint32_t)vals[u] | ((uint32_t)vals[u + 1] << 16);
-        }
-        const long long ncdd = 64LL * sdd - (long long)sd * sd;  // <= 4.3e9: fits an unsigned word
+        return;
+    }
+    *reinterpret_cast<uint4 *>(E.dpairs + (size_t)d * 32 + v * 4) =
+        make_uint4((uint32_t)vals[0] | ((uint32_t)vals[1] << 16), (uint32_t)vals[2] | ((uint32_t)vals[3] << 16),
+                   (uint32_t)vals[4] | ((uint32_t)vals[5] << 16), (uint32_t)vals[6] | ((uint32_t)vals[7] << 16));
+    const long long ncdd = 64LL * sdd - (long long)sd * sd;  // <= 4.3e9: fits an unsigned word
+    const float s = ncdd > 0 ? 1024.f / sqrtf((float)ncdd) : 0.f;
+    uint32_t hw[4];
+#pragma unroll
+    for (int u = 0; u < kExhB; u += 2) {
+        const uint32_t lo = __half_as_ushort(__float2half_rn((float)(64 * vals[u] - sd) * s));
+        const uint32_t hi = __half_as_ushort(__float2half_rn((float)(64 * vals[u + 1] - sd) * s));
+        hw[u / 2] = lo | (hi << 16);
+    }
+    *wrow = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    if (v == 0) {
         const float k512 = ncdd > 0 ? 512.f / (float)ncdd : 0.f;
         E.dstat[d] = make_int4(sd, (int)(uint32_t)ncdd, __float_as_int(k512), 1);
         const float sw = ncdd > 0 ? sqrtf(262144.f / (float)ncdd) : 0.f;
@@ -51,24 +81,52 @@ __global__ void exh_prep_domains(ExhDesc E) {
 }
 
 // Range rows, one per (range, isometry): A[sv * 8 + su] = r(u, v) where
-// (su, sv) is the domain element that isometry t puts at (u, v).
-__global__ void exh_prep_ranges(ExhDesc E) {
-    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < E.nr * 8; row += gridDim.x * blockDim.x) {
-        const int r = row >> 3, t = row & 7;
+// (su, sv) is the domain element that isometry t puts at (u, v), as bytes,
+// and the tensor path's screen operand: the same row with the range's mean
+// removed, r - Sr / 64, in fp16.  Eight threads per row, one per row sv of
+// A: its element su holds the pixel at the inverse isometry's image of
+// (su, sv) (the quarter turns 1 and 3 are each other's inverse, the other
+// six are involutions).  The grid covers the nr * 8 rows exactly.
+__global__ void __launch_bounds__(256) exh_prep_ranges(ExhDesc E) {
+    const unsigned FULL = 0xffffffffu;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = gt >> 3, sv = gt & 7;
+    const bool real = row < E.nr * 8;
+    const int r = row >> 3, t = row & 7;
+    int sr = 0, srr = 0;
+    int px[kExhB];
+    if (real) {
         const int x = (r % E.nrx) * kExhB, y = (r / E.nrx) * kExhB;
-        int sr = 0, srr = 0;
-        for (int v = 0; v < kExhB; ++v) {
-            for (int u = 0; u < kExhB; ++u) {
-                const int px = E.img[(size_t)(y + v) * E.W + x + u];
-                int su, sv;
-                exh_iso_src(t, kExhB, u, v, su, sv);
-                E.afp16[(size_t)row * kExhK + sv * kExhB + su] = __int2half_rn(px);
-                sr += px;
-                srr += px * px;
-            }
+        const int ti = t == 1 ? 3 : (t == 3 ? 1 : t);
+#pragma unroll
+        for (int su = 0; su < kExhB; ++su) {
+            int u, v;
+            exh_iso_src(ti, kExhB, su, sv, u, v);
+            px[su] = E.img[(size_t)(y + v) * E.W + x + u];
+            sr += px[su];
+            srr += px[su] * px[su];
         }
-        if (t == 0) E.rstat[r] = make_int4(sr, srr, 0, 0);
+    } else {
+#pragma unroll
+        for (int su = 0; su < kExhB; ++su) px[su] = 0;
     }
+#pragma unroll
+    for (int m = 1; m < 8; m <<= 1) {
+        sr += __shfl_xor_sync(FULL, sr, m);
+        srr += __shfl_xor_sync(FULL, srr, m);
+    }
+    if (real) {
+        uint32_t hw[4] = {0u, 0u, 0u, 0u}, bw[2] = {0u, 0u};
+        const float mean = (float)sr * 0.015625f;  // exact (a multiple of 1/64 below 256)
+#pragma unroll
+        for (int su = 0; su < kExhB; ++su) {
+            hw[su / 2] |= (uint32_t)__half_as_ushort(__float2half_rn((float)px[su] - mean)) << (16 * (su & 1));
+            bw[su / 4] |= (uint32_t)px[su] << (8 * (su & 3));
+        }
+        *reinterpret_cast<uint4 *>(E.afp16 + (size_t)row * kExhK + sv * kExhB) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint2 *>(E.rbytes + (size_t)row * kExhK + sv * kExhB) = make_uint2(bw[0], bw[1]);
+    }
+    if (real && t == 0 && sv == 0) E.rstat[r] = make_int4(sr, srr, 0, 0);
 }
 
 // Row state of the screening epilogue.
@@ -258,9 +316,9 @@ cudaError_t launch_exh_tc(const ExhDesc &E, uint32_t *err, int *nseg, cudaStream
 cudaError_t launch_exhaustive(const ExhDesc &E, int engine, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(E.info, 0, FIC_INFO_WORDS * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    exh_prep_domains<<<(E.nd_pad + 255) / 256, 256, 0, st>>>(E);
+    exh_prep_domains<<<(E.nd_pad * 8 + 255) / 256, 256, 0, st>>>(E);
     stage_mark(st, "exh_prep_domains");
-    exh_prep_ranges<<<(E.nr * 8 + 255) / 256, 256, 0, st>>>(E);
+    exh_prep_ranges<<<(E.nr * 64 + 255) / 256, 256, 0, st>>>(E);
     stage_mark(st, "exh_prep_ranges");
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

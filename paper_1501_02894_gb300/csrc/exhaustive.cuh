@@ -24,11 +24,13 @@ struct ExhDesc {
     int32_t s_bits, o_bits;
     int32_t nseg;             // domain segments whose per-row bests exh_finalize merges
     uint32_t *dpairs;         // [nd][32]   packed (d4, d4) pairs for dp2a
-    __half *dfp16;            // [nd_pad][64] decimated domains, K-major, fp16
+    __half *dsc;              // [nd_pad][64] screen operand of the tensor path, K-major, fp16:
+                              //            (64 d4_k - Sd) 1024 / sqrt(nCdd) (0 for flat or padding domains)
     int4 *dstat;              // [nd_pad]   Sd, nCdd (u32), 512/nCdd (float bits), valid
     float4 *dscr;             // [nd_pad]   screening constants: -Sd/64, 64 sqrt(512^2/nCdd), 130 sqrt(512^2/nCdd), 0
                               //            (NaN: padding)
-    __half *afp16;            // [nr * 8][64] range rows permuted per isometry, fp16
+    __half *afp16;            // [nr * 8][64] range rows permuted per isometry, mean removed (r - Sr / 64), fp16
+    uint8_t *rbytes;          // [nr * 8][64] the same rows as pixel bytes (exact sum r*d4 by dp2a)
     int4 *rstat;              // [nr]       Sr, Srr
     long long *row_g;         // [nseg][nr * 8] best s-part error of the (range, isometry) row
     int2 *row_dk;             // [nseg][nr * 8] its domain index and contrast code

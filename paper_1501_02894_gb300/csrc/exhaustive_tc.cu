@@ -1,21 +1,37 @@
-// exhaustive_tc.cu -- the exhaustive search's sum r*d4 on the 5th-generation
-// tensor cores (tcgen05), with the screening epilogue fused.
+// exhaustive_tc.cu -- the exhaustive search on the 5th-generation tensor
+// cores (tcgen05), with the screening epilogue fused.
 //
-// C[row, d] = sum_k A[row, k] B[d, k], A = range rows (range x isometry, 64
-// fp16 values), B = decimated domains (64 fp16 values).  Operands are exact
-// in fp16 (pixels <= 255, 2x2 sums <= 1020) and every partial sum is an
-// integer below 2^24, so the fp32 accumulator holds sum r*d4 exactly.
+// The contraction yields each candidate's screen value directly:
+// Y[row, d] = sum_k A[row, k] W[d, k], A = range rows (range x isometry) with
+// the range's mean removed, a_k = r_k - Sr / 64, W = the domain's screen
+// operand w_k = (64 d4_k - Sd) 1024 / sqrt(nCdd), both rounded to fp16.  With
+// x_k = 64 d4_k - Sd, sum_k x_k = 0 and sum_k x_k^2 = 64 nCdd, so exactly
+// sum_k a_k w_k = sum_k r_k w_k = 1024 nCdr / sqrt(nCdd) = +-2 sqrt(L), L the
+// largest improvement any contrast could give (exhaustive.cuh).  The error
+// is bounded per row, independently of the domain: by Cauchy-Schwarz
+// sum_k |a_k w_k| <= sqrt(nCrr / 64) 8192 = 1024 sqrt(nCrr); the two fp16
+// roundings (2^-11 relative each) move Y by at most sqrt(nCrr), the fp32
+// accumulation of 64 products by 0.03 sqrt(nCrr) (one unit in the last
+// place per addition, taken four times over), and operand values too small
+// to be normal fp16 by at most 1: |Y - 2 sqrt(L)| <= E_row = 1.1 sqrt(nCrr)
+// + 4.  A candidate can beat the row's best exact error g only if sqrt(L) >=
+// sqrt(-g), i.e. only if |Y| >= 2 sqrt(-g) - E_row; the epilogue screens a
+// batch of 32 candidates with one maximum of |Y| per candidate.  Candidates
+// that pass go to a per-warp queue; 32 at a time, one per lane, they are
+// settled exactly: sum r*d4 by dp2a from byte range rows and packed domain
+// pairs, then the int64 contrast search, and each row's owner lane takes the
+// best of its entries (the smaller domain index wins ties, so the order of
+// evaluation does not change the result).
 //
 // One CTA owns 128 rows (16 ranges x 8 isometries) and streams every domain
 // tile of 128 domains:
-//   warp 0      TMA producer: the A tile once, B tiles through a 4-stage ring
+//   warp 0      TMA producer: the A tile once, W tiles through a 4-stage ring
 //               (128-byte swizzle, mbarrier transaction counts);
 //   warp 1      allocates 256 TMEM columns (two 128-column fp32
 //               accumulators) and issues tcgen05.mma (M=128, N=128, K=16,
 //               four per tile) from one lane, committing to mbarriers;
 //   warps 2..9  epilogue: each warp reads one 32-lane quarter of an
-//               accumulator (tcgen05.ld, 32x32b) for half of the columns and
-//               offers every (row, domain) to the row's screening state.
+//               accumulator (tcgen05.ld, 32x32b) for half of the columns.
 // The accumulators alternate, so the epilogue of tile n overlaps the MMA of
 // tile n+1.  Every mbarrier wait is bounded; a timeout sets an error flag,
 // all roles leave their loops, and TMEM is freed before the CTA exits.
@@ -92,29 +108,109 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Row state of the screening epilogue (as in exhaustive.cu).
+// Row state of the screening epilogue.
 struct TcRow {
-    long long g;
-    float thr;
+    long long g;  // best exact s-part error
+    float thr;    // threshold on |Y| (tc_threshold)
     int d, k;
 };
 
-// The exact evaluation is rare (after a few tiles most candidates fail the
-// screen), so it is kept out of line: 32 inlined copies per column batch
-// would only crowd the instruction cache.
-__device__ __noinline__ TcRow tc_exact(TcRow b, int d, float acc, int sr, int4 ds, int s_bits) {
-    const int ncdr = 64 * __float2int_rn(acc) - ds.x * sr;
+// Screen threshold of a row with best exact error g: exh_threshold(g) is a
+// lower bound of sqrt(-g) (or -1 while g >= 0, when everything passes), and
+// |Y| + E_row >= 2 sqrt(L) for every candidate.
+__device__ __forceinline__ float tc_threshold(long long g, float er) {
+    const float t = exh_threshold(g);
+    return t > 0.f ? fmaf(2.f, t, -er) * (1.f - 1e-6f) - 1.f : -1.f;
+}
+
+// Exact sum r*d4 of one range row (64 bytes) and one domain (32 packed
+// pairs), in four independent dp2a chains.
+__device__ __forceinline__ int tc_sdr(const uint8_t *rb, const uint32_t *dp) {
+    const uint4 *a4 = reinterpret_cast<const uint4 *>(rb);
+    const uint4 *p4 = reinterpret_cast<const uint4 *>(dp);
+    uint4 a[4], p[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = __ldg(a4 + i);  // range values 16i .. 16i+15
+#pragma unroll
+    for (int i = 0; i < 8; ++i) p[i] = __ldg(p4 + i);
+    unsigned acc[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        acc[i] = dp2a_lo(p[2 * i].x, a[i].x, acc[i]);
+        acc[i] = dp2a_hi(p[2 * i].y, a[i].x, acc[i]);
+        acc[i] = dp2a_lo(p[2 * i].z, a[i].y, acc[i]);
+        acc[i] = dp2a_hi(p[2 * i].w, a[i].y, acc[i]);
+        acc[i] = dp2a_lo(p[2 * i + 1].x, a[i].z, acc[i]);
+        acc[i] = dp2a_hi(p[2 * i + 1].y, a[i].z, acc[i]);
+        acc[i] = dp2a_lo(p[2 * i + 1].z, a[i].w, acc[i]);
+        acc[i] = dp2a_hi(p[2 * i + 1].w, a[i].w, acc[i]);
+    }
+    return (int)(acc[0] + acc[1] + acc[2] + acc[3]);
+}
+
+// Best contrast code of a candidate and its exact s-part error.
+__device__ __forceinline__ long long tc_eval(int sdr, int sr, int4 ds, int s_bits, int &k) {
+    const int ncdr = 64 * sdr - ds.x * sr;
     const uint32_t ncdd = (uint32_t)ds.y;
-    const int k = best_contrast<true>((long long)ncdr, (long long)ncdd, s_bits);
+    k = best_contrast<true>((long long)ncdr, (long long)ncdd, s_bits);
     const long long c = contrast_code(k, s_bits);
-    const long long g = c * c * (long long)ncdd - 1024LL * c * ncdr;
+    return c * c * (long long)ncdd - 1024LL * c * ncdr;
+}
+
+__device__ __forceinline__ void tc_offer(TcRow &b, long long g, int d, int k, float er) {
     if (exh_better(g, d, b.g, b.d)) {
         b.g = g;
-        b.thr = exh_threshold(g);
+        b.thr = tc_threshold(g, er);
         b.d = d;
         b.k = k;
     }
-    return b;
+}
+
+// Settles entries 0 .. cnt-1 (cnt <= 32) of the warp's queue: lane i
+// evaluates entry i (owner lane, domain) exactly; the entries that beat
+// their owner's best as it stood (usually none) are then offered to their
+// owners one at a time.  Called by the whole warp.
+__device__ __forceinline__ void tc_flush(const ExhDesc &E, const uint2 *q, int cnt, int row_base, int sr, float er,
+                                         TcRow &best, int lane) {
+    const unsigned FULL = 0xffffffffu;
+    const uint2 e = lane < cnt ? q[lane] : make_uint2(0u, 0u);
+    const int o = (int)e.x, d = (int)e.y;
+    const int sro = __shfl_sync(FULL, sr, o);
+    const long long og = __shfl_sync(FULL, best.g, o);
+    const int od = __shfl_sync(FULL, best.d, o);
+    long long g = 0;
+    int k = 0;
+    bool cand = false;
+    if (lane < cnt) {
+        g = tc_eval(tc_sdr(E.rbytes + (size_t)(row_base + o) * kExhK, E.dpairs + (size_t)d * 32), sro,
+                    __ldg(E.dstat + d), E.s_bits, k);
+        cand = exh_better(g, d, og, od);
+    }
+    unsigned bal = __ballot_sync(FULL, cand);
+    while (bal) {
+        const int i = __ffs(bal) - 1;
+        bal &= bal - 1u;
+        const int oi = __shfl_sync(FULL, o, i), di = __shfl_sync(FULL, d, i), ki = __shfl_sync(FULL, k, i);
+        const long long gi = __shfl_sync(FULL, g, i);
+        if (lane == oi) tc_offer(best, gi, di, ki, er);
+    }
+}
+
+// Settles the first 32 queued entries and moves the rest (at most 96) down.
+__device__ __forceinline__ void tc_flush32(const ExhDesc &E, uint2 *q, int &qn, int row_base, int sr, float er,
+                                           TcRow &best, int lane) {
+    __syncwarp();
+    tc_flush(E, q, 32, row_base, sr, er, best, lane);
+    const int rest = qn - 32;
+    uint2 mv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) mv[i] = 32 * i + lane < rest ? q[32 + 32 * i + lane] : make_uint2(0u, 0u);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        if (32 * i + lane < rest) q[32 * i + lane] = mv[i];
+    __syncwarp();
+    qn = rest;
 }
 
 __global__ void __launch_bounds__(kTcThreads, 2)
@@ -129,7 +225,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     __shared__ TcRow s_half[kTcRows];  // the second epilogue warp of each lane quarter hands its state over
-    __shared__ float4 s_wc[kTcEpiWarps][2][kTcCols / 2];  // per epilogue warp: its half's constants, two tiles
+    __shared__ uint2 s_q[kTcEpiWarps][128];  // per epilogue warp: candidates to settle (owner lane, domain)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row0 = blockIdx.x * kTcRows;
@@ -228,7 +324,9 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         const int r = row >> 3, t = row & 7;
         const bool live = r < E.nr && t < E.isos;
         const int sr = live ? E.rstat[r].x : 0;
-        const float srf = (float)sr;
+        // nCrr = 64 Srr - Sr^2 (exact in int64, then below 2^28)
+        const float er = live ? fmaf(1.1f, sqrtf((float)(64LL * E.rstat[r].y - (long long)sr * sr)), 4.f) : 0.f;
+        const int row_base = row0 + 32 * q;  // the warp's rows: lane i owns row_base + i
         TcRow best;
         best.g = 0x7fffffffffffffffLL;
         best.thr = live ? -1.f : __int_as_float(0x7f800000);  // everything passes / dead rows never pass
@@ -236,51 +334,25 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         best.k = 0;
         if (live) {
             // seed with the grid domain nearest the range's centred domain: a
-            // good candidate from the start lowers the screen's threshold at
+            // good candidate from the start raises the screen's threshold at
             // once (ties still go to the smaller domain index, so the result
             // does not depend on the seed)
             const int rx = (r % E.nrx) * kExhB, ry = (r / E.nrx) * kExhB;
             const int cx = clampi(rx - kExhB / 2, 0, E.W - 2 * kExhB), cy = clampi(ry - kExhB / 2, 0, E.H - 2 * kExhB);
             const int ix = min((cx + E.step / 2) / E.step, E.ndx - 1), iy = min((cy + E.step / 2) / E.step, E.ndy - 1);
             const int d0 = iy * E.ndx + ix;
-            const uint4 *a = reinterpret_cast<const uint4 *>(E.afp16 + (size_t)row * kExhK);
-            const uint4 *bq = reinterpret_cast<const uint4 *>(E.dfp16 + (size_t)d0 * kExhK);
-            float acc = 0.f;  // integer products and sums below 2^24: exact
-#pragma unroll
-            for (int i = 0; i < kExhK / 8; ++i) {
-                const uint4 av = __ldg(a + i), bv = __ldg(bq + i);
-                const uint32_t aw[4] = {av.x, av.y, av.z, av.w}, bw[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float2 fa = __half22float2(*reinterpret_cast<const __half2 *>(&aw[j]));
-                    const float2 fb = __half22float2(*reinterpret_cast<const __half2 *>(&bw[j]));
-                    acc = fmaf(fa.x, fb.x, acc);
-                    acc = fmaf(fa.y, fb.y, acc);
-                }
-            }
-            best = tc_exact(best, d0, acc, sr, __ldg(E.dstat + d0), E.s_bits);
+            int k0;
+            const long long g0 =
+                tc_eval(tc_sdr(E.rbytes + (size_t)row * kExhK, E.dpairs + (size_t)d0 * 32), sr, __ldg(E.dstat + d0),
+                        E.s_bits, k0);
+            tc_offer(best, g0, d0, k0, er);
         }
-        // screening constants of each tile: every epilogue warp stages the
-        // 64 columns of its half in a buffer of its own (tile n+1's load is in
-        // flight while tile n is screened), so the warps never wait on one
-        // another; a wait that runs out ends the warp's loop (warp-uniform)
-        float4 *wc = &s_wc[ew][0][0];
-        const float4 *gc = E.dscr + (size_t)h * (kTcCols / 2) + lane;
-        float4 pre0 = make_float4(0.f, 0.f, 0.f, 0.f), pre1 = pre0;
-        if (ntiles > 0) {
-            pre0 = __ldg(gc + (size_t)t0 * kTcCols);
-            pre1 = __ldg(gc + (size_t)t0 * kTcCols + 32);
-        }
+        uint2 *qw = s_q[ew];
+        int qn = 0;  // queued entries (warp-uniform)
+        const unsigned lt = (1u << lane) - 1u;
         bool bad = false;
         for (int n = 0; n < ntiles; ++n) {
             const int acc = n & 1;
-            wc[acc * 64 + lane] = pre0;
-            wc[acc * 64 + 32 + lane] = pre1;
-            __syncwarp();
-            if (n + 1 < ntiles) {
-                pre0 = __ldg(gc + (size_t)(t0 + n + 1) * kTcCols);
-                pre1 = __ldg(gc + (size_t)(t0 + n + 1) * kTcCols + 32);
-            }
             const bool got = mbar_wait(&bar_acc_full[acc], (uint32_t)((n >> 1) & 1), kMbarLimit);
             if (!__all_sync(0xffffffffu, got) || s_abort) {
                 bad = true;
@@ -293,25 +365,39 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kTcCols + col), v);
                 const int dbase = (t0 + n) * kTcCols + col;
-                const float4 *cs = wc + acc * 64 + c0;
-                // the batch's largest screen value first, without branches (the
-                // 32 screens schedule as independent chains); the threshold only
-                // rises as the row's best improves, so a batch whose largest value
-                // is below it holds no candidate to evaluate
-                float m = -__int_as_float(0x7f800000);
+                // the batch's largest |Y| (32 independent maxima); the
+                // threshold only rises as the row's best improves, so a batch
+                // whose largest value is below it holds nothing to settle
+                float m = 0.f;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) m = fmaxf(m, exh_screen(v[j], srf, cs[j]));
-                if (m >= best.thr) {
+                for (int j = 0; j < 32; ++j) m = fmaxf(m, fabsf(v[j]));
+                if (__any_sync(0xffffffffu, m >= best.thr)) {
+                    unsigned pm = 0;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        if (exh_screen(v[j], srf, cs[j]) >= best.thr)
-                            best = tc_exact(best, dbase + j, v[j], sr, __ldg(E.dstat + dbase + j), E.s_bits);
+                    for (int j = 0; j < 32; ++j) pm |= (fabsf(v[j]) >= best.thr ? 1u : 0u) << j;
+                    const int nvalid = E.nd - dbase;  // padding domains are never settled
+                    if (nvalid < 32) pm &= nvalid > 0 ? (1u << nvalid) - 1u : 0u;
+                    unsigned cols = __reduce_or_sync(0xffffffffu, pm);
+                    while (cols) {
+                        const int j = __ffs(cols) - 1;
+                        cols &= cols - 1u;
+                        const bool p = (pm >> j) & 1u;
+                        const unsigned bal = __ballot_sync(0xffffffffu, p);
+                        if (p) qw[qn + __popc(bal & lt)] = make_uint2((uint32_t)lane, (uint32_t)(dbase + j));
+                        qn += __popc(bal);
+                        // settling waits until the accumulator is released,
+                        // unless the queue could overflow
+                        if (qn > 96) tc_flush32(E, qw, qn, row_base, sr, er, best, lane);
                     }
                 }
             }
             tc_fence_before();
             mbar_arrive(&bar_acc_empty[acc]);
-            __syncwarp();  // this buffer is rewritten two tiles later
+            while (qn >= 32) tc_flush32(E, qw, qn, row_base, sr, er, best, lane);
+        }
+        if (!bad && qn > 0) {
+            __syncwarp();
+            tc_flush(E, qw, qn, row_base, sr, er, best, lane);
         }
         if (bad) s_abort = 1;
         // merge the two column halves of each row (the lower domain half wins ties)
@@ -363,7 +449,7 @@ cudaError_t launch_exh_tc(const ExhDesc &E, uint32_t *err, int *nseg, cudaStream
     const int slots = sms * per;
     CUtensorMap ma, mb;
     // rows past the end of A read as zeros (TMA out-of-bounds fill)
-    if (make_f16_map(&ma, E.afp16, E.nr * 8) || make_f16_map(&mb, E.dfp16, E.nd_pad)) return cudaErrorInvalidValue;
+    if (make_f16_map(&ma, E.afp16, E.nr * 8) || make_f16_map(&mb, E.dsc, E.nd_pad)) return cudaErrorInvalidValue;
     const int ctas = (E.nr * 8 + kTcRows - 1) / kTcRows;
     const int ntiles = E.nd_pad / kTcCols;
     int seg = (4 * slots + ctas - 1) / ctas;  // about four waves of CTAs
