@@ -108,6 +108,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Order in which a CTA visits its ntiles domain tiles: tile i, i + step,
+// i + 2 step, ... (mod ntiles), with step near ntiles / phi and coprime with
+// ntiles (a bijection).  The first tiles then sample the whole domain pool,
+// so the rows' thresholds approach their final values early and fewer
+// candidates pass the screen; the result does not depend on the order.
+__device__ __forceinline__ int tc_tile_step(int ntiles) {
+    int step = max(1, (int)(0.618034f * (float)ntiles));
+    for (;; ++step) {
+        int a = step, b = ntiles;
+        while (b) {
+            const int t = a % b;
+            a = b;
+            b = t;
+        }
+        if (a == 1) return step;
+    }
+}
+
 // Row state of the screening epilogue.
 struct TcRow {
     long long g;  // best exact s-part error
@@ -233,6 +251,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     const int ntiles_all = E.nd_pad / kTcCols;
     const int t0 = (int)(((long long)blockIdx.y * ntiles_all) / gridDim.y);
     const int ntiles = (int)(((long long)(blockIdx.y + 1) * ntiles_all) / gridDim.y) - t0;
+    const int tstep = ntiles > 0 ? tc_tile_step(ntiles) : 1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTcStages; ++s) {
@@ -266,7 +285,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 "[%4];" ::"r"(smem_u32(sA)),
                 "l"(reinterpret_cast<uint64_t>(&mapA)), "r"(0), "r"(row0), "r"(smem_u32(&bar_a))
                 : "memory");
-            int issued = 0;
+            int issued = 0, tix = 0;
             for (int n = 0; n < ntiles; ++n) {
                 const int s = n % kTcStages;
                 const uint32_t par = (uint32_t)((n / kTcStages) & 1) ^ 1u;
@@ -279,8 +298,10 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 asm volatile(
                     "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
                     "%3}], [%4];" ::"r"(smem_u32(sB + s * kTileBytes)),
-                    "l"(reinterpret_cast<uint64_t>(&mapB)), "r"(0), "r"((t0 + n) * kTcCols), "r"(smem_u32(&bar_full[s]))
+                    "l"(reinterpret_cast<uint64_t>(&mapB)), "r"(0), "r"((t0 + tix) * kTcCols), "r"(smem_u32(&bar_full[s]))
                     : "memory");
+                tix += tstep;
+                if (tix >= ntiles) tix -= ntiles;
             }
             // copies still in flight must land before the CTA may leave
             mbar_wait(&bar_a, 0u, kMbarLimit);
@@ -351,7 +372,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         int qn = 0;  // queued entries (warp-uniform)
         const unsigned lt = (1u << lane) - 1u;
         bool bad = false;
-        for (int n = 0; n < ntiles; ++n) {
+        for (int n = 0, tix = 0; n < ntiles; ++n, tix = tix + tstep >= ntiles ? tix + tstep - ntiles : tix + tstep) {
             const int acc = n & 1;
             const bool got = mbar_wait(&bar_acc_full[acc], (uint32_t)((n >> 1) & 1), kMbarLimit);
             if (!__all_sync(0xffffffffu, got) || s_abort) {
@@ -364,7 +385,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 const int col = h * (kTcCols / 2) + c0;
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kTcCols + col), v);
-                const int dbase = (t0 + n) * kTcCols + col;
+                const int dbase = (t0 + tix) * kTcCols + col;
                 // the batch's largest |Y| (32 independent maxima); the
                 // threshold only rises as the row's best improves, so a batch
                 // whose largest value is below it holds nothing to settle
