@@ -126,6 +126,13 @@ __device__ __forceinline__ int tc_tile_step(int ntiles) {
     }
 }
 
+// Largest of three floats (three-input max of sm_100 and later).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Row state of the screening epilogue.
 struct TcRow {
     long long g;  // best exact s-part error
@@ -389,9 +396,12 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                 // the batch's largest |Y| (32 independent maxima); the
                 // threshold only rises as the row's best improves, so a batch
                 // whose largest value is below it holds nothing to settle
-                float m = 0.f;
+                float mp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int j = 0; j < 32; ++j) m = fmaxf(m, fabsf(v[j]));
+                for (int j = 0; j < 32; j += 8)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) mp[i] = fmax3(mp[i], fabsf(v[j + 2 * i]), fabsf(v[j + 2 * i + 1]));
+                const float m = fmax3(mp[0], mp[1], fmaxf(mp[2], mp[3]));
                 if (__any_sync(0xffffffffu, m >= best.thr)) {
                     unsigned pm = 0;
 #pragma unroll
