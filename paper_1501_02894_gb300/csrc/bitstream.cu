@@ -234,11 +234,16 @@ __global__ void tile_size_kernel(const __grid_constant__ BitBatch B) {
     if (lane == 0) D.sizes[t] = s;
 }
 
-// One CTA per stream: the index, and the stream's words zeroed.
+// kSerZeroCtas CTAs per stream (blockIdx.y): each zeroes a slice of the
+// stream's words (the writer ORs its fields in); the first also scans the
+// block sizes into the index.
+constexpr int kSerZeroCtas = 8;
 __global__ void __launch_bounds__(1024) ser_scan_kernel(const __grid_constant__ BitBatch B) {
     const BitDesc &D = B.d[blockIdx.x];
-    for (long long i = threadIdx.x; i < D.nwords; i += blockDim.x) D.words[i] = 0u;
-    cta_scan(D.sizes, D.ntop, D.tile_bits);
+    const long long per = (D.nwords + kSerZeroCtas - 1) / kSerZeroCtas;
+    const long long lo = per * blockIdx.y, hi = min(D.nwords, lo + per);
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) D.words[i] = 0u;
+    if (blockIdx.y == 0) cta_scan(D.sizes, D.ntop, D.tile_bits);
 }
 
 __global__ void write_kernel(const __grid_constant__ BitBatch B) {
@@ -377,56 +382,79 @@ struct LeafPos {
 };
 constexpr int kTileLeaves = 64;
 
-// Walk the headers of a block; returns its leaf count, or -1 for a block that
-// does not tile (or, with `out`, holds more than `cap` leaves).
-__device__ int walk_tile(const BitLayout &b, const uint32_t *words, long long nwords, unsigned long long pos,
-                         unsigned long long end, LeafPos *out, int cap) {
-    const int cells = b.bmax / b.bmin;
+// 32 bits of staged words starting at bit `pos` (the buffer holds four zero
+// words past the staged ones: every read of a walk starts less than 96 bits
+// past the block's end, which lies in the staged words).
+__device__ __forceinline__ uint32_t bits32(const uint32_t *w, uint32_t pos) {
+    return __funnelshift_r(w[pos >> 5], w[(pos >> 5) + 1], pos & 31);
+}
+
+// Walk the headers of a block in staged words (positions relative to the
+// first staged word); returns its leaf count, or -1 for a block that does
+// not tile (or, with OUT, holds more than `cap` leaves).  A leaf at level
+// `level` covers 4^(L - level) bmin cells (bmax / bmin = 2^(L - 1)), its
+// header is the level id (omitted under Technique 2 inside a group of four)
+// and the phase bit, and its fields have a fixed length for each phase and
+// level, so the walk reads only the headers.
+template <bool OUT>
+__device__ int walk_tile(const BitLayout &b, const uint32_t *words, uint32_t pos, uint32_t end, LeafPos *out,
+                         int cap) {
+    const int L = b.L, lbits = b.lbits;
+    const bool t2 = b.technique2 && L > 1, pbit = b.phase_bit, local = b.mode == FIC_LOCAL;
+    const int ncells = 1 << (2 * (L - 1));
+    const uint32_t lmask = (1u << lbits) - 1u;
+    const uint32_t len1 = (uint32_t)(b.s_bits + b.o_bits) + (local ? (uint32_t)b.local_bits : 0u) +
+                          (b.mode == FIC_EXHAUSTIVE ? (uint32_t)(b.dom_bits + b.iso_bits) : 0u);
+    const uint32_t len2_top = (uint32_t)b.o_bits + 3u * 5u + 4u, len2 = (uint32_t)b.o_bits + 3u * 6u + 4u;
+    const uint32_t lskip = (uint32_t)(b.s_bits + b.o_bits), lbm = (1u << b.local_bits) - 1u;
+    const uint32_t pp = (uint32_t)(b.per * b.per);
     int c = 0, count = 0;
-    while (c < cells * cells) {
-        int level;
-        if (b.technique2 && b.L > 1 && (c & 3) != 0) {
-            level = b.L;
-        } else {
-            level = (int)get_bits(words, pos, b.lbits, nwords) + 1;
-            pos += (unsigned)b.lbits;
+    while (c < ncells) {
+        const uint32_t hb = bits32(words, pos);
+        int level = L;
+        uint32_t used = 0;
+        if (!(t2 && (c & 3) != 0)) {
+            level = (int)(hb & lmask) + 1;
+            used = (uint32_t)lbits;
         }
-        if (level > b.L) return -1;
-        const int B = b.bmax >> (level - 1);
-        const int span = (B / b.bmin) * (B / b.bmin);
-        if (c % span) return -1;
+        if (level > L) return -1;
+        const int span_lg = 2 * (L - level);
+        if (c & ((1 << span_lg) - 1)) return -1;
         int phase = 1;
-        if (b.phase_bit && level < b.L) {
-            phase = get_bits(words, pos, 1, nwords) ? 2 : 1;
-            pos += 1;
+        if (pbit && level < L) {
+            phase = ((hb >> used) & 1u) ? 2 : 1;
+            ++used;
         }
-        if (out) {
+        pos += used;
+        if (OUT) {
             if (count >= cap) return -1;
-            out[count].pos = (uint32_t)pos;
+            out[count].pos = pos;
             out[count].c = (uint16_t)c;
             out[count].level = (uint8_t)level;
             out[count].phase = (uint8_t)phase;
         }
         if (phase == 1) {
-            pos += (unsigned)(b.s_bits + b.o_bits);
-            if (b.mode == FIC_LOCAL) {
-                if ((int)get_bits(words, pos, b.local_bits, nwords) >= b.per * b.per) return -1;
-                pos += (unsigned)b.local_bits;
-            } else if (b.mode == FIC_EXHAUSTIVE) {
-                pos += (unsigned)(b.dom_bits + b.iso_bits);
-            }
+            if (local && (bits32(words, pos + lskip) & lbm) >= pp) return -1;
+            pos += len1;
         } else {
-            pos += (unsigned)(b.o_bits + 3 * (level == 1 ? 5 : 6) + 4);
+            pos += level == 1 ? len2_top : len2;
         }
         if (pos > end) return -1;
         ++count;
-        c += span;
+        c += 1 << span_lg;
     }
     return pos == end ? count : -1;
 }
 
-// The record of one walked leaf of top-level block t.
-__device__ uint4 decode_leaf(const BitLayout &b, const uint32_t *words, long long nwords, const LeafPos &lp, int t) {
+// The next nb (<= 32) bits of staged words at `pos`, advancing it.
+__device__ __forceinline__ uint32_t take_bits(const uint32_t *w, uint32_t &pos, int nb) {
+    const uint32_t v = nb ? bits32(w, pos) & (0xffffffffu >> (32 - nb)) : 0u;
+    pos += (uint32_t)nb;
+    return v;
+}
+
+// The record of one walked leaf of top-level block t (staged words).
+__device__ uint4 decode_leaf(const BitLayout &b, const uint32_t *words, const LeafPos &lp, int t) {
     const int tw = b.W / b.bmax;
     const int tx = (t % tw) * b.bmax, ty = (t / tw) * b.bmax;
     const int c = lp.c, level = lp.level, phase = lp.phase;
@@ -437,36 +465,31 @@ __device__ uint4 decode_leaf(const BitLayout &b, const uint32_t *words, long lon
     }
     const int B = b.bmax >> (level - 1);
     const int x = tx + cx * b.bmin, y = ty + cy * b.bmin;
-    unsigned long long pos = lp.pos;
+    uint32_t pos = lp.pos;
     uint32_t k = 0, q = 0, dz = 0, iso = 0;
     int dx = centred_origin(x, B, b.W), dy = centred_origin(y, B, b.H);
     if (phase == 1) {
-        k = get_bits(words, pos, b.s_bits, nwords);
-        pos += (unsigned)b.s_bits;
-        q = get_bits(words, pos, b.o_bits, nwords);
-        pos += (unsigned)b.o_bits;
+        k = take_bits(words, pos, b.s_bits);
+        q = take_bits(words, pos, b.o_bits);
         if (b.mode == FIC_LOCAL) {
-            const int idx = (int)get_bits(words, pos, b.local_bits, nwords);
+            const int idx = (int)take_bits(words, pos, b.local_bits);
             dx += (idx % b.per - b.rstep) * b.step;
             dy += (idx / b.per - b.rstep) * b.step;
         } else if (b.mode == FIC_EXHAUSTIVE) {
-            const int idx = (int)get_bits(words, pos, b.dom_bits, nwords);
-            pos += (unsigned)b.dom_bits;
+            const int idx = (int)take_bits(words, pos, b.dom_bits);
             dx = (idx % b.ndx) * b.step;
             dy = (idx / b.ndx) * b.step;
-            iso = get_bits(words, pos, b.iso_bits, nwords);
+            iso = take_bits(words, pos, b.iso_bits);
         }
     } else {
         const int M = level == 1 ? 5 : 6;
-        q = get_bits(words, pos, b.o_bits, nwords);
-        pos += (unsigned)b.o_bits;
+        q = take_bits(words, pos, b.o_bits);
         for (int i = 0; i < 3; ++i) {
-            int d = (int)get_bits(words, pos, M, nwords);
-            pos += (unsigned)M;
+            int d = (int)take_bits(words, pos, M);
             if (d >= (1 << (M - 1))) d -= 1 << M;
             dz |= ((uint32_t)d & 0xffu) << (8 * i);
         }
-        k = get_bits(words, pos, 4, nwords);
+        k = take_bits(words, pos, 4);
     }
     return make_uint4((uint32_t)x | ((uint32_t)y << 16), (uint32_t)level | ((uint32_t)phase << 8) | (k << 16) | (q << 24),
                       dz | (iso << 24), (uint32_t)dx | ((uint32_t)dy << 16));
@@ -477,21 +500,23 @@ __device__ uint4 decode_leaf(const BitLayout &b, const uint32_t *words, long lon
 constexpr int kParseWarps = 4;
 constexpr int kBlockWords = 320;  // words staged per block (larger blocks read global memory)
 
-// Stage the words holding bits [beg, end) of a block; returns the first
-// staged word, or -1 when the block does not fit the buffer.
+// Stage the words holding bits [beg, end) of a block, then four zero words
+// (reads past the stream's last word give zeros, as get_bits does); returns
+// the first staged word, or -1 when the block does not fit the buffer
+// (kBlockWords + 4 words).
 __device__ __forceinline__ long long stage_block_words(const BitDesc &D, unsigned long long beg, unsigned long long end,
                                                        uint32_t *sw, int lane, int &nstaged) {
     const long long w0 = (long long)(beg >> 5);
     const long long w1 = min(D.nwords, (long long)((end + 63) >> 5));  // + the word a field may reach into
     nstaged = (int)(w1 - w0);
     if (nstaged > kBlockWords || nstaged < 0) return -1;
-    for (int i = lane; i < nstaged; i += 32) sw[i] = D.words_in[w0 + i];
+    for (int i = lane; i < nstaged + 4; i += 32) sw[i] = i < nstaged ? D.words_in[w0 + i] : 0u;
     __syncwarp();
     return w0;
 }
 
 __global__ void __launch_bounds__(kParseWarps * 32) parse_count_kernel(const __grid_constant__ BitBatch B) {
-    __shared__ uint32_t s_words[kParseWarps][kBlockWords];
+    __shared__ uint32_t s_words[kParseWarps][kBlockWords + 4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = blockIdx.x * kParseWarps + warp;
     if (g >= B.tops_base[B.count]) return;
@@ -504,8 +529,8 @@ __global__ void __launch_bounds__(kParseWarps * 32) parse_count_kernel(const __g
         int nst = 0;
         const long long w0 = stage_block_words(D, beg, end, s_words[warp], lane, nst);
         if (lane == 0)
-            n = w0 >= 0 ? walk_tile(D.b, s_words[warp], nst, beg - 32ull * (unsigned long long)w0,
-                                    end - 32ull * (unsigned long long)w0, nullptr, 0)
+            n = w0 >= 0 ? walk_tile<false>(D.b, s_words[warp], (uint32_t)(beg - 32ull * (unsigned long long)w0),
+                                           (uint32_t)(end - 32ull * (unsigned long long)w0), nullptr, 0)
                         : parse_tile<false>(D.b, D.words_in, D.nwords, beg, end, t, nullptr, nullptr);
     }
     // a block that does not parse is marked by the top bit (the scan finds it)
@@ -528,7 +553,7 @@ __global__ void __launch_bounds__(1024) parse_scan_kernel(const __grid_constant_
 }
 
 __global__ void __launch_bounds__(kParseWarps * 32) parse_write_kernel(const __grid_constant__ BitBatch B) {
-    __shared__ uint32_t s_words[kParseWarps][kBlockWords];
+    __shared__ uint32_t s_words[kParseWarps][kBlockWords + 4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = blockIdx.x * kParseWarps + warp;
     if (g >= B.tops_base[B.count]) return;
@@ -552,15 +577,15 @@ __global__ void __launch_bounds__(kParseWarps * 32) parse_write_kernel(const __g
     __shared__ LeafPos s_leaf[kParseWarps][kTileLeaves];
     int n = 0;
     if (lane == 0)
-        n = walk_tile(D.b, s_words[warp], nst, beg - 32ull * (unsigned long long)w0,
-                      end - 32ull * (unsigned long long)w0, s_leaf[warp], kTileLeaves);
+        n = walk_tile<true>(D.b, s_words[warp], (uint32_t)(beg - 32ull * (unsigned long long)w0),
+                            (uint32_t)(end - 32ull * (unsigned long long)w0), s_leaf[warp], kTileLeaves);
     n = __shfl_sync(0xffffffffu, n, 0);  // the count pass found the same blocks well formed
     __syncwarp();
     uint32_t mask = 0;
     fic_record *out = D.out_rec + D.first[t];
     for (int i = lane; i < n; i += 32) {
         const LeafPos lp = s_leaf[warp][i];
-        *reinterpret_cast<uint4 *>(out + i) = decode_leaf(D.b, s_words[warp], nst, lp, t);
+        *reinterpret_cast<uint4 *>(out + i) = decode_leaf(D.b, s_words[warp], lp, t);
         for (int a = 1; a < lp.level; ++a)
             mask |= 1u << (((1u << (2 * (a - 1))) - 1) / 3 + (uint32_t)(lp.c >> (2 * (D.b.L - a))));
     }
@@ -598,7 +623,7 @@ static int run_batch(BitBatch &B, bool parse, cudaStream_t s) {
         const int warps_per_cta = 8;
         const int grid = (tops + warps_per_cta - 1) / warps_per_cta;
         tile_size_kernel<<<grid, warps_per_cta * 32, 0, s>>>(B);
-        ser_scan_kernel<<<B.count, 1024, 0, s>>>(B);
+        ser_scan_kernel<<<dim3(B.count, kSerZeroCtas), 1024, 0, s>>>(B);
         write_kernel<<<grid, warps_per_cta * 32, 0, s>>>(B);
     } else {
         const int grid = (tops + kParseWarps - 1) / kParseWarps;
