@@ -302,6 +302,22 @@ FIC_API int fic_plan_autotune(fic_plan *plan, int iters, int reps, void *stream,
 FIC_API int fic_encode_noalloc(const uint8_t *d_img, int width, int height, const fic_params *p,
                                fic_stream *out, void *stream);
 
+/* ---- Records to host memory ----
+ * Copy each stream's records -- as many as its info block counts, at most
+ * its capacity -- and, when h_info is not NULL, its info block
+ * (FIC_INFO_WORDS words) to host memory, without a round trip to the host:
+ * the count is read on the device, so only the records the stream holds
+ * cross the bus (a plain device-to-host copy would have to move the whole
+ * capacity, or wait for the count).  h_records[i] (16-byte aligned, room
+ * for stream i's capacity) and h_info[i] must be host memory the device
+ * can address: page-locked (cudaHostAlloc / cudaMallocHost, or
+ * cudaHostRegister), or any host memory where the device reads the host's
+ * page tables (a coherent CPU-GPU link); other pointers, and misaligned
+ * ones, give FIC_EBADPARAM before anything is enqueued.  One kernel launch per 64 streams, asynchronous on `stream`:
+ * the host may read the buffers once the stream has passed this point. */
+FIC_API int fic_records_to_host(const fic_stream *sts, int count, fic_record *const *h_records,
+                                uint32_t *const *h_info, void *stream);
+
 /* ---- Bitstream of the stored parameters (Sections 3.3 and 3.4) ----
  * Layout: bits appended least-significant first into uint32 words; leaves
  * in the stream's canonical order; per leaf: level - 1 in ceil(log2 L)

@@ -25,6 +25,7 @@ from .fic import (  # noqa: F401
     params,
     parse,
     parse_batch,
+    records_to_host,
     rescale,
     serialize,
     serialize_batch,

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfic.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["encode_mns.cu", "encode_mns32.cu", "encode_local.cu", "exhaustive.cu", "exhaustive_tc.cu", "pack.cu", "decode.cu", "serve.cu", "stats.cu", "bitstream.cu", "api.cu"]
+SOURCES = ["encode_mns.cu", "encode_mns32.cu", "encode_local.cu", "exhaustive.cu", "exhaustive_tc.cu", "pack.cu", "decode.cu", "serve.cu", "stats.cu", "bitstream.cu", "transfer.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

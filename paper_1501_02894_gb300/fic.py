@@ -139,6 +139,7 @@ def lib():
         L.fic_encode_plan_run.argtypes = [vp, vp]
         L.fic_decode_plan_create.argtypes = [P(StreamC), ctypes.c_int, P(vp), vp, ctypes.c_size_t, vp, P(vp)]
         L.fic_decode_plan_run.argtypes = [vp, ctypes.c_int, vp]
+        L.fic_records_to_host.argtypes = [P(StreamC), ctypes.c_int, P(vp), P(vp), vp]
         L.fic_plan_destroy.argtypes = [vp]
         L.fic_plan_get_tuning.argtypes = [vp, P(Tuning)]
         L.fic_plan_run_timed.argtypes = [vp, ctypes.c_int, vp, P(ctypes.c_float), P(ctypes.c_char_p), ctypes.c_int,
@@ -327,6 +328,21 @@ def fic_decode(st: Stream, iters: int, out: torch.Tensor | None = None, workspac
     _check(lib().fic_decode(ctypes.byref(st.c), int(iters), _ptr(out), _ptr(ws), ws.numel(),
                             _stream_handle(stream)), "fic_decode")
     return out
+
+
+def records_to_host(sts, h_records, h_info=None, stream=None):
+    """Copy each Stream's records (as many as its info block counts) into the
+    page-locked host tensor h_records[i] (uint8, room for its capacity), and
+    its info block into h_info[i] when given, without waiting for the counts
+    on the host (fic_records_to_host).  Asynchronous on `stream`."""
+    n = len(sts)
+    Sa = (StreamC * n)(*[s.c for s in sts])
+    for s, h in zip(sts, h_records):
+        if not h.is_pinned() or h.numel() < 16 * s.capacity:
+            raise FicError(-2, "records_to_host: h_records must be pinned and hold the stream's capacity")
+    hr = (ctypes.c_void_p * n)(*[h.data_ptr() for h in h_records])
+    hi = (ctypes.c_void_p * n)(*[h.data_ptr() for h in h_info]) if h_info is not None else None
+    _check(lib().fic_records_to_host(Sa, n, hr, hi, _stream_handle(stream)), "fic_records_to_host")
 
 
 def fic_decode_batch(sts, iters: int, outs=None, workspace=None, stream=None):
