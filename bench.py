@@ -172,9 +172,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples_under_load": busy, "samples": len(self.lines)}
 
 
-def traffic_from_profile(kernel_key: str):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, valid
-    only while the kernel source is unchanged (hash recorded beside it)."""
+def profile_record(kernel_key: str):
+    """A kernel's record from its committed ncu summary (DRAM bytes and warp
+    instructions per launch), valid only while the kernel's sources are
+    unchanged (their hashes are recorded beside it); None otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -184,9 +185,35 @@ def traffic_from_profile(kernel_key: str):
             h = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
             if h != h0:
                 return None
-        return float(ent["bytes_per_launch"])
+        return ent
     except Exception:
         return None
+
+
+def traffic_from_profile(kernel_key: str):
+    """DRAM bytes per launch of a kernel (profile_record)."""
+    ent = profile_record(kernel_key)
+    return float(ent["bytes_per_launch"]) if ent else None
+
+
+def issue_from_profile(kernel_key: str, dur_ms: float, clocks: dict, sms: int):
+    """The kernel's instruction issue rate against the GPU's: warp
+    instructions per launch (ncu, profile_record) / the launch's duration,
+    over one warp instruction per scheduler per clock (4 per SM) at the SM
+    clock sampled during the timed region."""
+    ent = profile_record(kernel_key)
+    if not ent or not ent.get("inst_per_launch") or not dur_ms:
+        return None
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+    if not mhz:
+        return None
+    inst = float(ent["inst_per_launch"])
+    ach = inst / (dur_ms * 1e-3)
+    peak = 4.0 * sms * mhz * 1e6
+    return {"warp_instructions_per_launch": inst, "achieved_per_s": round(ach, 1), "peak_per_s": round(peak, 1),
+            "frac": round(ach / peak, 4),
+            "source": "smsp__inst_executed.sum of the kernel's committed ncu capture (valid while its sources are "
+                      "unchanged); peak = SMs x 4 schedulers x the SM clock sampled under load"}
 
 
 def gpu_uuid(torch, dev):
@@ -688,6 +715,10 @@ def run_batched(args, spec: Spec):
                                    if 2 * pixels < L2_BYTES else "larger than L2")
         ev_ms = ktab[dom]["ms_per_launch"]
         roofline["frac_event_serialised"] = round(alg[dom] / (ev_ms * 1e-3) / 1e9 / peak, 4)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roofline["issue"] = issue_from_profile(key, dur_ms, clocks, sms)
+    if roofline_fit:
+        roofline_fit["issue"] = issue_from_profile(f"{fit_k}_{spec.name}", roofline_fit["ms_per_launch"], clocks, sms)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
