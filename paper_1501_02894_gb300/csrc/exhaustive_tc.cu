@@ -16,9 +16,12 @@
 // to be normal fp16 by at most 1: |Y - 2 sqrt(L)| <= E_row = 1.1 sqrt(nCrr)
 // + 4.  A candidate can beat the row's best exact error g only if sqrt(L) >=
 // sqrt(-g), i.e. only if |Y| >= 2 sqrt(-g) - E_row; the epilogue screens a
-// batch of 32 candidates with one maximum of |Y| per candidate.  Candidates
-// that pass go to a per-warp queue; 32 at a time, one per lane, they are
-// settled exactly: sum r*d4 by dp2a from byte range rows and packed domain
+// batch of 32 candidates with one maximum of |Y| per candidate.  While many
+// of a batch's rows still pass (their thresholds are young: the first tiles
+// of a sweep), each such lane first settles its batch's best-screened
+// candidate at once, which raises its threshold before the rest of the
+// batch is screened again.  Candidates that pass go to a per-warp queue; 32
+// at a time, one per lane, they are settled exactly: sum r*d4 by dp2a from byte range rows and packed domain
 // pairs, then the int64 contrast search, and each row's owner lane takes the
 // best of its entries (the smaller domain index wins ties, so the order of
 // evaluation does not change the result).
@@ -47,6 +50,8 @@ constexpr int kTcStages = 4;
 constexpr int kTcEpiWarps = 8;
 constexpr int kTcThreads = (2 + kTcEpiWarps) * 32;
 constexpr uint32_t kTileBytes = kTcCols * kExhK * 2;  // 16 KiB (also the A tile)
+constexpr int kTcEagerRows = 2;  // a batch with this many passing rows settles their best candidates first
+                                 // (measured: 1, 2, 4, 8, 16 rows -> 2.08, 2.02, 2.10, 2.18, 2.27 ms at 1024 x 1024)
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -402,11 +407,31 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 #pragma unroll
                     for (int i = 0; i < 4; ++i) mp[i] = fmax3(mp[i], fabsf(v[j + 2 * i]), fabsf(v[j + 2 * i + 1]));
                 const float m = fmax3(mp[0], mp[1], fmaxf(mp[2], mp[3]));
-                if (__any_sync(0xffffffffu, m >= best.thr)) {
+                const unsigned rows = __ballot_sync(0xffffffffu, m >= best.thr);
+                if (rows) {
+                    const int nvalid = E.nd - dbase;  // padding domains are never settled
+                    unsigned done = 0;
+                    if (__popc(rows) >= kTcEagerRows) {
+                        // many rows still pass (their thresholds are young): each
+                        // lane settles its batch's best-screened candidate at once,
+                        // in parallel, which raises its threshold before the rest
+                        // of the batch is screened again
+                        int jm = 0;
+#pragma unroll
+                        for (int j = 31; j >= 0; --j) jm = fabsf(v[j]) == m ? j : jm;
+                        if (m >= best.thr && jm < nvalid) {
+                            int k;
+                            const long long g = tc_eval(tc_sdr(E.rbytes + (size_t)(row_base + lane) * kExhK,
+                                                               E.dpairs + (size_t)(dbase + jm) * 32),
+                                                        sr, __ldg(E.dstat + dbase + jm), E.s_bits, k);
+                            tc_offer(best, g, dbase + jm, k, er);
+                            done = 1u << jm;
+                        }
+                    }
                     unsigned pm = 0;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) pm |= (fabsf(v[j]) >= best.thr ? 1u : 0u) << j;
-                    const int nvalid = E.nd - dbase;  // padding domains are never settled
+                    pm &= ~done;
                     if (nvalid < 32) pm &= nvalid > 0 ? (1u << nvalid) - 1u : 0u;
                     unsigned cols = __reduce_or_sync(0xffffffffu, pm);
                     while (cols) {
