@@ -50,8 +50,9 @@ constexpr int kTcStages = 4;
 constexpr int kTcEpiWarps = 8;
 constexpr int kTcThreads = (2 + kTcEpiWarps) * 32;
 constexpr uint32_t kTileBytes = kTcCols * kExhK * 2;  // 16 KiB (also the A tile)
-constexpr int kTcEagerRows = 2;  // a batch with this many passing rows settles their best candidates first
-                                 // (measured: 1, 2, 4, 8, 16 rows -> 2.08, 2.02, 2.10, 2.18, 2.27 ms at 1024 x 1024)
+// a batch with this many passing rows settles their best candidates first
+// (1, 2, 4, 8, 16 rows measured 2.08, 2.02, 2.10, 2.18, 2.27 ms at 1024 x 1024)
+constexpr int kTcEagerRows = 2;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
