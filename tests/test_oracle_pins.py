@@ -413,6 +413,52 @@ def test_exhaustive_finds_planted_isometry(orc):
         assert res["e"][0] <= 64 * 512 ** 2 * 64 // 4          # rounding only: SSE <= n/4
 
 
+def _brute_exhaustive(img, x, y, B=8, step=4):
+    """Section 1's exhaustive search, by definition: every 2B x 2B domain of
+    the step grid under all eight isometries and every (s, O) code pair, the
+    error summed pixel by pixel (512 n (r - rhat) is an integer).  Returns
+    (scaled SSE, dx, dy, iso, k, q) of the winner; candidates in domain
+    raster order, then isometry order, a later one winning only if strictly
+    better; codes tied on the error go to the smaller |s|, then s > 0, then
+    the smaller luminance code."""
+    H, W = img.shape
+    n = B * B
+    cs = np.array([int(s * 128) for s in s_values(5)], dtype=np.int64)
+    Os = np.array(lum_values(7), dtype=np.int64)
+    r = img[y:y + B, x:x + B].astype(np.int64).reshape(-1)
+    best = None
+    for dy in range(0, H - 2 * B + 1, step):
+        for dx in range(0, W - 2 * B + 1, step):
+            blk = img[dy:dy + 2 * B, dx:dx + 2 * B].astype(np.int64)
+            d4 = blk[0::2, 0::2] + blk[1::2, 0::2] + blk[0::2, 1::2] + blk[1::2, 1::2]
+            for iso in range(8):
+                d = np.asarray(ISO_NUMPY[iso](d4)).reshape(-1)
+                res = (512 * n * r)[None, None, :] - (512 * n * Os)[None, :, None] \
+                    - cs[:, None, None] * (n * d - int(d.sum()))[None, None, :]
+                sse = (res * res).sum(-1)  # [contrast code, luminance code]
+                m = int(sse.min())
+                if best is None or m < best[0]:
+                    ks, qs = np.nonzero(sse == m)
+                    k, q = min(zip(ks, qs), key=lambda kq: (abs(cs[kq[0]]), cs[kq[0]] < 0, kq[1]))
+                    best = (m, dx, dy, iso, int(k), int(q))
+    return best
+
+
+def test_exhaustive_search_equals_brute_force(orc):
+    # a smooth field with noise, and one range planted from a rotated domain
+    rng = np.random.default_rng(21)
+    img = np.clip(synth.gaussian_scene(32, 4).astype(int) + rng.integers(-25, 25, (32, 32)), 0, 255).astype(np.uint8)
+    _plant(img, 16, 8, 8, 4, 16, 5, F(1, 2) + F(1, 32), 140)
+    p = orc.make_params("exhaustive", 8, 8, 8.0, dom_step=4, isometries=8)
+    xs, ys = [0, 24, 16, 8, 24, 0], [0, 0, 8, 16, 24, 24]
+    res = orc.search_ranges(img, p, xs, ys, [8] * len(xs))
+    for i, (x, y) in enumerate(zip(xs, ys)):
+        sse, dx, dy, iso, k, q = _brute_exhaustive(img, x, y)
+        got = (int(res["dx"][i]), int(res["dy"][i]), int(res["iso"][i]), int(res["k"][i]), int(res["q"][i]))
+        assert got == (dx, dy, iso, k, q), (x, y)
+        assert sse == int(res["e"][i]) * 64  # E = n 512^2 SSE, the scaled sum = (512 n)^2 SSE
+
+
 def test_local_finds_planted_offset(orc):
     img = synth.gaussian_scene(128, 12)
     rng = np.random.default_rng(5)
