@@ -413,35 +413,40 @@ def test_exhaustive_finds_planted_isometry(orc):
         assert res["e"][0] <= 64 * 512 ** 2 * 64 // 4          # rounding only: SSE <= n/4
 
 
-def _brute_exhaustive(img, x, y, B=8, step=4):
-    """Section 1's exhaustive search, by definition: every 2B x 2B domain of
-    the step grid under all eight isometries and every (s, O) code pair, the
-    error summed pixel by pixel (512 n (r - rhat) is an integer).  Returns
-    (scaled SSE, dx, dy, iso, k, q) of the winner; candidates in domain
-    raster order, then isometry order, a later one winning only if strictly
-    better; codes tied on the error go to the smaller |s|, then s > 0, then
-    the smaller luminance code."""
-    H, W = img.shape
+def _brute_search(img, x, y, B, cands):
+    """Phase-1 search of range (x, y) over the candidates (dx, dy, iso), in
+    the order given, by definition: every (s, O) code pair of each candidate,
+    the error summed pixel by pixel (512 n (r - rhat) is an integer).
+    Returns (scaled SSE, dx, dy, iso, k, q) of the winner; a later candidate
+    wins only if strictly better; codes tied on the error go to the smaller
+    |s|, then s > 0, then the smaller luminance code."""
     n = B * B
     cs = np.array([int(s * 128) for s in s_values(5)], dtype=np.int64)
     Os = np.array(lum_values(7), dtype=np.int64)
     r = img[y:y + B, x:x + B].astype(np.int64).reshape(-1)
     best = None
-    for dy in range(0, H - 2 * B + 1, step):
-        for dx in range(0, W - 2 * B + 1, step):
-            blk = img[dy:dy + 2 * B, dx:dx + 2 * B].astype(np.int64)
-            d4 = blk[0::2, 0::2] + blk[1::2, 0::2] + blk[0::2, 1::2] + blk[1::2, 1::2]
-            for iso in range(8):
-                d = np.asarray(ISO_NUMPY[iso](d4)).reshape(-1)
-                res = (512 * n * r)[None, None, :] - (512 * n * Os)[None, :, None] \
-                    - cs[:, None, None] * (n * d - int(d.sum()))[None, None, :]
-                sse = (res * res).sum(-1)  # [contrast code, luminance code]
-                m = int(sse.min())
-                if best is None or m < best[0]:
-                    ks, qs = np.nonzero(sse == m)
-                    k, q = min(zip(ks, qs), key=lambda kq: (abs(cs[kq[0]]), cs[kq[0]] < 0, kq[1]))
-                    best = (m, dx, dy, iso, int(k), int(q))
+    for dx, dy, iso in cands:
+        blk = img[dy:dy + 2 * B, dx:dx + 2 * B].astype(np.int64)
+        d4 = blk[0::2, 0::2] + blk[1::2, 0::2] + blk[0::2, 1::2] + blk[1::2, 1::2]
+        d = np.asarray(ISO_NUMPY[iso](d4)).reshape(-1)
+        res = (512 * n * r)[None, None, :] - (512 * n * Os)[None, :, None] \
+            - cs[:, None, None] * (n * d - int(d.sum()))[None, None, :]
+        sse = (res * res).sum(-1)  # [contrast code, luminance code]
+        m = int(sse.min())
+        if best is None or m < best[0]:
+            ks, qs = np.nonzero(sse == m)
+            k, q = min(zip(ks, qs), key=lambda kq: (abs(cs[kq[0]]), cs[kq[0]] < 0, kq[1]))
+            best = (m, dx, dy, iso, int(k), int(q))
     return best
+
+
+def _brute_exhaustive(img, x, y, B=8, step=4):
+    """Section 1's exhaustive search: every 2B x 2B domain of the step grid
+    in raster order, each under the eight isometries in order."""
+    H, W = img.shape
+    cands = [(dx, dy, iso) for dy in range(0, H - 2 * B + 1, step) for dx in range(0, W - 2 * B + 1, step)
+             for iso in range(8)]
+    return _brute_search(img, x, y, B, cands)
 
 
 def test_exhaustive_search_equals_brute_force(orc):
@@ -457,6 +462,26 @@ def test_exhaustive_search_equals_brute_force(orc):
         got = (int(res["dx"][i]), int(res["dy"][i]), int(res["iso"][i]), int(res["k"][i]), int(res["q"][i]))
         assert got == (dx, dy, iso, k, q), (x, y)
         assert sse == int(res["e"][i]) * 64  # E = n 512^2 SSE, the scaled sum = (512 n)^2 SSE
+
+
+def test_local_search_equals_brute_force(orc):
+    """Section 2's local search: the domains whose offsets from the centred
+    one (x - B/2 clamped into the image) are multiples of 4 within +-16 in x
+    and y, offsets in raster order, those that leave the image skipped, no
+    isometries; ranges at the border lose candidates."""
+    img = np.clip(synth.gaussian_scene(64, 6).astype(int) + np.random.default_rng(8).integers(-30, 30, (64, 64)),
+                  0, 255).astype(np.uint8)
+    p = orc.make_params("local", 8, 8, 8.0)
+    xs, ys = [0, 56, 24, 32, 8], [0, 8, 24, 56, 40]
+    res = orc.search_ranges(img, p, xs, ys, [8] * len(xs))
+    for i, (x, y) in enumerate(zip(xs, ys)):
+        cx, cy = min(max(x - 4, 0), 64 - 16), min(max(y - 4, 0), 64 - 16)
+        cands = [(cx + ox, cy + oy, 0) for oy in range(-16, 17, 4) for ox in range(-16, 17, 4)
+                 if 0 <= cx + ox <= 64 - 16 and 0 <= cy + oy <= 64 - 16]
+        sse, dx, dy, iso, k, q = _brute_search(img, x, y, 8, cands)
+        got = (int(res["dx"][i]), int(res["dy"][i]), int(res["iso"][i]), int(res["k"][i]), int(res["q"][i]))
+        assert got == (dx, dy, iso, k, q), (x, y)
+        assert sse == int(res["e"][i]) * 64
 
 
 def test_local_finds_planted_offset(orc):
